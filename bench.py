@@ -1,0 +1,462 @@
+#!/usr/bin/env python
+"""Benchmark of the PDEP hot path on one GB300 (or N replicas).
+
+Workload: the 48^3 Gaussian-well system (L = 20 bohr cube, 64 wells,
+N_occ = 64, N_pdep = 128, 6 Davidson iterations, Sternheimer CG to 1e-10).
+One step = one pdep_solve: random start block, 6 chi0bar applications
+(each 128 perturbations x 64 occupied states of Sternheimer solves, density
+response, projection), Rayleigh-Ritz, orthonormalisation.  The setup
+(potential upload, occupied states) happens once before timing.
+
+  value    Sternheimer solves/s of the mixed-precision path (FP32 CG, FP64
+           refinement), inputs resident in HBM, CUDA events on the stream
+           the library runs on, W warm-up steps then K timed steps.
+  fp64     the same step with the plain FP64 path.
+  e2e      the mixed step through the public API with pinned host buffers
+           (start block in, eigenvalues and eigenvectors out).
+  roofline the dominant kernel class of the timed region, from the library's
+           per-launch CUDA-event profile and its algorithmic flop/byte counts.
+
+--impl reference times the FP64 CPU oracle (Sternheimer CG with the dense
+Hamiltonian) on a bounded sample of the same solves.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Sternheimer solves/s & PDEP eigenpairs/s, mixed vs FP64 on 1 GB300 at eig err<=1e-6"
+WORKLOAD = ("cube48: 48^3 grid, L=20 bohr, 64 Gaussian wells (seed 1501031411), N_occ=64, "
+            "N_pdep=128, 6 Davidson iterations, Sternheimer tol 1e-10")
+# Nominal units x clocks of a GB300 (152 SMs, 128 FP32 lanes each, 2070 MHz):
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12     # 80.5 TFLOP/s FFMA
+FP64_PEAK_TFLOPS = 1.25                                # nominal FP64 rate of GB300
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
+CSRC = os.path.join(ROOT, "paper_1501_03141_gb300", "csrc")
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (one process per GPU; replicas, no data-path collective)
+# ---------------------------------------------------------------------------
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def dist_init(backend):
+    import torch.distributed as dist
+    rank, world, _ = dist_env()
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend, rank=rank, world_size=world)
+    return rank, world
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def reduce_scalar(x: float, op: str, device=None) -> float:
+    """max or sum of a float over ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+REASON_BITS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
+               0x8: "hw_slowdown", 0x10: "sync_boost", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown",
+               0x100: "display_clock_setting"}
+
+
+class ClockSampler:
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "utilization.gpu")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 6:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]),
+                             int(parts[4], 16), float(parts[5])))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        loaded = [r for r in rows if r[4] >= 50] or rows
+        reasons = set()
+        for r in loaded:
+            for bit, name in REASON_BITS.items():
+                if r[3] & bit and name != "gpu_idle":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r[0] for r in loaded),
+                "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows),
+                "samples": len(rows), "samples_under_load": len(loaded),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# roofline of the dominant kernel class
+# ---------------------------------------------------------------------------
+def measured_peaks():
+    try:
+        p = json.load(open(PEAKS_FILE))
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def csrc_hash():
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(CSRC)):
+        if name.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(CSRC, name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(cls_name):
+    """ncu DRAM bytes per launch of a kernel class, if captured on the current source."""
+    try:
+        t = json.load(open(TRAFFIC_FILE))
+    except (OSError, ValueError):
+        return None
+    if t.get("csrc_hash") != csrc_hash():
+        return None
+    v = t.get("classes", {}).get(cls_name)
+    return None if v is None else float(v["dram_bytes_per_launch"])
+
+
+def roofline(prof):
+    hbm, src = measured_peaks()
+    best = None
+    for name, c in prof["classes"].items():
+        if c["launches"] == 0 or c["ms"] <= 0:
+            continue
+        if best is None or c["ms"] > best[1]["ms"]:
+            best = (name, c)
+    if best is None:
+        return None
+    name, c = best
+    per = c["ms"] / c["launches"] / 1e3                     # seconds per launch
+    gbs = c["bytes"] / c["launches"] / per / 1e9
+    tfl = c["flops"] / c["launches"] / per / 1e12
+    alu_peak = FP64_PEAK_TFLOPS if name.endswith("f64") else FP32_PEAK_TFLOPS
+    f_hbm, f_alu = gbs / hbm, tfl / alu_peak
+    share = c["ms"] / sum(v["ms"] for v in prof["classes"].values())
+    tr = traffic_for(name)
+    if f_alu >= f_hbm:
+        r = {"bound": "alu", "achieved": round(tfl, 3), "peak": round(alu_peak, 3),
+             "unit": "TFLOP/s", "frac": round(f_alu, 4),
+             "peak_source": "derived from unit counts x 2070 MHz (" +
+                            ("FP64 nominal 1.25 TFLOP/s" if name.endswith("f64") else
+                             "152 SM x 128 FP32 lanes x 2") + ")",
+             "hbm_frac_of_" + src: round(f_hbm, 4)}
+    else:
+        r = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+             "frac": round(f_hbm, 4), "peak_source": src, "alu_frac": round(f_alu, 4)}
+    r.update({"kernel": name, "launches": c["launches"], "share_of_kernel_time": round(share, 4),
+              "algorithmic_bytes_per_launch": c["bytes"] / c["launches"],
+              "algorithmic_flops_per_launch": c["flops"] / c["launches"],
+              "traffic": tr})
+    return r
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    dist_init("nccl" if torch.cuda.is_available() else "gloo")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1501_03141_gb300 as pg
+    import synthetic
+
+    dev = torch.device("cuda", local)
+    system = synthetic.make_system("cube48")
+    opts = dict(dav_tol=0.0, dav_max_iter=6)
+    stream = torch.cuda.current_stream(dev)
+    ctx = pg.Context(system, precision=pg.PDEP_MIXED, stream=stream.cuda_stream, **opts)
+    dim = ctx.sizes()["n_pdep_dim"]
+    npd = system.n_pdep
+    ev = torch.empty(npd, dtype=torch.float64, device=dev)
+    evec = torch.empty(npd, dim, dtype=torch.float64, device=dev)
+
+    stats = None
+    for _ in range(args.warmup):
+        _, _, stats = ctx.pdep_solve(eigvals=ev, eigvecs=evec)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    pg.profile_start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    solves = 0
+    for _ in range(args.steps):
+        _, _, stats = ctx.pdep_solve(eigvals=ev, eigvecs=evec)
+        solves += stats["sternheimer_solves"]
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    prof = pg.profile_stop()
+    clk = clocks.stop()
+    barrier()
+    t_local = e0.elapsed_time(e1) / 1e3
+    t = reduce_scalar(t_local, "max", dev if world > 1 else None)
+    total_solves = reduce_scalar(solves, "sum", dev if world > 1 else None)
+    value = total_solves / t
+    eigpairs = world * npd * args.steps / t
+    mixed_vals = ev.cpu().numpy()
+
+    # e2e: the same step through the public API with pinned host buffers
+    phi0 = torch.from_numpy(synthetic.random_vectors(11, npd, dim)).pin_memory()
+    ev_h = torch.empty(npd, dtype=torch.float64).pin_memory()
+    evec_h = torch.empty(npd, dim, dtype=torch.float64).pin_memory()
+    if args.e2e_steps > 0:
+        ctx.pdep_solve(phi0=phi0, eigvals=ev_h, eigvecs=evec_h)
+    barrier()
+    t0 = time.perf_counter()
+    e_solves = 0
+    for _ in range(args.e2e_steps):
+        _, _, st = ctx.pdep_solve(phi0=phi0, eigvals=ev_h, eigvecs=evec_h)
+        e_solves += st["sternheimer_solves"]
+    torch.cuda.synchronize(dev)
+    te = reduce_scalar(time.perf_counter() - t0, "max", dev if world > 1 else None)
+    e_solves = reduce_scalar(e_solves, "sum", dev if world > 1 else None)
+    e2e = {"value": round(e_solves / te, 2) if args.e2e_steps > 0 else None, "unit": "solves/s",
+           "h2d_bytes_per_step": int(phi0.numel() * 8),
+           "d2h_bytes_per_step": int((ev_h.numel() + evec_h.numel()) * 8),
+           "steps": args.e2e_steps}
+    ctx.close()
+
+    # plain FP64 path on the same step
+    fp64 = None
+    if args.fp64_steps > 0:
+        c64 = pg.Context(system, precision=pg.PDEP_FP64, stream=stream.cuda_stream, **opts)
+        for _ in range(args.fp64_warmup):
+            c64.pdep_solve(eigvals=ev, eigvecs=evec)
+        torch.cuda.synchronize(dev)
+        barrier()
+        e0.record(stream)
+        s64 = 0
+        for _ in range(args.fp64_steps):
+            _, _, st = c64.pdep_solve(eigvals=ev, eigvecs=evec)
+            s64 += st["sternheimer_solves"]
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        t64 = reduce_scalar(e0.elapsed_time(e1) / 1e3, "max", dev if world > 1 else None)
+        s64 = reduce_scalar(s64, "sum", dev if world > 1 else None)
+        v64 = ev.cpu().numpy()
+        err = np.abs(mixed_vals - v64) / np.abs(v64)
+        fp64 = {"value": round(s64 / t64, 2), "unit": "solves/s",
+                "eigenpairs_per_s": round(world * npd * args.fp64_steps / t64, 4),
+                "ms_per_step": round(1e3 * t64 / args.fp64_steps, 1),
+                "steps": args.fp64_steps, "warmup": args.fp64_warmup,
+                "mixed_eig_rel_err_max": float(err.max()),
+                "mixed_eig_rel_err": [float(f"{x:.3e}") for x in err]}
+        c64.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": "solves/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * t / args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "mixed: FP32 FFT/H*psi/P_v in CG, "
+                       "FP64 refinement, density response, orthonormalisation, Rayleigh-Ritz",
+                       "l2": "working set larger than L2 (transform scratch ~1.4 GB per "
+                             "chi0bar application), no flush",
+                       "parallelism": f"replicas x{world}",
+                       "solves_per_step": stats["sternheimer_solves"],
+                       "cg_iterations_per_step": stats["cg_iterations"],
+                       "cg_iterations_max": stats["cg_iterations_max"],
+                       "refine_rounds_max": stats["refine_rounds_max"],
+                       "max_cg_residual": stats["max_cg_residual"]},
+            "eigenpairs_per_s": round(eigpairs, 4),
+            "fp64": fp64,
+            "e2e": e2e,
+            "gpu_launches": int(prof["launches"]),
+            "roofline": roofline(prof),
+            "kernel_profile": {k: {"launches": v["launches"], "ms": round(v["ms"], 2)}
+                               for k, v in prof["classes"].items() if v["launches"]},
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (the reference arm and the cpu_baseline object)
+# ---------------------------------------------------------------------------
+def _oracle_setup():
+    import synthetic
+    from oracle import response
+    from oracle.basis import Basis
+    from oracle.hamiltonian import dense_hamiltonian, ks_states
+    s = synthetic.make_system("cube48")
+    b = Basis(s.grid, s.cell)
+    ks = ks_states(b, s.v_r, s.n_occ)
+    h = dense_hamiltonian(b, s.v_r)
+    dv = synthetic.random_grid_potentials(5, 1, s.grid, s.cell)[0]
+    u = response.occupied_grid(b, ks)
+    return s, b, ks, h, dv, u
+
+
+def _oracle_solves(setup, n_states):
+    """Time the oracle's Sternheimer CG on n_states occupied states spread evenly
+    over the occupied spectrum (one perturbation)."""
+    from oracle import response
+    s, b, ks, h, dv, u = setup
+    states = sorted(set(int(round(x)) for x in
+                        [i * (s.n_occ - 1) / max(1, n_states - 1) for i in range(n_states)]))
+    t0 = time.perf_counter()
+    response.sternheimer_cg(b, ks, h, dv, tol=s.cg_tol, u_occ=u, states=states)
+    return len(states), time.perf_counter() - t0
+
+
+def cpu_baseline(seconds_budget=20.0):
+    setup = _oracle_setup()
+    n, dt = _oracle_solves(setup, 1)
+    k = 1
+    while dt * 2.2 < seconds_budget and k < setup[0].n_occ:
+        k = min(setup[0].n_occ, 2 * k)
+        n, dt = _oracle_solves(setup, k)
+    return {"value": round(n / dt, 4), "unit": "solves/s", "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": f"{n} Sternheimer CG solves (dense FP64 H, tol 1e-10, occupied states "
+                      f"spread over the spectrum, one random perturbation) of the cube48 "
+                      f"workload in {dt:.1f} s; setup (dense H, eigh) excluded"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    setup = _oracle_setup()
+    k = 4
+    for _ in range(args.warmup):
+        _oracle_solves(setup, 1)
+    t0 = time.perf_counter()
+    n = 0
+    for _ in range(args.steps):
+        m, _ = _oracle_solves(setup, k)
+        n += m
+    dt = time.perf_counter() - t0
+    v = n / dt
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "solves/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * dt / args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "parallelism": "CPU oracle, rank 0 only"},
+            "cpu_baseline": {"value": round(v, 4), "unit": "solves/s", "cores": os.cpu_count(),
+                             "kind": "oracle",
+                             "sample": f"{k} Sternheimer CG solves per step (dense FP64 H, "
+                                       "occupied states spread over the spectrum, one "
+                                       "perturbation)"},
+            "e2e": {"value": round(v, 4), "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_small(args):
+    """One chi0bar application (16 perturbations) on the same system: the small
+    case for hardware-counter captures."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1501_03141_gb300 as pg
+    import synthetic
+    system = synthetic.make_system("cube48")
+    prec = pg.PDEP_FP64 if args.case == "small64" else pg.PDEP_MIXED
+    with pg.Context(system, precision=prec) as ctx:
+        dim = ctx.sizes()["n_pdep_dim"]
+        phi = torch.tensor(synthetic.random_vectors(3, 16, dim), device="cuda")
+        out = ctx.chi0_apply(phi, allow_unconverged=True)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": args.case, "norm": float(out.norm())}))
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--fp64-warmup", type=int, default=1)
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", choices=["bench", "small", "small64"], default="bench",
+                    help="small/small64: one chi0bar application of 16 perturbations "
+                         "(mixed/FP64), for profiler captures")
+    args = ap.parse_args(argv)
+    if args.case != "bench":
+        run_small(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,208 @@
+/*
+ * pdep.h -- C ABI of the GB300 PDEP library (libpdep.so).
+ *
+ * The library computes the projective dielectric eigendecomposition (PDEP)
+ * of Govoni & Galli, "Large scale GW calculations" (Sec. II D, "Projective
+ * dielectric eigenpotential (PDEP) basis set"): the leading eigenpairs of the
+ * symmetrised static irreducible polarizability
+ *     chi0bar = v^{1/2} chi0 v^{1/2}          (Eq. symmoperator, omega = 0)
+ * by a Davidson iteration (Sec. II D; Fig. pdepscheme) in which every
+ * application of chi0bar is a batch of Sternheimer solves (Eq. stern)
+ *     (H - eps_v) P_c dpsi_v = - P_c dV psi_v,   P_c = 1 - sum_v |v><v|,
+ * one per occupied state v and perturbation, followed by the density
+ * response of Eq. (deltani) and the projection of Eq. (chiisamatrixinpdep).
+ *
+ * Model and conventions
+ *   - Hartree atomic units, Gamma point, spin-unpolarised, real orbitals,
+ *     integer occupations (the n_occ lowest states), local potential only:
+ *     H = -1/2 nabla^2 + V(r).  chi0bar eigenvalues are dimensionless, so
+ *     the paper's Rydberg units give the same numbers.
+ *   - Orthorhombic cell L1 x L2 x L3 (bohr) on an N1 x N2 x N3 grid; grid
+ *     arrays are row-major with N3 fastest; point (i1,i2,i3) sits at
+ *     (i1 L1/N1, i2 L2/N2, i3 L3/N3).
+ *   - Basis (Eq. planewaveexpansionofwfc): plane waves with G =
+ *     2 pi (n1/L1, n2/L2, n3/L3) and 0.5 |G|^2 <= ecut (compared in double
+ *     precision).  ecut = 0 selects the alias-free grid rule
+ *     ecut = 0.5 (min_i 2 pi r_i / L_i)^2 with r_i = (N_i - 1) / 4.
+ *   - Real-coefficient layout of a sphere vector (length n_pw = 2 nh + 1):
+ *     the half space {n3 > 0} u {n3 = 0, n2 > 0} u {n3 = n2 = 0, n1 > 0},
+ *     restricted to the sphere and sorted by (n3, n2, n1) ascending, gives
+ *     G_0 .. G_{nh-1}; a real function f(r) = Omega^{-1/2} sum_G c(G) e^{iG.r}
+ *     is stored as x[2k] = sqrt2 Re c(G_k), x[2k+1] = sqrt2 Im c(G_k),
+ *     x[2nh] = c(0).  Euclidean dot products are L2 inner products.
+ *   - A PDEP vector (the PDEP basis excludes G = 0, the body of Table
+ *     limitqchi0) has length n_pdep_dim = 2 nh: the first 2 nh entries.
+ *   - chi0bar is restricted to that sphere minus G = 0; v^{1/2}(G) =
+ *     sqrt(4 pi)/|G| (e^2 = 1).  The density response of a perturbation
+ *     dV is dn(r) = 4 sum_v psi_v(r) dpsi_v(r) (2 for spin, 2 for the c.c.
+ *     term of Eq. deltani).
+ *
+ * Memory, streams, errors
+ *   - Array arguments may be host or device pointers; the library inspects
+ *     each pointer and stages host data through its own device workspace.
+ *     The caller owns every argument buffer; the library owns the context and
+ *     its workspace and frees them in pdep_destroy.
+ *   - 'stream' is a cudaStream_t (NULL = legacy default stream).  Calls
+ *     enqueue work on it and return once their results are complete in the
+ *     output buffers (the Sternheimer and Davidson loops read convergence
+ *     flags from the device between steps).
+ *   - Every function returns a pdep_status.  pdep_last_error() gives a
+ *     human-readable message for the most recent failure in this thread.
+ *     Device-detected conditions (a non-finite CG scalar, a solve that hit
+ *     its iteration cap) are returned as PDEP_ERR_NONFINITE /
+ *     PDEP_ERR_NOT_CONVERGED by the call that detected them; outputs are
+ *     still written.
+ *   - One GPU (the device current when pdep_setup is called).  Calls on one
+ *     context must not run concurrently.
+ */
+#ifndef PDEP_H
+#define PDEP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pdep_ctx pdep_ctx; /* opaque; owned by the library */
+
+typedef enum {
+  PDEP_OK = 0,
+  PDEP_ERR_INVALID_ARG = 1,   /* bad size, unsupported grid, null pointer */
+  PDEP_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+  PDEP_ERR_OOM = 3,           /* device allocation failed or workspace limit hit */
+  PDEP_ERR_NO_GAP = 4,        /* eps_{n_occ+1} - eps_{n_occ} < gap_min */
+  PDEP_ERR_NOT_CONVERGED = 5, /* a solve reached its iteration cap */
+  PDEP_ERR_NONFINITE = 6,     /* NaN/Inf met in the data or a CG scalar */
+  PDEP_ERR_TIMEOUT = 7,       /* reserved: no device loop waits on another agent */
+  PDEP_ERR_UNSUPPORTED = 8    /* option combination not implemented */
+} pdep_status;
+
+typedef enum {
+  PDEP_FP64 = 0,  /* every step in FP64 */
+  PDEP_MIXED = 1  /* FP32 FFTs, H*psi and projections inside the Sternheimer
+                     CG, FP64 residual refinement, FP64 density response,
+                     orthogonalisation and Rayleigh-Ritz */
+} pdep_precision;
+
+/* One system. v_r: [N1*N2*N3] local potential (Ha), host or device. */
+typedef struct {
+  int grid[3];
+  double cell[3];
+  double ecut;        /* Ha; 0 = alias-free grid rule */
+  const double* v_r;
+  int n_occ;          /* occupied states (>= 1) */
+  int n_pdep;         /* PDEP eigenpairs wanted (>= 1) */
+} pdep_system_desc;
+
+typedef struct {
+  int precision;             /* pdep_precision */
+  double cg_tol;             /* Sternheimer: ||b - A x|| / ||b|| target (1e-10) */
+  int cg_max_iter;           /* CG iteration cap per solve (FP64 path) */
+  double inner_tol;          /* mixed: FP32 inner CG reduction per refinement round */
+  int inner_max_iter;        /* mixed: FP32 CG iteration cap per round */
+  int max_refine;            /* mixed: refinement rounds cap */
+  double dav_tol;            /* Davidson: max ||chi0bar x - theta x|| / |theta_1|; 0 = run dav_max_iter */
+  int dav_max_iter;          /* Davidson iterations cap (each applies chi0bar once) */
+  int dav_subspace_factor;   /* subspace holds at most factor * n_pdep vectors (>= 2) */
+  unsigned long long seed;   /* Philox4x32-10 seed of the random start block */
+  double gap_min;            /* minimum HOMO-LUMO gap (Ha) */
+  double setup_tol;          /* setup eigensolver: ||H psi - eps psi|| target */
+  int setup_max_iter;
+  size_t workspace_limit_bytes; /* 0 = no limit */
+} pdep_options;
+
+typedef struct {
+  int dav_iterations;           /* chi0bar applications performed */
+  int converged;                /* 1 if dav_tol was met (or dav_tol = 0) */
+  long long sternheimer_solves; /* (v, perturbation) systems solved to cg_tol */
+  long long cg_iterations;      /* sum over solves (FP32 inner iterations in mixed mode) */
+  int cg_iterations_max;        /* largest per-solve count */
+  int refine_rounds_max;        /* mixed mode: largest refinement round count */
+  double max_cg_residual;       /* largest final ||b - A x|| / ||b||, recomputed in FP64 */
+  double max_dav_residual;      /* largest final ||chi0bar x - theta x|| / |theta_1| */
+  double seconds;               /* wall time of the call */
+} pdep_stats;
+
+/* Fill *opt with the defaults (FP64, cg_tol 1e-10, dav_tol 1e-8, ...). */
+void pdep_default_options(pdep_options* opt);
+
+/* Build one context for n_sys systems: sphere tables, potential upload and the
+ * FP64 setup eigensolve of the n_occ lowest states (the unperturbed occupied
+ * states of Sec. II D), with the gap check.  Returns PDEP_ERR_NO_GAP when
+ * eps_{n_occ+1} - eps_{n_occ} < gap_min, PDEP_ERR_INVALID_ARG for an
+ * unsupported grid (N1 in {24,32,40,48,64}; N2 = N3 in that set, or
+ * N2 = 64 with N3 = 192). */
+int pdep_setup(const pdep_system_desc* sys, int n_sys, const pdep_options* opt, void* stream,
+               pdep_ctx** out);
+
+/* Sizes of system 'sys': n_pw (sphere real DOF), n_r (grid points),
+ * n_pdep_dim = n_pw - 1.  Any output pointer may be NULL. */
+int pdep_get_sizes(const pdep_ctx* ctx, int sys, int* n_pw, int* n_r, int* n_pdep_dim);
+
+/* Occupied states of the setup: psi [n_occ][n_pw] real layout (may be NULL),
+ * eps [n_occ + 1] eigenvalues including the lowest empty state (may be NULL). */
+int pdep_get_occupied(pdep_ctx* ctx, int sys, double* psi, double* eps, void* stream);
+
+/* chi0bar applied to n_pert PDEP vectors (Eqs. stern, deltani,
+ * chiisamatrixinpdep): phi [n_pert][n_pdep_dim] in, chi0_phi
+ * [n_pert][n_pdep_dim] out; dn_r [n_pert][n_r] (may be NULL) receives the
+ * density response dn(r) (electrons/bohr^3) to dV = v^{1/2} phi. */
+int chi0_apply(pdep_ctx* ctx, int sys, const double* phi, int n_pert, double* chi0_phi,
+               double* dn_r, void* stream);
+
+/* Sternheimer solves (Eq. stern) for n_pert perturbing potentials dv_r
+ * [n_pert][n_r] (Ha) against every occupied state: dpsi [n_pert][n_occ][n_pw]
+ * receives P_c dpsi_v; iters and resid [n_pert*n_occ] (may be NULL) receive
+ * the CG iteration count and the final relative residual recomputed in FP64. */
+int sternheimer_solve(pdep_ctx* ctx, int sys, const double* dv_r, int n_pert, double* dpsi,
+                      int* iters, double* resid, void* stream);
+
+/* Davidson PDEP solve (Sec. II D): the n_pdep most negative eigenvalues of
+ * chi0bar, ascending, into eigvals [n_pdep]; eigvecs [n_pdep][n_pdep_dim]
+ * (may be NULL).  phi0 [n_pdep][n_pdep_dim] is the start block (NULL: seeded
+ * Philox4x32-10 normal deviates).  sys = -1 solves every system in turn and
+ * then eigvals/eigvecs are the concatenation over systems.  stats is a host
+ * struct (may be NULL). */
+int pdep_solve(pdep_ctx* ctx, int sys, const double* phi0, double* eigvals, double* eigvecs,
+               pdep_stats* stats, void* stream);
+
+/* y = H x for n sphere vectors x [n][n_pw] -> y [n][n_pw], H = -nabla^2/2 + V
+ * (the local-potential Hamiltonian of the setup), evaluated with the pruned
+ * sphere <-> grid transforms; precision PDEP_FP64 or PDEP_MIXED (FP32
+ * transforms).  This is the H*psi kernel the Sternheimer CG applies. */
+int pdep_apply_hamiltonian(pdep_ctx* ctx, int sys, const double* x, int n, double* y,
+                           int precision, void* stream);
+
+/* u [n][n_r]: u(r_k) = sum_G c(G) exp(i G.r_k) for n sphere vectors x
+ * [n][n_pw] (so the normalised function is Omega^{-1/2} u). */
+int pdep_to_grid(pdep_ctx* ctx, int sys, const double* x, int n, double* u, void* stream);
+
+/* Kernel profile of this process's library calls (CUDA events around each
+ * launch of the main kernel families, on the stream the kernel runs on).
+ * enable = 1 clears the counters and starts recording; enable = 0 stops,
+ * waits for the recorded events and fills *out (may be NULL).  flops and
+ * bytes are the algorithmic counts of the launches (complex line FFT:
+ * 5 L log2 L flops; bytes: every input read and output written once). */
+#define PDEP_PROFILE_CLASSES 10
+typedef struct {
+  char name[24];
+  long long launches;
+  double ms;
+  double flops;
+  double bytes;
+} pdep_kernel_class;
+typedef struct {
+  long long launches; /* every kernel the library launched while recording */
+  pdep_kernel_class cls[PDEP_PROFILE_CLASSES];
+} pdep_profile_t;
+int pdep_profile(int enable, pdep_profile_t* out);
+
+void pdep_destroy(pdep_ctx* ctx);
+const char* pdep_status_string(int status);
+const char* pdep_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PDEP_H */

@@ -54,10 +54,12 @@ def sternheimer_sos(basis: Basis, ks: KSStates, dv_r, u_occ=None):
 
 
 def sternheimer_cg(basis: Basis, ks: KSStates, h, dv_r, tol=1e-12, max_iter=5000,
-                   u_occ=None):
+                   u_occ=None, states=None):
     """P_c dpsi_v by CG on P_c (H - eps_v) P_c x = -P_c dV psi_v; (N_occ, N_pw).
 
     h is the dense Hamiltonian of the unperturbed system (dense_hamiltonian).
+    states (optional) restricts the solves to those occupied indices; the
+    other rows of the result stay zero.
     Returns (dpsi, iterations, relative residuals).
     """
     if u_occ is None:
@@ -72,7 +74,7 @@ def sternheimer_cg(basis: Basis, ks: KSStates, h, dv_r, tol=1e-12, max_iter=5000
     out = np.zeros((nocc, basis.n_pw))
     its = np.zeros(nocc, dtype=int)
     res = np.zeros(nocc)
-    for v in range(nocc):
+    for v in (range(nocc) if states is None else states):
         b = -pc(w[v])
         bn = np.linalg.norm(b)
         x = np.zeros_like(b)

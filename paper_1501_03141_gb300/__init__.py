@@ -1,0 +1,189 @@
+"""GB300 PDEP library: Python front end of libpdep.so.
+
+The hot path (Sec. II D of Govoni & Galli, "Large scale GW calculations"):
+Davidson diagonalisation of chi0bar = v^{1/2} chi0 v^{1/2} at omega = 0,
+where every chi0bar application is a batch of Sternheimer solves.  All the
+arithmetic runs in the CUDA kernels of csrc/; this module only marshals
+arguments through the C ABI of include/pdep.h.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _abi
+from ._abi import PDEP_FP64, PDEP_MIXED, PdepError  # noqa: F401
+
+
+def default_options(**kw) -> _abi.pdep_options:
+    """pdep_options with the library defaults, overridden by keyword."""
+    lib = _abi.load()
+    o = _abi.pdep_options()
+    lib.pdep_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _stream(stream):
+    if stream is not None:
+        return stream
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:  # pragma: no cover - torch is optional for the binding
+        pass
+    return None
+
+
+def profile_start():
+    """Start recording per-kernel-class CUDA-event times (pdep_profile(1))."""
+    _abi.check(_abi.load().pdep_profile(1, None), "pdep_profile")
+
+
+def profile_stop():
+    """Stop recording; returns {'launches': n, 'classes': {name: {...}}}."""
+    out = _abi.pdep_profile_t()
+    _abi.check(_abi.load().pdep_profile(0, ctypes.byref(out)), "pdep_profile")
+    classes = {}
+    for c in out.cls:
+        classes[c.name.decode()] = {"launches": c.launches, "ms": c.ms, "flops": c.flops,
+                                    "bytes": c.bytes}
+    return {"launches": out.launches, "classes": classes}
+
+
+class Context:
+    """One pdep_ctx holding one or more systems (pdep_setup ... pdep_destroy).
+
+    systems: objects with .grid, .cell, .v_r (float64 array), .n_occ, .n_pdep
+    (e.g. synthetic.System).  ecut = 0 selects the alias-free grid rule.
+    """
+
+    def __init__(self, systems, options=None, stream=None, ecut=0.0, **opt_kw):
+        if not isinstance(systems, (list, tuple)):
+            systems = [systems]
+        lib = _abi.load()
+        self._lib = lib
+        self.options = options if options is not None else default_options(**opt_kw)
+        n = len(systems)
+        desc = (_abi.pdep_system_desc * n)()
+        self._keep = []
+        for i, s in enumerate(systems):
+            v = np.ascontiguousarray(np.asarray(s.v_r, dtype=np.float64))
+            self._keep.append(v)
+            desc[i].grid[:] = [int(x) for x in s.grid]
+            desc[i].cell[:] = [float(x) for x in s.cell]
+            desc[i].ecut = float(ecut)
+            desc[i].v_r = v.ctypes.data
+            desc[i].n_occ = int(s.n_occ)
+            desc[i].n_pdep = int(s.n_pdep)
+        self.stream = stream
+        h = ctypes.c_void_p()
+        _abi.check(lib.pdep_setup(desc, n, ctypes.byref(self.options), _stream(stream),
+                                  ctypes.byref(h)), "pdep_setup")
+        self._h = h
+        self.systems = list(systems)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.pdep_destroy(self._h)
+            self._h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- queries -------------------------------------------------------------
+    def sizes(self, sys: int = 0):
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _abi.check(self._lib.pdep_get_sizes(self._h, sys, ctypes.byref(a), ctypes.byref(b),
+                                            ctypes.byref(c)), "pdep_get_sizes")
+        return {"n_pw": a.value, "n_r": b.value, "n_pdep_dim": c.value}
+
+    def occupied(self, sys: int = 0):
+        """(psi [n_occ, n_pw], eps [n_occ + 1]) as numpy arrays."""
+        sz = self.sizes(sys)
+        s = self.systems[sys]
+        psi = np.empty((s.n_occ, sz["n_pw"]))
+        eps = np.empty(s.n_occ + 1)
+        _abi.check(self._lib.pdep_get_occupied(self._h, sys, _abi.ptr(psi), _abi.ptr(eps),
+                                               _stream(self.stream)), "pdep_get_occupied")
+        return psi, eps
+
+    def apply_hamiltonian(self, x, sys: int = 0, precision: int = PDEP_FP64, out=None):
+        """H x for sphere vectors x [n, n_pw]."""
+        if out is None:
+            out = np.empty_like(x) if isinstance(x, np.ndarray) else x.new_empty(x.shape)
+        _abi.check(self._lib.pdep_apply_hamiltonian(self._h, sys, _abi.ptr(x), int(x.shape[0]),
+                                                    _abi.ptr(out), precision,
+                                                    _stream(self.stream)), "pdep_apply_hamiltonian")
+        return out
+
+    def to_grid(self, x, sys: int = 0, out=None):
+        """u(r) = sum_G c(G) e^{iG.r} for sphere vectors x [n, n_pw]; shape [n, n_r]."""
+        n_r = self.sizes(sys)["n_r"]
+        if out is None:
+            out = np.empty((x.shape[0], n_r))
+        _abi.check(self._lib.pdep_to_grid(self._h, sys, _abi.ptr(x), int(x.shape[0]), _abi.ptr(out),
+                                          _stream(self.stream)), "pdep_to_grid")
+        return out
+
+    # -- hot path ------------------------------------------------------------
+    def chi0_apply(self, phi, sys: int = 0, out=None, dn=None, allow_unconverged=False):
+        """chi0bar phi for phi [n_pert, n_pdep_dim]; returns out (and dn if given)."""
+        n_pert = int(phi.shape[0])
+        if out is None:
+            out = np.empty_like(phi) if isinstance(phi, np.ndarray) else phi.new_empty(phi.shape)
+        allow = (_abi.PDEP_OK, _abi.PDEP_ERR_NOT_CONVERGED) if allow_unconverged else (_abi.PDEP_OK,)
+        _abi.check(self._lib.chi0_apply(self._h, sys, _abi.ptr(phi), n_pert, _abi.ptr(out),
+                                        _abi.ptr(dn), _stream(self.stream)), "chi0_apply", allow)
+        return out
+
+    def sternheimer_solve(self, dv, sys: int = 0, dpsi=None, iters=None, resid=None,
+                          allow_unconverged=False):
+        """P_c dpsi for dv [n_pert, n_r]; returns (dpsi [n_pert, n_occ, n_pw], iters, resid)."""
+        n_pert = int(dv.shape[0])
+        sz = self.sizes(sys)
+        s = self.systems[sys]
+        if dpsi is None:
+            dpsi = np.empty((n_pert, s.n_occ, sz["n_pw"]))
+        if iters is None:
+            iters = np.empty(n_pert * s.n_occ, dtype=np.int32)
+        if resid is None:
+            resid = np.empty(n_pert * s.n_occ)
+        allow = (_abi.PDEP_OK, _abi.PDEP_ERR_NOT_CONVERGED) if allow_unconverged else (_abi.PDEP_OK,)
+        _abi.check(self._lib.sternheimer_solve(self._h, sys, _abi.ptr(dv), n_pert, _abi.ptr(dpsi),
+                                               _abi.ptr(iters), _abi.ptr(resid),
+                                               _stream(self.stream)), "sternheimer_solve", allow)
+        return dpsi, iters, resid
+
+    def pdep_solve(self, sys: int = 0, phi0=None, eigvals=None, eigvecs=None,
+                   allow_unconverged=False):
+        """Davidson PDEP solve; returns (eigvals, eigvecs, stats dict)."""
+        systems = self.systems if sys == -1 else [self.systems[sys]]
+        idx = range(len(self.systems)) if sys == -1 else [sys]
+        nval = sum(s.n_pdep for s in systems)
+        nvec = sum(s.n_pdep * self.sizes(i)["n_pdep_dim"] for s, i in zip(systems, idx))
+        if eigvals is None:
+            eigvals = np.empty(nval)
+        if eigvecs is None:
+            eigvecs = np.empty(nvec)
+        st = _abi.pdep_stats()
+        allow = (_abi.PDEP_OK, _abi.PDEP_ERR_NOT_CONVERGED) if allow_unconverged else (_abi.PDEP_OK,)
+        _abi.check(self._lib.pdep_solve(self._h, sys, _abi.ptr(phi0), _abi.ptr(eigvals),
+                                        _abi.ptr(eigvecs), ctypes.byref(st),
+                                        _stream(self.stream)), "pdep_solve", allow)
+        stats = {k: getattr(st, k) for k, _ in _abi.pdep_stats._fields_}
+        return eigvals, eigvecs, stats

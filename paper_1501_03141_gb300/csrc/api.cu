@@ -1,0 +1,1273 @@
+// C ABI and host orchestration of the PDEP hot path (Sec. II D of Govoni &
+// Galli): setup eigensolve, batched Sternheimer CG, density response,
+// chi0bar application and the Davidson iteration.  Everything here only
+// enqueues kernels on the caller's stream and reads small convergence flags
+// back between steps.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "linalg.cuh"
+#include "transforms.cuh"
+
+namespace pdep {
+
+static thread_local std::string g_last_error;
+
+void set_last_error(const char* file, int line, const char* msg) {
+  char buf[512];
+  snprintf(buf, sizeof(buf), "%s:%d: %s", file, line, msg);
+  g_last_error = buf;
+}
+
+static int fail(int status, const char* msg) {
+  g_last_error = msg;
+  return status;
+}
+
+#define CK(call)                                                                 \
+  do {                                                                           \
+    cudaError_t e_ = (call);                                                     \
+    if (e_ != cudaSuccess) {                                                     \
+      pdep::set_last_error(__FILE__, __LINE__, cudaGetErrorString(e_));          \
+      return e_ == cudaErrorMemoryAllocation ? PDEP_ERR_OOM : PDEP_ERR_CUDA;     \
+    }                                                                            \
+  } while (0)
+
+#define RET(call)                  \
+  do {                             \
+    int r_ = (call);               \
+    if (r_ != PDEP_OK) return r_;  \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// per-system data
+// ---------------------------------------------------------------------------
+struct SysData {
+  int N[3] = {0, 0, 0};
+  double L[3] = {0, 0, 0};
+  double omega = 0, ecut = 0;
+  int n_r = 0, n_half = 0, n_pw = 0, ld = 0, n_occ = 0, n_pdep = 0;
+  int n_col = 0, n_ucol = 0, R3 = 0;
+  std::vector<UCol> ucol;
+  std::vector<int2> slot;
+  std::vector<double> g2;
+  UCol* d_ucol = nullptr;
+  int2* d_slot = nullptr;
+  double* d_g2 = nullptr;
+  cpx<double>* d_tw64[3] = {nullptr, nullptr, nullptr};
+  cpx<float>* d_tw32[3] = {nullptr, nullptr, nullptr};
+  double* d_v = nullptr;
+  float* d_vf = nullptr;
+  double* d_psi = nullptr;   // [n_occ][ld]
+  float* d_psif = nullptr;
+  double* d_u = nullptr;     // [n_occ][n_r]  u_v(r) = Omega^{1/2} psi_v(r)
+  double* d_negeps = nullptr;
+  double* d_ekin = nullptr;
+  std::vector<double> eps;   // n_occ + 1
+  double alpha = 0;          // shift of the occupied space in H - eps_v + alpha P_v
+  SphereDev<double> sd{};
+  SphereDev<float> sf{};
+};
+
+}  // namespace pdep
+
+using namespace pdep;
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+struct pdep_ctx {
+  int device = 0;
+  pdep_options opt{};
+  std::vector<SysData> sys;
+  std::map<std::string, DevBuf> bufs;
+  size_t ws_bytes = 0;
+  std::vector<void*> owned;
+  unsigned* d_status = nullptr;
+  int* d_counter = nullptr;
+  int* h_pin = nullptr;  // pinned host scratch (ints)
+  // statistics of the current call
+  long long st_solves = 0, st_cg_iters = 0;
+  int st_cg_max = 0, st_refine_max = 0;
+  double st_max_res = 0;
+};
+
+namespace {
+
+template <typename T>
+int persistent(pdep_ctx* c, T** p, size_t count) {
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * count);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(PDEP_ERR_OOM, "cudaMalloc failed for a persistent buffer");
+  }
+  c->owned.push_back(*p);
+  return PDEP_OK;
+}
+
+// named, grow-only workspace buffer
+template <typename T>
+int ws(pdep_ctx* c, const char* name, size_t count, T** out) {
+  if (count == 0) count = 1;
+  size_t bytes = sizeof(T) * count;
+  DevBuf& b = c->bufs[name];
+  if (b.cap < bytes) {
+    size_t newcap = bytes;
+    if (c->opt.workspace_limit_bytes && c->ws_bytes - b.cap + newcap > c->opt.workspace_limit_bytes)
+      return fail(PDEP_ERR_OOM, "workspace limit exceeded");
+    if (b.p) {
+      cudaFree(b.p);
+      c->ws_bytes -= b.cap;
+      b.p = nullptr;
+      b.cap = 0;
+    }
+    cudaError_t e = cudaMalloc(&b.p, newcap);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(PDEP_ERR_OOM, "cudaMalloc failed for the workspace");
+    }
+    b.cap = newcap;
+    c->ws_bytes += newcap;
+  }
+  *out = (T*)b.p;
+  return PDEP_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+cudaMemcpyKind kind_to_dev(const void* src) {
+  return is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+}
+cudaMemcpyKind kind_from_dev(const void* dst) {
+  return is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+}
+
+// host source -> host or device destination
+int copy_from_host(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  if (is_device_ptr(dst)) {
+    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+  } else {
+    memcpy(dst, src, bytes);
+  }
+  return PDEP_OK;
+}
+
+int sync(cudaStream_t st) {
+  CK(cudaStreamSynchronize(st));
+  return PDEP_OK;
+}
+
+int read_int(pdep_ctx* c, const int* d, int* h, cudaStream_t st) {
+  CK(cudaMemcpyAsync(c->h_pin, d, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  *h = *c->h_pin;
+  return PDEP_OK;
+}
+
+int check_status(pdep_ctx* c, cudaStream_t st) {
+  unsigned h = 0;
+  CK(cudaMemcpyAsync(c->h_pin, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  memcpy(&h, c->h_pin, sizeof(unsigned));
+  if (h & DEV_NONFINITE) return fail(PDEP_ERR_NONFINITE, "non-finite value met on the device");
+  if (h & DEV_BREAKDOWN) return fail(PDEP_ERR_NONFINITE, "CG breakdown (p.Ap <= 0)");
+  return PDEP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// sphere tables (Eq. planewaveexpansionofwfc at Gamma, half-space layout)
+// ---------------------------------------------------------------------------
+int build_sphere(SysData& s, double ecut_in) {
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int a = 0; a < 3; ++a)
+    if (s.N[a] <= 0 || !(s.L[a] > 0)) return fail(PDEP_ERR_INVALID_ARG, "bad grid or cell");
+  double ecut = ecut_in;
+  if (!(ecut > 0)) {
+    double gmax = 1e300;
+    for (int a = 0; a < 3; ++a) gmax = std::min(gmax, two_pi * ((s.N[a] - 1) / 4.0) / s.L[a]);
+    ecut = 0.5 * gmax * gmax;
+  }
+  s.ecut = ecut;
+  s.omega = s.L[0] * s.L[1] * s.L[2];
+  s.n_r = s.N[0] * s.N[1] * s.N[2];
+  int lim[3];
+  for (int a = 0; a < 3; ++a) lim[a] = (s.N[a] - 1) / 2;
+  auto inside = [&](int n1, int n2, int n3) {
+    double gx = two_pi * n1 / s.L[0], gy = two_pi * n2 / s.L[1], gz = two_pi * n3 / s.L[2];
+    return 0.5 * (gx * gx + gy * gy + gz * gz) <= ecut;
+  };
+  // x-extent of every (n2, n3) column
+  auto r1 = [&](int n2, int n3) {
+    if (!inside(0, n2, n3)) return -1;
+    int r = 0;
+    while (r + 1 <= lim[0] && inside(r + 1, n2, n3)) ++r;
+    return r;
+  };
+  // aliasing guard: every product of two sphere functions must fit the grid
+  for (int n3 = -lim[2]; n3 <= lim[2]; ++n3)
+    for (int n2 = -lim[1]; n2 <= lim[1]; ++n2) {
+      int r = r1(n2, n3);
+      if (r < 0) continue;
+      if (2 * std::abs(n2) >= s.N[1] / 2 || 2 * std::abs(n3) >= s.N[2] / 2 || 2 * r >= s.N[0] / 2)
+        return fail(PDEP_ERR_INVALID_ARG, "ecut too large for the grid (products would alias)");
+    }
+  int R3 = -1;
+  for (int n3 = 0; n3 <= lim[2]; ++n3)
+    if (r1(0, n3) >= 0) R3 = n3;
+  if (R3 < 0) return fail(PDEP_ERR_INVALID_ARG, "empty sphere");
+  s.R3 = R3;
+  // full column list in (n3, n2) order
+  std::map<std::pair<int, int>, int> colidx;
+  s.slot.assign(2 * R3 + 1, make_int2(0, 0));
+  int ncol = 0;
+  for (int n3 = -R3; n3 <= R3; ++n3) {
+    int R2 = -1;
+    for (int n2 = 0; n2 <= lim[1]; ++n2)
+      if (r1(n2, n3) >= 0) R2 = n2;
+    if (R2 < 0) return fail(PDEP_ERR_INVALID_ARG, "sphere not convex in n2");
+    s.slot[n3 + R3] = make_int2(R2, ncol);
+    for (int n2 = -R2; n2 <= R2; ++n2) {
+      if (r1(n2, n3) < 0) return fail(PDEP_ERR_INVALID_ARG, "sphere not convex");
+      colidx[{n2, n3}] = ncol++;
+    }
+  }
+  s.n_col = ncol;
+  // half space (n3 > 0 | n3 = 0, n2 > 0 | n3 = n2 = 0, n1 > 0) in (n3, n2, n1) order
+  s.g2.clear();
+  s.ucol.clear();
+  int nh = 0;
+  for (int n3 = 0; n3 <= R3; ++n3) {
+    const int R2 = s.slot[n3 + R3].x;
+    for (int n2 = (n3 == 0 ? 0 : -R2); n2 <= R2; ++n2) {
+      const int R1 = r1(n2, n3);
+      UCol u;
+      u.n2 = n2;
+      u.n3 = n3;
+      u.R1 = R1;
+      u.h0 = nh;
+      u.col = colidx[{n2, n3}];
+      u.mcol = colidx[{-n2, -n3}];
+      const int lo = (n3 == 0 && n2 == 0) ? 1 : -R1;
+      for (int n1 = lo; n1 <= R1; ++n1) {
+        double gx = two_pi * n1 / s.L[0], gy = two_pi * n2 / s.L[1], gz = two_pi * n3 / s.L[2];
+        s.g2.push_back(gx * gx + gy * gy + gz * gz);
+        ++nh;
+      }
+      s.ucol.push_back(u);
+    }
+  }
+  s.n_half = nh;
+  s.n_pw = 2 * nh + 1;
+  s.ld = ((s.n_pw + 31) / 32) * 32;
+  s.n_ucol = (int)s.ucol.size();
+  return PDEP_OK;
+}
+
+int upload_tables(pdep_ctx* c, SysData& s) {
+  RET(persistent(c, &s.d_ucol, s.ucol.size()));
+  RET(persistent(c, &s.d_slot, s.slot.size()));
+  RET(persistent(c, &s.d_g2, s.g2.size()));
+  CK(cudaMemcpy(s.d_ucol, s.ucol.data(), sizeof(UCol) * s.ucol.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(s.d_slot, s.slot.data(), sizeof(int2) * s.slot.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(s.d_g2, s.g2.data(), sizeof(double) * s.g2.size(), cudaMemcpyHostToDevice));
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int a = 0; a < 3; ++a) {
+    const int N = s.N[a];
+    std::vector<cpx<double>> td(N);
+    std::vector<cpx<float>> tf(N);
+    for (int j = 0; j < N; ++j) {
+      double ang = two_pi * j / N;
+      td[j] = mk(cos(ang), sin(ang));
+      tf[j] = mk((float)cos(ang), (float)sin(ang));
+    }
+    RET(persistent(c, &s.d_tw64[a], N));
+    RET(persistent(c, &s.d_tw32[a], N));
+    CK(cudaMemcpy(s.d_tw64[a], td.data(), sizeof(cpx<double>) * N, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(s.d_tw32[a], tf.data(), sizeof(cpx<float>) * N, cudaMemcpyHostToDevice));
+  }
+  auto fill = [&](auto& d, auto tw) {
+    d.N1 = s.N[0];
+    d.N2 = s.N[1];
+    d.N3 = s.N[2];
+    d.R3 = s.R3;
+    d.n_half = s.n_half;
+    d.n_pw = s.n_pw;
+    d.n_col = s.n_col;
+    d.n_ucol = s.n_ucol;
+    d.ucol = s.d_ucol;
+    d.slot = s.d_slot;
+    d.g2 = s.d_g2;
+    d.tw1 = tw[0];
+    d.tw2 = tw[1];
+    d.tw3 = tw[2];
+  };
+  fill(s.sd, s.d_tw64);
+  fill(s.sf, s.d_tw32);
+  return PDEP_OK;
+}
+
+// precision selectors
+inline const SphereDev<double>& sph(const SysData& s, double*) { return s.sd; }
+inline const SphereDev<float>& sph(const SysData& s, float*) { return s.sf; }
+inline const double* vgrid(const SysData& s, double*) { return s.d_v; }
+inline const float* vgrid(const SysData& s, float*) { return s.d_vf; }
+inline const double* psi_of(const SysData& s, double*) { return s.d_psi; }
+inline const float* psi_of(const SysData& s, float*) { return s.d_psif; }
+
+size_t b1_count(const SysData& s, int n_items) {
+  return (size_t)n_items * s.N[0] * s.n_col;
+}
+
+// Y = (H + shift_v) X for the vectors of 'map' (H = -nabla^2/2 + V); shift
+// indexed by vector % period (null: none).  Then, if with_pv, the occupied
+// space is shifted: Y += alpha Psi (Psi^T X) over all n columns.
+template <typename R>
+int apply_h(pdep_ctx* c, SysData& s, const R* X, R* Y, int n, const int* d_list, int n_list,
+            const double* shift, int period, bool with_pv, cudaStream_t st) {
+  ItemMap map{n, (n + 1) / 2};
+  int n_items = (n + 1) / 2;
+  if (d_list) {
+    map.list = d_list;
+    map.n_list = n_list;
+    n_items = (n_list + 1) / 2;
+  }
+  if (n_items > 0) {
+    cpx<R>* b1;
+    RET(ws(c, sizeof(R) == 8 ? "b1_64" : "b1_32", b1_count(s, n_items), &b1));
+    const SphereDev<R>& sd = sph(s, (R*)nullptr);
+    CK(launch_cols_fwd<R>(sd, X, s.ld, map, n_items, COEF_ONE, b1, st));
+    SlabArgs<R> a{};
+    a.mode = SLAB_HPSI;
+    a.b1 = b1;
+    a.n_items = n_items;
+    a.v = vgrid(s, (R*)nullptr);
+    a.map = map;
+    CK(launch_slab<R>(sd, a, st));
+    Epilogue<R> ep{};
+    ep.y = Y;
+    ep.ldy = s.ld;
+    ep.x_in = X;
+    ep.ldx = s.ld;
+    ep.shift = shift;
+    ep.shift_period = period > 0 ? period : 1;
+    ep.scale = 1.0 / s.n_r;
+    ep.kin = 1.0;
+    ep.beta = 0.0;
+    ep.coef = COEF_ONE;
+    CK(launch_cols_bwd<R>(sd, b1, map, n_items, ep, st));
+  }
+  if (with_pv) {
+    R* S;
+    RET(ws(c, sizeof(R) == 8 ? "pv_64" : "pv_32", (size_t)s.n_occ * n, &S));
+    const R* P = psi_of(s, (R*)nullptr);
+    CK(gemm<R>(true, s.n_occ, n, s.n_pw, 1.0, P, s.ld, X, s.ld, 0.0, S, s.n_occ, st));
+    CK(gemm<R>(false, s.n_pw, n, s.n_occ, s.alpha, P, s.ld, S, s.n_occ, 1.0, Y, s.ld, st));
+  }
+  return PDEP_OK;
+}
+
+// X <- X - Psi (Psi^T X)  (FP64, all n columns)
+int project_pc(pdep_ctx* c, SysData& s, double* X, int n, cudaStream_t st) {
+  double* S;
+  RET(ws(c, "pc_64", (size_t)s.n_occ * n, &S));
+  CK(gemm<double>(true, s.n_occ, n, s.n_pw, 1.0, s.d_psi, s.ld, X, s.ld, 0.0, S, s.n_occ, st));
+  CK(gemm<double>(false, s.n_pw, n, s.n_occ, -1.0, s.d_psi, s.ld, S, s.n_occ, 1.0, X, s.ld, st));
+  return PDEP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// small dense helpers on the device
+// ---------------------------------------------------------------------------
+int eigh_ws(pdep_ctx* c, int n, EighWork* wk) {
+  RET(ws(c, "eig_a", (size_t)n * n, &wk->a));
+  RET(ws(c, "eig_v", (size_t)n * n, &wk->v));
+  RET(ws(c, "eig_t", (size_t)n * n + n, &wk->tmp));
+  RET(ws(c, "eig_w", (size_t)n, &wk->w));
+  RET(ws(c, "eig_f", (size_t)4, &wk->flag));
+  return PDEP_OK;
+}
+
+// Orthonormalise the m columns of T (rows = n_pw, ld) against the nb columns of
+// B and among themselves (two passes of block Gram-Schmidt + symmetric
+// normalisation through the Gram matrix's eigendecomposition).  Columns that
+// are numerically dependent are dropped; the kept ones are written to OUT.
+// Returns the kept count in *kept.
+int orthonormalize(pdep_ctx* c, SysData& s, const double* B, int nb, double* T, int m, double* OUT,
+                   int* kept, cudaStream_t st) {
+  *kept = 0;
+  if (m <= 0) return PDEP_OK;
+  const int rows = s.n_pw;
+  double *S, *G, *Q, *d;
+  RET(ws(c, "on_s", (size_t)std::max(nb, 1) * m, &S));
+  RET(ws(c, "on_g", (size_t)m * m, &G));
+  RET(ws(c, "on_q", (size_t)m * m, &Q));
+  RET(ws(c, "on_d", (size_t)m, &d));
+  EighWork wk;
+  RET(eigh_ws(c, m, &wk));
+  int cur = m;
+  double* src = T;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int rep = 0; rep < 2 && nb > 0; ++rep) {
+      CK(gemm<double>(true, nb, cur, rows, 1.0, B, s.ld, src, s.ld, 0.0, S, nb, st));
+      CK(gemm<double>(false, rows, cur, nb, -1.0, B, s.ld, S, nb, 1.0, src, s.ld, st));
+    }
+    CK(gemm<double>(true, cur, cur, rows, 1.0, src, s.ld, src, s.ld, 0.0, G, cur, st));
+    CK(eigh(cur, G, cur, d, Q, cur, wk, st));
+    std::vector<double> hd(cur);
+    CK(cudaMemcpyAsync(hd.data(), d, sizeof(double) * cur, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const double dmax = hd[cur - 1];
+    if (!(dmax > 0) || !std::isfinite(dmax)) return PDEP_OK;
+    const double thr = 1e-12 * dmax;
+    int first = 0;
+    while (first < cur && !(hd[first] > thr)) ++first;
+    const int keep = cur - first;
+    CK(scale_by_isqrt_clamped(Q, cur, cur, d, thr, nullptr, st));
+    // OUT[:, 0:keep] = src * Q[:, first:cur]
+    CK(gemm<double>(false, rows, keep, cur, 1.0, src, s.ld, Q + (size_t)first * cur, cur, 0.0,
+                    OUT, s.ld, st));
+    cur = keep;
+    if (pass == 0 && cur > 0) {
+      // second pass works on OUT in place through T
+      CK(cudaMemcpy2DAsync(T, s.ld * sizeof(double), OUT, s.ld * sizeof(double),
+                           rows * sizeof(double), cur, cudaMemcpyDeviceToDevice, st));
+      src = T;
+    }
+    if (cur == 0) break;
+  }
+  *kept = cur;
+  return PDEP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// generic block Davidson for the lowest eigenpairs of a symmetric operator
+// ---------------------------------------------------------------------------
+struct DavidsonOut {
+  int iterations = 0;
+  int converged = 0;
+  double max_res = 0;
+};
+
+using OpFn = std::function<int(const double* X, double* Y, int m)>;
+using PrecFn = std::function<int(double* T, int m, const int* d_idx, const double* X)>;
+
+// Block Davidson (Davidson 1975, as used for Eq. chiisamatrixinpdep): the
+// nwant lowest Ritz pairs are carried; the first nconv must reach
+// ||A x - theta x|| <= tol (times |theta_1| when rel_tol).
+int davidson(pdep_ctx* c, SysData& s, int nwant, int nconv, int nb_max, const double* start,
+             int nstart, double tol, bool rel_tol, int max_iter, int zero_slot, OpFn op,
+             PrecFn prec, double* X /*[nwant][ld]*/, double* theta_host, DavidsonOut* out,
+             cudaStream_t st) {
+  const int rows = s.n_pw;
+  const long long ld = s.ld;
+  nb_max = std::max(nb_max, 2 * nwant);
+  double *B, *AB, *M, *Y, *th, *AX, *R, *T, *nr;
+  int* idx;
+  RET(ws(c, "dv_B", (size_t)nb_max * ld, &B));
+  RET(ws(c, "dv_AB", (size_t)nb_max * ld, &AB));
+  RET(ws(c, "dv_M", (size_t)nb_max * nb_max, &M));
+  RET(ws(c, "dv_Y", (size_t)nb_max * nb_max, &Y));
+  RET(ws(c, "dv_th", (size_t)nb_max, &th));
+  RET(ws(c, "dv_AX", (size_t)nwant * ld, &AX));
+  RET(ws(c, "dv_R", (size_t)nwant * ld, &R));
+  RET(ws(c, "dv_T", (size_t)nwant * ld, &T));
+  RET(ws(c, "dv_nr", (size_t)nwant, &nr));
+  RET(ws(c, "dv_idx", (size_t)nwant, &idx));
+  EighWork wk;
+  RET(eigh_ws(c, nb_max, &wk));
+
+  CK(cudaMemsetAsync(B, 0, sizeof(double) * (size_t)nb_max * ld, st));
+  CK(cudaMemsetAsync(AB, 0, sizeof(double) * (size_t)nb_max * ld, st));
+  CK(cudaMemcpy2DAsync(T, ld * sizeof(double), start, ld * sizeof(double), rows * sizeof(double),
+                       nstart, cudaMemcpyDeviceToDevice, st));
+  if (zero_slot >= 0) CK(zero_row(T, ld, zero_slot, nstart, st));
+  int nb = 0;
+  RET(orthonormalize(c, s, B, 0, T, nstart, B, &nb, st));
+  if (nb < nwant) return fail(PDEP_ERR_INVALID_ARG, "start block is rank deficient");
+  int lo = 0, hi = nb;
+  std::vector<double> hth(nb_max), hnr(nwant);
+  out->iterations = 0;
+  out->converged = 0;
+  for (int it = 0; it < max_iter; ++it) {
+    RET(op(B + (size_t)lo * ld, AB + (size_t)lo * ld, hi - lo));
+    out->iterations = it + 1;
+    // Rayleigh-Ritz in span(B)
+    CK(gemm<double>(true, nb, nb, rows, 1.0, B, ld, AB, ld, 0.0, M, nb, st));
+    CK(symmetrize<double>(M, nb, nb, st));
+    CK(eigh(nb, M, nb, th, Y, nb, wk, st));
+    CK(gemm<double>(false, rows, nwant, nb, 1.0, B, ld, Y, nb, 0.0, X, ld, st));
+    CK(gemm<double>(false, rows, nwant, nb, 1.0, AB, ld, Y, nb, 0.0, AX, ld, st));
+    CK(ritz_residual(AX, X, ld, rows, nwant, th, R, st));
+    CK(col_norms<double>(R, ld, rows, nwant, nr, st));
+    CK(cudaMemcpyAsync(hth.data(), th, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hnr.data(), nr, sizeof(double) * nwant, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const double scale = rel_tol ? std::max(std::fabs(hth[0]), 1e-300) : 1.0;
+    std::vector<int> unconv;
+    double mres = 0;
+    bool done = true;
+    for (int i = 0; i < nwant; ++i) {
+      const double r = hnr[i] / scale;
+      if (i < nconv) {
+        mres = std::max(mres, r);
+        if (!(r <= tol)) done = false;
+      }
+      if (!(r <= tol)) unconv.push_back(i);
+    }
+    out->max_res = mres;
+    for (int i = 0; i < nwant; ++i) theta_host[i] = hth[i];
+    if (done) {
+      out->converged = 1;
+      break;
+    }
+    if (it == max_iter - 1) break;
+    // corrections: residuals of the unconverged Ritz pairs
+    const int m = (int)unconv.size();
+    CK(cudaMemcpyAsync(idx, unconv.data(), sizeof(int) * m, cudaMemcpyHostToDevice, st));
+    CK(gather_cols(R, ld, T, ld, rows, idx, m, st));
+    if (prec) RET(prec(T, m, idx, X));
+    if (zero_slot >= 0) CK(zero_row(T, ld, zero_slot, m, st));
+    if (nb + m > nb_max) {
+      // restart from the Ritz vectors
+      CK(cudaMemcpy2DAsync(B, ld * sizeof(double), X, ld * sizeof(double), rows * sizeof(double),
+                           nwant, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpy2DAsync(AB, ld * sizeof(double), AX, ld * sizeof(double),
+                           rows * sizeof(double), nwant, cudaMemcpyDeviceToDevice, st));
+      nb = nwant;
+    }
+    int kept = 0;
+    RET(orthonormalize(c, s, B, nb, T, m, B + (size_t)nb * ld, &kept, st));
+    if (kept == 0) break;
+    lo = nb;
+    hi = nb + kept;
+    nb += kept;
+  }
+  return PDEP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// setup: lowest n_occ + 1 eigenpairs of H (FP64)
+// ---------------------------------------------------------------------------
+int setup_states(pdep_ctx* c, SysData& s, cudaStream_t st) {
+  const int nocc = s.n_occ;
+  const int ns = std::min(s.n_pw, nocc + std::max(4, nocc / 8));
+  if (nocc + 1 > s.n_pw) return fail(PDEP_ERR_INVALID_ARG, "n_occ too large for the basis");
+  // start vectors: plane waves of lowest kinetic energy plus small noise
+  std::vector<std::pair<double, int>> comps;
+  comps.push_back({0.0, 2 * s.n_half});
+  for (int k = 0; k < s.n_half; ++k) {
+    comps.push_back({s.g2[k] + 1e-12 * k, 2 * k});
+    comps.push_back({s.g2[k] + 1e-12 * k + 5e-13, 2 * k + 1});
+  }
+  std::sort(comps.begin(), comps.end());
+  std::vector<int> hc(ns);
+  for (int i = 0; i < ns; ++i) hc[i] = comps[i].second;
+  int* dcomp;
+  double *X0, *X, *ek;
+  RET(ws(c, "su_comp", ns, &dcomp));
+  RET(ws(c, "su_x0", (size_t)ns * s.ld, &X0));
+  RET(ws(c, "su_x", (size_t)ns * s.ld, &X));
+  RET(ws(c, "su_ek", (size_t)ns, &ek));
+  CK(cudaMemcpyAsync(dcomp, hc.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st));
+  CK(unit_start(X0, s.ld, s.n_pw, dcomp, ns, 1e-3, c->opt.seed ^ 0x5eed5eedULL, st));
+  OpFn op = [&](const double* in, double* outv, int m) -> int {
+    return apply_h<double>(c, s, in, outv, m, nullptr, 0, nullptr, 1, false, st);
+  };
+  double* xt;
+  RET(ws(c, "su_xt", (size_t)ns * s.ld, &xt));
+  // Teter-Payne-Allan preconditioner scaled by each Ritz vector's kinetic energy
+  PrecFn prec = [&](double* T, int m, const int* d_idx, const double* Xr) -> int {
+    CK(gather_cols(Xr, s.ld, xt, s.ld, s.n_pw, d_idx, m, st));
+    CK(kinetic_energy(xt, s.ld, s.n_half, m, s.d_g2, ek, st));
+    CK(precondition_tpa(T, s.ld, s.n_pw, s.n_half, m, s.d_g2, ek, st));
+    return (int)PDEP_OK;
+  };
+  std::vector<double> th(ns);
+  DavidsonOut dout;
+  const int nwant = nocc + 1;
+  RET(davidson(c, s, ns, nwant, 4 * ns, X0, ns, c->opt.setup_tol, false, c->opt.setup_max_iter,
+               -1, op, prec, X, th.data(), &dout, st));
+  if (!dout.converged)
+    return fail(PDEP_ERR_NOT_CONVERGED, "setup eigensolver did not converge");
+  s.eps.assign(th.begin(), th.begin() + nwant);
+  const double gap = s.eps[nocc] - s.eps[nocc - 1];
+  if (!(gap >= c->opt.gap_min)) return fail(PDEP_ERR_NO_GAP, "HOMO-LUMO gap below gap_min");
+  s.alpha = 2.0 * (s.eps[nocc] - s.eps[0]);
+  RET(persistent(c, &s.d_psi, (size_t)nocc * s.ld));
+  RET(persistent(c, &s.d_psif, (size_t)nocc * s.ld));
+  RET(persistent(c, &s.d_u, (size_t)nocc * s.n_r));
+  RET(persistent(c, &s.d_negeps, nocc));
+  RET(persistent(c, &s.d_ekin, nocc));
+  CK(cudaMemsetAsync(s.d_psi, 0, sizeof(double) * (size_t)nocc * s.ld, st));
+  CK(cudaMemcpy2DAsync(s.d_psi, s.ld * sizeof(double), X, s.ld * sizeof(double),
+                       s.n_pw * sizeof(double), nocc, cudaMemcpyDeviceToDevice, st));
+  CK((convert<float, double>(s.d_psif, s.ld, s.d_psi, s.ld, s.ld, nocc, st)));
+  std::vector<double> ne(nocc);
+  for (int v = 0; v < nocc; ++v) ne[v] = -s.eps[v];
+  CK(cudaMemcpyAsync(s.d_negeps, ne.data(), sizeof(double) * nocc, cudaMemcpyHostToDevice, st));
+  CK(kinetic_energy(s.d_psi, s.ld, s.n_half, nocc, s.d_g2, s.d_ekin, st));
+  // occupied states on the grid: u_v(r) = sum_G c_v(G) e^{iG.r}
+  {
+    ItemMap map{nocc, (nocc + 1) / 2};
+    const int n_items = (nocc + 1) / 2;
+    cpx<double>* b1;
+    RET(ws(c, "b1_64", b1_count(s, n_items), &b1));
+    CK(launch_cols_fwd<double>(s.sd, s.d_psi, s.ld, map, n_items, COEF_ONE, b1, st));
+    SlabArgs<double> a{};
+    a.mode = SLAB_TO_GRID;
+    a.b1 = b1;
+    a.n_items = n_items;
+    a.out = s.d_u;
+    a.out_stride = s.n_r;
+    a.out_scale = 1.0;
+    a.map = map;
+    CK(launch_slab<double>(s.sd, a, st));
+  }
+  RET(sync(st));
+  return PDEP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Sternheimer solves: (H - eps_v + alpha P_v) x = b with b in range(P_c)
+// (equivalent to Eq. stern: the occupied component of x vanishes)
+// ---------------------------------------------------------------------------
+template <typename R>
+int cg_loop(pdep_ctx* c, SysData& s, const R* b, R* x, int n, double tol, int max_iter,
+            CgScal* sc, cudaStream_t st, bool* hit_cap) {
+  R *r, *p, *ap;
+  int* list;
+  const char* tag = sizeof(R) == 8 ? "64" : "32";
+  std::string nr = std::string("cg_r") + tag, np = std::string("cg_p") + tag,
+              na = std::string("cg_ap") + tag;
+  RET(ws(c, nr.c_str(), (size_t)n * s.ld, &r));
+  RET(ws(c, np.c_str(), (size_t)n * s.ld, &p));
+  RET(ws(c, na.c_str(), (size_t)n * s.ld, &ap));
+  RET(ws(c, "cg_list", (size_t)n, &list));
+  CgArgs<R> a{};
+  a.x = x;
+  a.r = r;
+  a.p = p;
+  a.ap = ap;
+  a.ld = s.ld;
+  a.n_pw = s.n_pw;
+  a.n_half = s.n_half;
+  a.n_rhs = n;
+  a.g2 = s.d_g2;
+  a.ekin = s.d_ekin;
+  a.n_occ = s.n_occ;
+  a.sc = sc;
+  a.tol = tol;
+  a.status = c->d_status;
+  a.n_active = c->d_counter;
+  CK(cudaMemsetAsync(c->d_counter, 0, sizeof(int), st));
+  CK(cg_start<R>(a, b, s.ld, st));
+  *hit_cap = false;
+  for (int it = 0;; ++it) {
+    int n_act = 0;
+    RET(read_int(c, c->d_counter, &n_act, st));
+    if (n_act == 0) break;
+    if (it >= max_iter) {
+      *hit_cap = true;
+      break;
+    }
+    CK(active_list(sc, n, list, c->d_counter + 1, st));
+    RET(apply_h<R>(c, s, p, ap, n, list, n_act, s.d_negeps, s.n_occ, true, st));
+    CK(cudaMemsetAsync(c->d_counter, 0, sizeof(int), st));
+    CK(cg_step<R>(a, st));
+  }
+  return PDEP_OK;
+}
+
+int collect_cg_stats(pdep_ctx* c, const CgScal* sc, int n, int* iters_out, cudaStream_t st,
+                     std::vector<int>* its) {
+  std::vector<CgScal> h(n);
+  CK(cudaMemcpyAsync(h.data(), sc, sizeof(CgScal) * n, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  its->resize(n);
+  for (int i = 0; i < n; ++i) {
+    (*its)[i] = h[i].iters;
+    c->st_cg_iters += h[i].iters;
+    c->st_cg_max = std::max(c->st_cg_max, h[i].iters);
+  }
+  (void)iters_out;
+  return PDEP_OK;
+}
+
+// Solve for n right-hand sides b (FP64, [n][ld]); x out (FP64).  h_iters and
+// h_res (host, may be null) get per-RHS iteration counts and FP64 residuals.
+int solve_rhs(pdep_ctx* c, SysData& s, const double* b, double* x, int n, int* h_iters,
+              double* h_res, cudaStream_t st) {
+  const double tol = c->opt.cg_tol;
+  double *rel, *ap64;
+  RET(ws(c, "sv_rel", (size_t)n, &rel));
+  RET(ws(c, "sv_ap64", (size_t)n * s.ld, &ap64));
+  std::vector<int> its_total(n, 0);
+  bool capped = false;
+  int rounds = 0;
+  if (c->opt.precision == PDEP_FP64) {
+    CgScal* sc;
+    RET(ws(c, "cg_sc64", (size_t)n, &sc));
+    RET(cg_loop<double>(c, s, b, x, n, tol, c->opt.cg_max_iter, sc, st, &capped));
+    std::vector<int> its;
+    RET(collect_cg_stats(c, sc, n, nullptr, st, &its));
+    for (int i = 0; i < n; ++i) its_total[i] = its[i];
+    rounds = 1;
+  } else {
+    // mixed: FP32 inner CG on the scaled residual, FP64 residual refinement
+    float *r32, *d32;
+    double* rn;
+    CgScal* sc;
+    int* list;
+    RET(ws(c, "mx_r32", (size_t)n * s.ld, &r32));
+    RET(ws(c, "mx_d32", (size_t)n * s.ld, &d32));
+    RET(ws(c, "mx_rn", (size_t)n, &rn));
+    RET(ws(c, "cg_sc32", (size_t)n, &sc));
+    RET(ws(c, "mx_list", (size_t)n, &list));
+    CK(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)n * s.ld, st));
+    // r64 = b initially (x = 0): ap64 holds the residual
+    CK(cudaMemcpyAsync(ap64, b, sizeof(double) * (size_t)n * s.ld, cudaMemcpyDeviceToDevice, st));
+    {
+      std::vector<double> ones(n, 1.0);
+      CK(cudaMemcpyAsync(rel, ones.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
+      RET(sync(st));
+    }
+    for (int round = 0; round < c->opt.max_refine; ++round) {
+      CK(unconverged_list(rel, tol, n, list, c->d_counter + 1, st));
+      int n_un = 0;
+      RET(read_int(c, c->d_counter + 1, &n_un, st));
+      if (n_un == 0) break;
+      rounds = round + 1;
+      CK(refine_prepare(ap64, s.ld, s.n_pw, n, rel, tol, r32, s.ld, rn, st));
+      bool cap = false;
+      RET(cg_loop<float>(c, s, r32, d32, n, c->opt.inner_tol, c->opt.inner_max_iter, sc, st, &cap));
+      std::vector<int> its;
+      RET(collect_cg_stats(c, sc, n, nullptr, st, &its));
+      for (int i = 0; i < n; ++i) its_total[i] += its[i];
+      CK(refine_accumulate(x, s.ld, d32, s.ld, s.n_pw, n, rn, st));
+      // FP64 residual of the active RHS: ap64 = b - A x
+      RET(apply_h<double>(c, s, x, ap64, n, list, n_un, s.d_negeps, s.n_occ, true, st));
+      CK(residual_norms(b, s.ld, ap64, s.ld, s.n_pw, n_un, rel, list, st));
+    }
+    {
+      CK(unconverged_list(rel, tol, n, list, c->d_counter + 1, st));
+      int n_un = 0;
+      RET(read_int(c, c->d_counter + 1, &n_un, st));
+      capped = n_un > 0;
+    }
+  }
+  c->st_refine_max = std::max(c->st_refine_max, rounds);
+  // remove any occupied component left by rounding, then the FP64 residual
+  RET(project_pc(c, s, x, n, st));
+  RET(apply_h<double>(c, s, x, ap64, n, nullptr, 0, s.d_negeps, s.n_occ, true, st));
+  CK(residual_norms(b, s.ld, ap64, s.ld, s.n_pw, n, rel, nullptr, st));
+  std::vector<double> hr(n);
+  CK(cudaMemcpyAsync(hr.data(), rel, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+  RET(sync(st));
+  for (int i = 0; i < n; ++i) {
+    c->st_max_res = std::max(c->st_max_res, hr[i]);
+    if (h_res) h_res[i] = hr[i];
+    if (h_iters) h_iters[i] = its_total[i];
+  }
+  c->st_solves += n;
+  RET(check_status(c, st));
+  if (capped) return fail(PDEP_ERR_NOT_CONVERGED, "Sternheimer CG reached its iteration cap");
+  return PDEP_OK;
+}
+
+// b_vj = -P_c [dV_j psi_v] for perturbation grids dv [m][n_r]  -> bvec [m*n_occ][ld]
+int build_rhs(pdep_ctx* c, SysData& s, const double* dv, int m, double* bvec, cudaStream_t st) {
+  const int nocc = s.n_occ;
+  ItemMap map{nocc, (nocc + 1) / 2};
+  const int n_items = m * ((nocc + 1) / 2);
+  cpx<double>* b1;
+  RET(ws(c, "b1_64", b1_count(s, n_items), &b1));
+  SlabArgs<double> a{};
+  a.mode = SLAB_FROM_GRID;
+  a.b1 = b1;
+  a.n_items = n_items;
+  a.src.f = dv;
+  a.src.f_stride = s.n_r;
+  a.src.g = s.d_u;
+  a.src.g_stride = s.n_r;
+  a.map = map;
+  CK(launch_slab<double>(s.sd, a, st));
+  Epilogue<double> ep{};
+  ep.y = bvec;
+  ep.ldy = s.ld;
+  ep.shift_period = 1;
+  ep.scale = -1.0 / s.n_r;
+  ep.coef = COEF_ONE;
+  CK(launch_cols_bwd<double>(s.sd, b1, map, n_items, ep, st));
+  RET(project_pc(c, s, bvec, m * nocc, st));
+  return PDEP_OK;
+}
+
+// dn_j(r) = (4/Omega) sum_v u_v(r) du_vj(r) for x [m*n_occ][ld]  (Eq. deltani)
+int density(pdep_ctx* c, SysData& s, const double* x, int m, double* dn, cudaStream_t st) {
+  const int nocc = s.n_occ;
+  ItemMap map{nocc, (nocc + 1) / 2};
+  const int n_items = m * ((nocc + 1) / 2);
+  cpx<double>* b1;
+  RET(ws(c, "b1_64", b1_count(s, n_items), &b1));
+  CK(launch_cols_fwd<double>(s.sd, x, s.ld, map, n_items, COEF_ONE, b1, st));
+  SlabArgs<double> a{};
+  a.mode = SLAB_DENSITY;
+  a.b1 = b1;
+  a.n_items = n_items;
+  a.out = dn;
+  a.out_stride = s.n_r;
+  a.out_scale = 4.0 / s.omega;
+  a.src.g = s.d_u;
+  a.src.g_stride = s.n_r;
+  a.map = map;
+  CK(launch_slab<double>(s.sd, a, st));
+  return PDEP_OK;
+}
+
+// chi0bar phi for m PDEP vectors (internal layout [m][ld], G=0 slot zero)
+int chi0_internal(pdep_ctx* c, SysData& s, const double* phi, int m, double* out, double* dn_out,
+                  cudaStream_t st) {
+  const int nocc = s.n_occ;
+  // perturbation chunk: keep roughly 10 vectors of n_rhs*ld doubles bounded
+  size_t per = (size_t)nocc * s.ld * sizeof(double) * 9 + b1_count(s, (nocc + 1) / 2) * 16 +
+               (size_t)s.n_r * 16;
+  size_t budget = (size_t)24 << 30;
+  if (c->opt.workspace_limit_bytes) budget = c->opt.workspace_limit_bytes / 2;
+  int mc_max = (int)std::max<size_t>(1, budget / per);
+  for (int j0 = 0; j0 < m; j0 += mc_max) {
+    const int mc = std::min(mc_max, m - j0);
+    double *dv, *bvec, *xvec, *dn;
+    RET(ws(c, "c0_dv", (size_t)mc * s.n_r, &dv));
+    RET(ws(c, "c0_b", (size_t)mc * nocc * s.ld, &bvec));
+    RET(ws(c, "c0_x", (size_t)mc * nocc * s.ld, &xvec));
+    if (dn_out)
+      dn = dn_out + (size_t)j0 * s.n_r;
+    else
+      RET(ws(c, "c0_dn", (size_t)mc * s.n_r, &dn));
+    // dV_j(r) = Omega^{-1/2} sum_G sqrt(4pi)/|G| phi_j(G) e^{iG.r}
+    {
+      ItemMap map{mc, (mc + 1) / 2};
+      const int n_items = (mc + 1) / 2;
+      cpx<double>* b1;
+      RET(ws(c, "b1_64", b1_count(s, n_items), &b1));
+      CK(launch_cols_fwd<double>(s.sd, phi + (size_t)j0 * s.ld, s.ld, map, n_items,
+                                 COEF_SQRT_COULOMB, b1, st));
+      SlabArgs<double> a{};
+      a.mode = SLAB_TO_GRID;
+      a.b1 = b1;
+      a.n_items = n_items;
+      a.out = dv;
+      a.out_stride = s.n_r;
+      a.out_scale = 1.0 / std::sqrt(s.omega);
+      a.map = map;
+      CK(launch_slab<double>(s.sd, a, st));
+    }
+    RET(build_rhs(c, s, dv, mc, bvec, st));
+    int r = solve_rhs(c, s, bvec, xvec, mc * nocc, nullptr, nullptr, st);
+    if (r != PDEP_OK && r != PDEP_ERR_NOT_CONVERGED) return r;
+    RET(density(c, s, xvec, mc, dn, st));
+    // (chi0bar phi_j)(G) = sqrt(4pi)/|G| * Omega^{1/2}/N_r * FFT[dn_j](G)
+    {
+      ItemMap map{mc, (mc + 1) / 2};
+      const int n_items = (mc + 1) / 2;
+      cpx<double>* b1;
+      RET(ws(c, "b1_64", b1_count(s, n_items), &b1));
+      SlabArgs<double> a{};
+      a.mode = SLAB_FROM_GRID;
+      a.b1 = b1;
+      a.n_items = n_items;
+      a.src.g = dn;
+      a.src.g_stride = s.n_r;
+      a.map = map;
+      CK(launch_slab<double>(s.sd, a, st));
+      Epilogue<double> ep{};
+      ep.y = out + (size_t)j0 * s.ld;
+      ep.ldy = s.ld;
+      ep.shift_period = 1;
+      ep.scale = std::sqrt(s.omega) / s.n_r;
+      ep.coef = COEF_SQRT_COULOMB;
+      CK(launch_cols_bwd<double>(s.sd, b1, map, n_items, ep, st));
+    }
+    if (r == PDEP_ERR_NOT_CONVERGED) return r;
+  }
+  return PDEP_OK;
+}
+
+int check_sys(const pdep_ctx* c, int sys) {
+  if (!c) return fail(PDEP_ERR_INVALID_ARG, "null context");
+  if (sys < 0 || sys >= (int)c->sys.size()) return fail(PDEP_ERR_INVALID_ARG, "bad system index");
+  return PDEP_OK;
+}
+
+void reset_stats(pdep_ctx* c) {
+  c->st_solves = 0;
+  c->st_cg_iters = 0;
+  c->st_cg_max = 0;
+  c->st_refine_max = 0;
+  c->st_max_res = 0;
+}
+
+int solve_one(pdep_ctx* c, int si, const double* phi0, double* eigvals, double* eigvecs,
+              pdep_stats* stats, cudaStream_t st) {
+  SysData& s = c->sys[si];
+  const int np = s.n_pdep;
+  const int dim = s.n_pw - 1;
+  if (np > dim) return fail(PDEP_ERR_INVALID_ARG, "n_pdep exceeds the PDEP dimension");
+  double *start, *X;
+  RET(ws(c, "pd_start", (size_t)np * s.ld, &start));
+  RET(ws(c, "pd_X", (size_t)np * s.ld, &X));
+  CK(cudaMemsetAsync(start, 0, sizeof(double) * (size_t)np * s.ld, st));
+  if (phi0) {
+    CK(cudaMemcpy2DAsync(start, s.ld * sizeof(double), phi0, dim * sizeof(double),
+                         dim * sizeof(double), np, kind_to_dev(phi0), st));
+  } else {
+    CK(philox_normal(start, s.ld, dim, np, c->opt.seed, 0ULL, st));
+  }
+  int app_status = PDEP_OK;
+  OpFn op = [&](const double* in, double* outv, int m) -> int {
+    int r = chi0_internal(c, s, in, m, outv, nullptr, st);
+    if (r == PDEP_ERR_NOT_CONVERGED) {
+      app_status = r;
+      return (int)PDEP_OK;
+    }
+    return r;
+  };
+  std::vector<double> th(np);
+  DavidsonOut dout;
+  const bool fixed = !(c->opt.dav_tol > 0);
+  RET(davidson(c, s, np, np, std::max(2, c->opt.dav_subspace_factor) * np, start, np,
+               fixed ? 0.0 : c->opt.dav_tol, true, c->opt.dav_max_iter, s.n_pw - 1, op, nullptr,
+               X, th.data(), &dout, st));
+  RET(copy_from_host(eigvals, th.data(), sizeof(double) * np, st));
+  if (eigvecs)
+    CK(cudaMemcpy2DAsync(eigvecs, dim * sizeof(double), X, s.ld * sizeof(double),
+                         dim * sizeof(double), np, kind_from_dev(eigvecs), st));
+  RET(sync(st));
+  if (stats) {
+    stats->dav_iterations += dout.iterations;
+    if (!fixed && !dout.converged) stats->converged = 0;
+    stats->max_dav_residual = std::max(stats->max_dav_residual, dout.max_res);
+  }
+  if (!fixed && !dout.converged) return fail(PDEP_ERR_NOT_CONVERGED, "Davidson did not converge");
+  return app_status;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void pdep_default_options(pdep_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->precision = PDEP_FP64;
+  o->cg_tol = 1e-10;
+  o->cg_max_iter = 2000;
+  o->inner_tol = 1e-5;
+  o->inner_max_iter = 1000;
+  o->max_refine = 6;
+  o->dav_tol = 1e-8;
+  o->dav_max_iter = 30;
+  o->dav_subspace_factor = 4;
+  o->seed = 1501031410ULL;
+  o->gap_min = 1e-3;
+  o->setup_tol = 1e-11;
+  o->setup_max_iter = 400;
+  o->workspace_limit_bytes = 0;
+}
+
+const char* pdep_status_string(int s) {
+  switch (s) {
+    case PDEP_OK: return "ok";
+    case PDEP_ERR_INVALID_ARG: return "invalid argument";
+    case PDEP_ERR_CUDA: return "CUDA error";
+    case PDEP_ERR_OOM: return "out of device memory";
+    case PDEP_ERR_NO_GAP: return "no gap at the Fermi level";
+    case PDEP_ERR_NOT_CONVERGED: return "not converged";
+    case PDEP_ERR_NONFINITE: return "non-finite value";
+    case PDEP_ERR_TIMEOUT: return "timeout";
+    case PDEP_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char* pdep_last_error(void) { return g_last_error.c_str(); }
+
+void pdep_destroy(pdep_ctx* c) {
+  if (!c) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  for (auto& kv : c->bufs)
+    if (kv.second.p) cudaFree(kv.second.p);
+  for (void* p : c->owned) cudaFree(p);
+  if (c->d_status) cudaFree(c->d_status);
+  if (c->d_counter) cudaFree(c->d_counter);
+  if (c->h_pin) cudaFreeHost(c->h_pin);
+  cudaSetDevice(cur);
+  delete c;
+}
+
+int pdep_setup(const pdep_system_desc* sys, int n_sys, const pdep_options* opt, void* stream,
+               pdep_ctx** out) {
+  if (!out) return fail(PDEP_ERR_INVALID_ARG, "null output pointer");
+  *out = nullptr;
+  if (!sys || n_sys <= 0) return fail(PDEP_ERR_INVALID_ARG, "no systems");
+  cudaStream_t st = (cudaStream_t)stream;
+  pdep_ctx* c = new pdep_ctx();
+  if (opt)
+    c->opt = *opt;
+  else
+    pdep_default_options(&c->opt);
+  auto bail = [&](int r) {
+    pdep_destroy(c);
+    return r;
+  };
+  if (cudaGetDevice(&c->device) != cudaSuccess) return bail(fail(PDEP_ERR_CUDA, "no CUDA device"));
+  if (upload_local_twiddles() != cudaSuccess) return bail(fail(PDEP_ERR_CUDA, "twiddle upload"));
+  if (cudaMalloc(&c->d_status, sizeof(unsigned)) != cudaSuccess ||
+      cudaMalloc(&c->d_counter, 4 * sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&c->h_pin, 16 * sizeof(int)) != cudaSuccess)
+    return bail(fail(PDEP_ERR_OOM, "context allocation"));
+  cudaMemset(c->d_status, 0, sizeof(unsigned));
+  c->sys.resize(n_sys);
+  for (int i = 0; i < n_sys; ++i) {
+    const pdep_system_desc& d = sys[i];
+    SysData& s = c->sys[i];
+    for (int a = 0; a < 3; ++a) {
+      s.N[a] = d.grid[a];
+      s.L[a] = d.cell[a];
+    }
+    s.n_occ = d.n_occ;
+    s.n_pdep = d.n_pdep;
+    if (!d.v_r || d.n_occ < 1 || d.n_pdep < 1)
+      return bail(fail(PDEP_ERR_INVALID_ARG, "bad system descriptor"));
+    if (!grid_supported(s.N[0], s.N[1], s.N[2]))
+      return bail(fail(PDEP_ERR_INVALID_ARG, "unsupported grid shape"));
+    int r = build_sphere(s, d.ecut);
+    if (r != PDEP_OK) return bail(r);
+    if (s.n_pdep > s.n_pw - 1) return bail(fail(PDEP_ERR_INVALID_ARG, "n_pdep too large"));
+    const size_t smem = slab_smem_bytes(s.n_col, s.R3, s.N[1], sizeof(double));
+    if (smem > 200 * 1024) return bail(fail(PDEP_ERR_UNSUPPORTED, "slab does not fit shared memory"));
+    r = upload_tables(c, s);
+    if (r != PDEP_OK) return bail(r);
+    if ((r = persistent(c, &s.d_v, s.n_r)) != PDEP_OK) return bail(r);
+    if ((r = persistent(c, &s.d_vf, s.n_r)) != PDEP_OK) return bail(r);
+    if (cudaMemcpyAsync(s.d_v, d.v_r, sizeof(double) * s.n_r, kind_to_dev(d.v_r), st) != cudaSuccess)
+      return bail(fail(PDEP_ERR_CUDA, "potential upload"));
+    if (convert<float, double>(s.d_vf, s.n_r, s.d_v, s.n_r, s.n_r, 1, st) != cudaSuccess)
+      return bail(fail(PDEP_ERR_CUDA, "potential conversion"));
+    // the potential must be finite
+    std::vector<double> hv(s.n_r);
+    if (cudaMemcpyAsync(hv.data(), s.d_v, sizeof(double) * s.n_r, cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return bail(fail(PDEP_ERR_CUDA, "potential check"));
+    for (double v : hv)
+      if (!std::isfinite(v)) return bail(fail(PDEP_ERR_NONFINITE, "non-finite potential"));
+    r = setup_states(c, s, st);
+    if (r != PDEP_OK) return bail(r);
+  }
+  *out = c;
+  return PDEP_OK;
+}
+
+int pdep_get_sizes(const pdep_ctx* c, int sys, int* n_pw, int* n_r, int* n_pdep_dim) {
+  RET(check_sys(c, sys));
+  const SysData& s = c->sys[sys];
+  if (n_pw) *n_pw = s.n_pw;
+  if (n_r) *n_r = s.n_r;
+  if (n_pdep_dim) *n_pdep_dim = s.n_pw - 1;
+  return PDEP_OK;
+}
+
+int pdep_get_occupied(pdep_ctx* c, int sys, double* psi, double* eps, void* stream) {
+  RET(check_sys(c, sys));
+  cudaStream_t st = (cudaStream_t)stream;
+  SysData& s = c->sys[sys];
+  if (psi)
+    CK(cudaMemcpy2DAsync(psi, s.n_pw * sizeof(double), s.d_psi, s.ld * sizeof(double),
+                         s.n_pw * sizeof(double), s.n_occ, kind_from_dev(psi), st));
+  RET(sync(st));
+  if (eps) RET(copy_from_host(eps, s.eps.data(), sizeof(double) * (s.n_occ + 1), st));
+  return PDEP_OK;
+}
+
+int chi0_apply(pdep_ctx* c, int sys, const double* phi, int n_pert, double* chi0_phi, double* dn_r,
+               void* stream) {
+  RET(check_sys(c, sys));
+  if (n_pert < 0 || (n_pert > 0 && (!phi || !chi0_phi)))
+    return fail(PDEP_ERR_INVALID_ARG, "bad chi0_apply arguments");
+  if (n_pert == 0) return PDEP_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  SysData& s = c->sys[sys];
+  reset_stats(c);
+  const int dim = s.n_pw - 1;
+  double *in, *outv, *dn = nullptr;
+  RET(ws(c, "api_in", (size_t)n_pert * s.ld, &in));
+  RET(ws(c, "api_out", (size_t)n_pert * s.ld, &outv));
+  CK(cudaMemsetAsync(in, 0, sizeof(double) * (size_t)n_pert * s.ld, st));
+  CK(cudaMemcpy2DAsync(in, s.ld * sizeof(double), phi, dim * sizeof(double), dim * sizeof(double),
+                       n_pert, kind_to_dev(phi), st));
+  const bool dn_dev = dn_r && is_device_ptr(dn_r);
+  if (dn_r) {
+    if (dn_dev)
+      dn = dn_r;
+    else
+      RET(ws(c, "api_dn", (size_t)n_pert * s.n_r, &dn));
+  }
+  int r = chi0_internal(c, s, in, n_pert, outv, dn, st);
+  if (r != PDEP_OK && r != PDEP_ERR_NOT_CONVERGED) return r;
+  CK(cudaMemcpy2DAsync(chi0_phi, dim * sizeof(double), outv, s.ld * sizeof(double),
+                       dim * sizeof(double), n_pert, kind_from_dev(chi0_phi), st));
+  if (dn_r && !dn_dev)
+    CK(cudaMemcpyAsync(dn_r, dn, sizeof(double) * (size_t)n_pert * s.n_r, cudaMemcpyDeviceToHost,
+                       st));
+  RET(sync(st));
+  return r;
+}
+
+int sternheimer_solve(pdep_ctx* c, int sys, const double* dv_r, int n_pert, double* dpsi,
+                      int* iters, double* resid, void* stream) {
+  RET(check_sys(c, sys));
+  if (n_pert < 0 || (n_pert > 0 && (!dv_r || !dpsi)))
+    return fail(PDEP_ERR_INVALID_ARG, "bad sternheimer_solve arguments");
+  if (n_pert == 0) return PDEP_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  SysData& s = c->sys[sys];
+  reset_stats(c);
+  const int n = n_pert * s.n_occ;
+  double *dv, *bvec, *xvec;
+  RET(ws(c, "st_dv", (size_t)n_pert * s.n_r, &dv));
+  RET(ws(c, "st_b", (size_t)n * s.ld, &bvec));
+  RET(ws(c, "st_x", (size_t)n * s.ld, &xvec));
+  CK(cudaMemcpyAsync(dv, dv_r, sizeof(double) * (size_t)n_pert * s.n_r, kind_to_dev(dv_r), st));
+  RET(build_rhs(c, s, dv, n_pert, bvec, st));
+  std::vector<int> hi(n);
+  std::vector<double> hr(n);
+  int r = solve_rhs(c, s, bvec, xvec, n, hi.data(), hr.data(), st);
+  if (r != PDEP_OK && r != PDEP_ERR_NOT_CONVERGED) return r;
+  CK(cudaMemcpy2DAsync(dpsi, s.n_pw * sizeof(double), xvec, s.ld * sizeof(double),
+                       s.n_pw * sizeof(double), n, kind_from_dev(dpsi), st));
+  RET(sync(st));
+  if (iters) RET(copy_from_host(iters, hi.data(), sizeof(int) * n, st));
+  if (resid) RET(copy_from_host(resid, hr.data(), sizeof(double) * n, st));
+  return r;
+}
+
+int pdep_apply_hamiltonian(pdep_ctx* c, int sys, const double* x, int n, double* y,
+                           int precision, void* stream) {
+  RET(check_sys(c, sys));
+  if (n < 0 || (n > 0 && (!x || !y))) return fail(PDEP_ERR_INVALID_ARG, "bad arguments");
+  if (n == 0) return PDEP_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  SysData& s = c->sys[sys];
+  double *in, *outv;
+  RET(ws(c, "api_in", (size_t)n * s.ld, &in));
+  RET(ws(c, "api_out", (size_t)n * s.ld, &outv));
+  CK(cudaMemsetAsync(in, 0, sizeof(double) * (size_t)n * s.ld, st));
+  CK(cudaMemcpy2DAsync(in, s.ld * sizeof(double), x, s.n_pw * sizeof(double),
+                       s.n_pw * sizeof(double), n, kind_to_dev(x), st));
+  if (precision == PDEP_FP64) {
+    RET(apply_h<double>(c, s, in, outv, n, nullptr, 0, nullptr, 1, false, st));
+  } else {
+    float *in32, *out32;
+    RET(ws(c, "api_in32", (size_t)n * s.ld, &in32));
+    RET(ws(c, "api_out32", (size_t)n * s.ld, &out32));
+    CK((convert<float, double>(in32, s.ld, in, s.ld, s.ld, n, st)));
+    RET(apply_h<float>(c, s, in32, out32, n, nullptr, 0, nullptr, 1, false, st));
+    CK((convert<double, float>(outv, s.ld, out32, s.ld, s.n_pw, n, st)));
+  }
+  CK(cudaMemcpy2DAsync(y, s.n_pw * sizeof(double), outv, s.ld * sizeof(double),
+                       s.n_pw * sizeof(double), n, kind_from_dev(y), st));
+  return sync(st);
+}
+
+int pdep_to_grid(pdep_ctx* c, int sys, const double* x, int n, double* u, void* stream) {
+  RET(check_sys(c, sys));
+  if (n < 0 || (n > 0 && (!x || !u))) return fail(PDEP_ERR_INVALID_ARG, "bad arguments");
+  if (n == 0) return PDEP_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  SysData& s = c->sys[sys];
+  double *in, *grid;
+  RET(ws(c, "api_in", (size_t)n * s.ld, &in));
+  RET(ws(c, "api_grid", (size_t)n * s.n_r, &grid));
+  CK(cudaMemsetAsync(in, 0, sizeof(double) * (size_t)n * s.ld, st));
+  CK(cudaMemcpy2DAsync(in, s.ld * sizeof(double), x, s.n_pw * sizeof(double),
+                       s.n_pw * sizeof(double), n, kind_to_dev(x), st));
+  ItemMap map{n, (n + 1) / 2};
+  const int n_items = (n + 1) / 2;
+  cpx<double>* b1;
+  RET(ws(c, "b1_64", b1_count(s, n_items), &b1));
+  CK(launch_cols_fwd<double>(s.sd, in, s.ld, map, n_items, COEF_ONE, b1, st));
+  SlabArgs<double> a{};
+  a.mode = SLAB_TO_GRID;
+  a.b1 = b1;
+  a.n_items = n_items;
+  a.out = grid;
+  a.out_stride = s.n_r;
+  a.out_scale = 1.0;
+  a.map = map;
+  CK(launch_slab<double>(s.sd, a, st));
+  CK(cudaMemcpyAsync(u, grid, sizeof(double) * (size_t)n * s.n_r, kind_from_dev(u), st));
+  return sync(st);
+}
+
+int pdep_solve(pdep_ctx* c, int sys, const double* phi0, double* eigvals, double* eigvecs,
+               pdep_stats* stats, void* stream) {
+  if (!c) return fail(PDEP_ERR_INVALID_ARG, "null context");
+  if (!eigvals) return fail(PDEP_ERR_INVALID_ARG, "null eigvals");
+  if (sys != -1) RET(check_sys(c, sys));
+  cudaStream_t st = (cudaStream_t)stream;
+  auto t0 = std::chrono::steady_clock::now();
+  reset_stats(c);
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->converged = 1;
+  }
+  int result = PDEP_OK;
+  const int lo = sys == -1 ? 0 : sys, hi = sys == -1 ? (int)c->sys.size() : sys + 1;
+  size_t off_val = 0, off_vec = 0;
+  for (int i = lo; i < hi; ++i) {
+    SysData& s = c->sys[i];
+    const double* p0 = phi0 ? phi0 + off_vec : nullptr;
+    int r = solve_one(c, i, p0, eigvals + off_val, eigvecs ? eigvecs + off_vec : nullptr, stats, st);
+    if (r != PDEP_OK && r != PDEP_ERR_NOT_CONVERGED) return r;
+    if (r != PDEP_OK) result = r;
+    off_val += s.n_pdep;
+    off_vec += (size_t)s.n_pdep * (s.n_pw - 1);
+  }
+  if (stats) {
+    stats->sternheimer_solves = c->st_solves;
+    stats->cg_iterations = c->st_cg_iters;
+    stats->cg_iterations_max = c->st_cg_max;
+    stats->refine_rounds_max = c->st_refine_max;
+    stats->max_cg_residual = c->st_max_res;
+    stats->seconds =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return result;
+}
+
+}  // extern "C"

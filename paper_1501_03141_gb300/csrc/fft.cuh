@@ -1,0 +1,233 @@
+// Register-resident line FFTs for the plane-wave sphere <-> grid transforms.
+//
+// A line of length N = TPL * M is held by TPL consecutive lanes of a warp
+// (a "group", aligned to TPL).  Two data distributions are used:
+//   A: lane t holds element n = t + TPL*i in register i      (i = 0..M-1)
+//   B: lane t holds element k = i + M*rev(t) in register i   (rev = bit reversal
+//      over log2(TPL) bits)
+// fft_a2b computes an M-point DFT in registers, multiplies by the twiddles
+// w_N^{S t k2} and finishes with a TPL-point DFT across the group using
+// radix-2 decimation-in-frequency butterflies on warp shuffles.  fft_b2a is
+// the transposed network (DIT shuffles, twiddles, local DFT); because the
+// DFT matrix is symmetric it computes the same transform from B to A.  A
+// sphere->grid pass therefore runs A->B and the grid->sphere pass B->A with
+// no data exchange in between.
+//
+// Sign convention: S = +1 is sum_n x_n exp(+2 pi i n k / N) (sphere -> grid,
+// unnormalised), S = -1 the forward transform (grid -> sphere).
+#pragma once
+
+#include "common.cuh"
+
+namespace pdep {
+
+// ---------------------------------------------------------------------------
+// twiddles of the in-register DFTs (compile-time indices -> constant bank)
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int local_tw_offset(int M) {
+  return M == 6 ? 0 : M == 8 ? 6 : M == 10 ? 14 : M == 12 ? 24 : M == 16 ? 36
+       : M == 20 ? 52 : M == 24 ? 72 : M == 32 ? 96 : M == 48 ? 128 : M == 64 ? 176 : -1;
+}
+constexpr int LOCAL_TW_SIZE = 240;
+
+// defined here: fft.cuh is included by a single translation unit (no -rdc)
+__constant__ double2 c_local_tw_d[LOCAL_TW_SIZE];
+__constant__ float2 c_local_tw_f[LOCAL_TW_SIZE];
+
+template <typename R>
+struct LocalTw;
+template <>
+struct LocalTw<double> {
+  static __device__ __forceinline__ cpx<double> get(int i) {
+    double2 v = c_local_tw_d[i];
+    return mk(v.x, v.y);
+  }
+};
+template <>
+struct LocalTw<float> {
+  static __device__ __forceinline__ cpx<float> get(int i) {
+    float2 v = c_local_tw_f[i];
+    return mk(v.x, v.y);
+  }
+};
+
+// exp(S * 2 pi i j / M) for the local DFT of size M
+template <typename R, int S, int M>
+__device__ __forceinline__ cpx<R> local_w(int j) {
+  cpx<R> w = LocalTw<R>::get(local_tw_offset(M) + j);
+  return S > 0 ? w : conj(w);
+}
+
+__host__ __device__ constexpr int pick_radix(int M) {
+  return (M % 4 == 0 && M != 4) ? 4 : (M % 2 == 0 && M != 2) ? 2 : (M % 3 == 0 && M != 3) ? 3 : 5;
+}
+
+// In-place DFT of compile-time size M over a register array:
+//   a[k] <- sum_n a[n] exp(S 2 pi i n k / M)
+template <typename R, int M, int S>
+struct DFT {
+  static constexpr int P = pick_radix(M);
+  static constexpr int Q = M / P;
+  static __device__ __forceinline__ void run(cpx<R>* a) {
+    // n = p + P q,  k = k1 + Q k2
+    cpx<R> y[P][Q];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+#pragma unroll
+      for (int q = 0; q < Q; ++q) y[p][q] = a[p + P * q];
+      DFT<R, Q, S>::run(y[p]);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < Q; ++k1) {
+      cpx<R> z[P];
+#pragma unroll
+      for (int p = 0; p < P; ++p)
+        z[p] = (p * k1 == 0) ? y[p][k1] : y[p][k1] * local_w<R, S, M>((p * k1) % M);
+      DFT<R, P, S>::run(z);
+#pragma unroll
+      for (int k2 = 0; k2 < P; ++k2) a[k1 + Q * k2] = z[k2];
+    }
+  }
+};
+
+template <typename R, int S>
+struct DFT<R, 1, S> {
+  static __device__ __forceinline__ void run(cpx<R>*) {}
+};
+
+template <typename R, int S>
+struct DFT<R, 2, S> {
+  static __device__ __forceinline__ void run(cpx<R>* a) {
+    cpx<R> t = a[0];
+    a[0] = t + a[1];
+    a[1] = t - a[1];
+  }
+};
+
+template <typename R, int S>
+struct DFT<R, 3, S> {
+  static __device__ __forceinline__ void run(cpx<R>* a) {
+    const R h = R(0.8660254037844386467637231707529362);  // sqrt(3)/2
+    cpx<R> t1 = a[1] + a[2];
+    cpx<R> t2 = a[1] - a[2];
+    cpx<R> m = a[0] - scale(t1, R(0.5));
+    cpx<R> n = scale(mul_si<R, S>(t2), h);
+    a[0] = a[0] + t1;
+    a[1] = m + n;
+    a[2] = m - n;
+  }
+};
+
+template <typename R, int S>
+struct DFT<R, 4, S> {
+  static __device__ __forceinline__ void run(cpx<R>* a) {
+    cpx<R> t0 = a[0] + a[2];
+    cpx<R> t1 = a[0] - a[2];
+    cpx<R> t2 = a[1] + a[3];
+    cpx<R> t3 = mul_si<R, S>(a[1] - a[3]);
+    a[0] = t0 + t2;
+    a[2] = t0 - t2;
+    a[1] = t1 + t3;
+    a[3] = t1 - t3;
+  }
+};
+
+template <typename R, int S>
+struct DFT<R, 5, S> {
+  static __device__ __forceinline__ void run(cpx<R>* a) {
+    const R c1 = R(0.3090169943749474241022934171828191);   // cos(2 pi/5)
+    const R c2 = R(-0.8090169943749474241022934171828191);  // cos(4 pi/5)
+    const R s1 = R(0.9510565162951535721164393333793821);   // sin(2 pi/5)
+    const R s2 = R(0.5877852522924731291687059546390728);   // sin(4 pi/5)
+    cpx<R> t1 = a[1] + a[4];
+    cpx<R> t2 = a[2] + a[3];
+    cpx<R> t3 = a[1] - a[4];
+    cpx<R> t4 = a[2] - a[3];
+    cpx<R> b1 = a[0] + scale(t1, c1) + scale(t2, c2);
+    cpx<R> b2 = a[0] + scale(t1, c2) + scale(t2, c1);
+    cpx<R> d1 = mul_si<R, S>(scale(t3, s1) + scale(t4, s2));
+    cpx<R> d2 = mul_si<R, S>(scale(t3, s2) - scale(t4, s1));
+    a[0] = a[0] + t1 + t2;
+    a[1] = b1 + d1;
+    a[4] = b1 - d1;
+    a[2] = b2 + d2;
+    a[3] = b2 - d2;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// line FFT across a lane group
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x >> 1); }
+
+__device__ __forceinline__ int bitrev(int t, int bits) {
+  return bits == 0 ? 0 : (int)(__brev((unsigned)t) >> (32 - bits));
+}
+
+// exp(S 2 pi i j / N) from a global table of exp(+2 pi i j / N), j in [0, N)
+template <typename R, int S>
+__device__ __forceinline__ cpx<R> table_w(const cpx<R>* __restrict__ tw, int j) {
+  cpx<R> w;
+  w.x = __ldg(&tw[j].x);
+  w.y = __ldg(&tw[j].y);
+  return S > 0 ? w : conj(w);
+}
+
+// Distribution A -> B.  t = lane index inside the group (0..TPL-1).
+template <typename R, int N, int TPL, int S>
+__device__ __forceinline__ void fft_a2b(cpx<R> (&v)[N / TPL], int t, const cpx<R>* __restrict__ tw) {
+  constexpr int M = N / TPL;
+  DFT<R, M, S>::run(v);
+  if constexpr (TPL > 1) {
+#pragma unroll
+    for (int k2 = 1; k2 < M; ++k2) v[k2] = v[k2] * table_w<R, S>(tw, (t * k2) % N);
+#pragma unroll
+    for (int half = TPL / 2; half >= 1; half >>= 1) {
+      const int L = 2 * half;
+      const int j = t & (half - 1);
+      const bool up = (t & half) != 0;
+      const cpx<R> W = table_w<R, S>(tw, j * (N / L));
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        cpx<R> p = shfl_xor(v[i], half);
+        v[i] = up ? (p - v[i]) * W : v[i] + p;
+      }
+    }
+  }
+}
+
+// Distribution B -> A (the transposed network of fft_a2b).
+template <typename R, int N, int TPL, int S>
+__device__ __forceinline__ void fft_b2a(cpx<R> (&v)[N / TPL], int t, const cpx<R>* __restrict__ tw) {
+  constexpr int M = N / TPL;
+  if constexpr (TPL > 1) {
+#pragma unroll
+    for (int half = 1; half < TPL; half <<= 1) {
+      const int L = 2 * half;
+      const int j = t & (half - 1);
+      const bool up = (t & half) != 0;
+      const cpx<R> W = table_w<R, S>(tw, j * (N / L));
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        cpx<R> own = up ? v[i] * W : v[i];
+        cpx<R> p = shfl_xor(own, half);
+        v[i] = up ? p - own : own + p;
+      }
+    }
+#pragma unroll
+    for (int k2 = 1; k2 < M; ++k2) v[k2] = v[k2] * table_w<R, S>(tw, (t * k2) % N);
+  }
+  DFT<R, M, S>::run(v);
+}
+
+// position held by (lane t, register i) in each distribution
+template <int N, int TPL>
+__device__ __forceinline__ int pos_a(int t, int i) { return t + TPL * i; }
+template <int N, int TPL>
+__device__ __forceinline__ int pos_b(int t, int i) {
+  return i + (N / TPL) * bitrev(t, ilog2c(TPL));
+}
+// signed frequency of grid position p (|n| < N/2 for every sphere member)
+__device__ __forceinline__ int freq_of(int p, int N) { return p < N / 2 ? p : p - N; }
+
+}  // namespace pdep

@@ -1,0 +1,809 @@
+// Dense linear algebra, vector and CG kernels (see linalg.cuh).
+#include "linalg.cuh"
+#include "profile.cuh"
+
+#include <vector>
+
+namespace pdep {
+
+static int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 132;
+  }
+  return n;
+}
+
+template <typename R>
+__device__ __forceinline__ R warp_sum(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block-wide sum of up to two values; every thread gets the result
+__device__ __forceinline__ double2 block_sum2(double a, double b) {
+  __shared__ double sa[32], sb[32];
+  a = warp_sum(a);
+  b = warp_sum(b);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) {
+    sa[w] = a;
+    sb[w] = b;
+  }
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  double x = 0.0, y = 0.0;
+  for (int i = 0; i < nw; ++i) {
+    x += sa[i];
+    y += sb[i];
+  }
+  return make_double2(x, y);
+}
+
+// ---------------------------------------------------------------------------
+// GEMM (SIMT, register-tiled 64x64x16)
+// ---------------------------------------------------------------------------
+template <typename R, bool TA>
+__global__ void __launch_bounds__(256) k_gemm(int m, int n, int k, R alpha, const R* __restrict__ A,
+                                              long long lda, const R* __restrict__ B, long long ldb,
+                                              R beta, R* __restrict__ C, long long ldc, int kchunk,
+                                              int atomic) {
+  constexpr int BM = 64, BN = 64, BK = 16;
+  __shared__ R As[BK][BM + 1];
+  __shared__ R Bs[BK][BN + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int row0 = blockIdx.x * BM, col0 = blockIdx.y * BN;
+  const int kbeg = blockIdx.z * kchunk;
+  const int kend = min(k, kbeg + kchunk);
+  R acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = R(0);
+
+  for (int kb = kbeg; kb < kend; kb += BK) {
+    if (TA) {
+      const int i = tid >> 2, kk0 = (tid & 3) * 4;
+      const int gi = row0 + i;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int gk = kb + kk0 + q;
+        As[kk0 + q][i] = (gi < m && gk < kend) ? A[gk + (long long)gi * lda] : R(0);
+      }
+    } else {
+      const int kk = tid >> 4, i0 = (tid & 15) * 4;
+      const int gk = kb + kk;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int gi = row0 + i0 + q;
+        As[kk][i0 + q] = (gi < m && gk < kend) ? A[gi + (long long)gk * lda] : R(0);
+      }
+    }
+    {
+      const int j = tid >> 2, kk0 = (tid & 3) * 4;
+      const int gj = col0 + j;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int gk = kb + kk0 + q;
+        Bs[kk0 + q][j] = (gj < n && gk < kend) ? B[gk + (long long)gj * ldb] : R(0);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      R av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = As[kk][tx + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][ty + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int gi = row0 + tx + 16 * a;
+    if (gi >= m) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int gj = col0 + ty + 16 * b;
+      if (gj >= n) continue;
+      R* c = C + gi + (long long)gj * ldc;
+      if (atomic) {
+        atomicAdd(c, alpha * acc[a][b]);
+      } else {
+        R v = alpha * acc[a][b];
+        if (beta != R(0)) v += beta * *c;
+        *c = v;
+      }
+    }
+  }
+}
+
+template <typename R>
+__global__ void k_scale_mat(R* C, long long ldc, int m, int n, R beta) {
+  const long long tot = (long long)m * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % m), j = (int)(e / m);
+    R* c = C + i + (long long)j * ldc;
+    *c = beta == R(0) ? R(0) : beta * *c;
+  }
+}
+
+template <typename R>
+cudaError_t gemm(bool transA, int m, int n, int k, double alpha, const R* A, long long lda,
+                 const R* B, long long ldb, double beta, R* C, long long ldc, cudaStream_t st) {
+  if (m <= 0 || n <= 0) return cudaSuccess;
+  const int tm = (m + 63) / 64, tn = (n + 63) / 64;
+  int splits = 1;
+  const long long tiles = (long long)tm * tn;
+  if (tiles < 2LL * num_sms() && k > 256) {
+    splits = (int)((2LL * num_sms() + tiles - 1) / tiles);
+    splits = std::min(splits, (k + 255) / 256);
+    splits = std::max(splits, 1);
+  }
+  int kchunk = (k + splits - 1) / splits;
+  kchunk = ((kchunk + 15) / 16) * 16;
+  if (kchunk == 0) kchunk = 16;
+  splits = std::max(1, (k + kchunk - 1) / kchunk);
+  if (k <= 0) splits = 1;
+  int atomic = 0;
+  if (splits > 1 || k <= 0) {
+    const long long tot = (long long)m * n;
+    const int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
+    count_launch();
+    k_scale_mat<R><<<blocks, 256, 0, st>>>(C, ldc, m, n, (R)beta);
+    if (k <= 0) return cudaGetLastError();
+    atomic = 1;
+  }
+  dim3 grid(tm, tn, splits);
+  ProfScope ps(sizeof(R) == 8 ? PC_GEMM_F64 : PC_GEMM_F32, st, 2.0 * m * n * (double)k,
+               ((double)m * k + (double)k * n + (beta != 0.0 ? 2.0 : 1.0) * m * n) * sizeof(R));
+  count_launch();
+  if (transA)
+    k_gemm<R, true><<<grid, 256, 0, st>>>(m, n, k, (R)alpha, A, lda, B, ldb, (R)beta, C, ldc,
+                                          kchunk, atomic);
+  else
+    k_gemm<R, false><<<grid, 256, 0, st>>>(m, n, k, (R)alpha, A, lda, B, ldb, (R)beta, C, ldc,
+                                           kchunk, atomic);
+  return cudaGetLastError();
+}
+
+template cudaError_t gemm<double>(bool, int, int, int, double, const double*, long long,
+                                  const double*, long long, double, double*, long long,
+                                  cudaStream_t);
+template cudaError_t gemm<float>(bool, int, int, int, double, const float*, long long,
+                                 const float*, long long, double, float*, long long, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// one-sided Jacobi eigensolver
+// ---------------------------------------------------------------------------
+__global__ void k_gershgorin(const double* __restrict__ M, long long ldm, int n, double* out) {
+  double mx = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) s += fabs(M[i + (long long)j * ldm]);
+    mx = fmax(mx, s);
+  }
+  __shared__ double sm[32];
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m2 = 0.0;
+    for (int w = 0; w < (int)((blockDim.x + 31) / 32); ++w) m2 = fmax(m2, sm[w]);
+    *out = m2 > 0.0 ? m2 * (1.0 + 1e-3) : 1.0;
+  }
+}
+
+__global__ void k_jacobi_init(const double* __restrict__ M, long long ldm, int n,
+                              const double* __restrict__ sigma, double* A, double* V) {
+  const long long tot = (long long)n * n;
+  const double s = *sigma;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    double m = 0.5 * (M[i + (long long)j * ldm] + M[j + (long long)i * ldm]);
+    A[e] = (i == j) ? m - s : m;
+    V[e] = (i == j) ? 1.0 : 0.0;
+  }
+}
+
+__global__ void k_jacobi_round(double* A, double* V, int n, int nn, int round,
+                               unsigned* counter) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= nn / 2) return;
+  int p, q;
+  if (warp == 0) {
+    p = nn - 1;
+    q = round;
+  } else {
+    p = (round + warp) % (nn - 1);
+    q = (round - warp + (nn - 1)) % (nn - 1);
+  }
+  if (p >= n || q >= n) return;
+  double* ap = A + (long long)p * n;
+  double* aq = A + (long long)q * n;
+  double al = 0.0, be = 0.0, ga = 0.0;
+  for (int r = lane; r < n; r += 32) {
+    const double x = ap[r], y = aq[r];
+    al += x * x;
+    be += y * y;
+    ga += x * y;
+  }
+  al = warp_sum(al);
+  be = warp_sum(be);
+  ga = warp_sum(ga);
+  if (ga == 0.0 || fabs(ga) <= 1e-15 * sqrt(al * be)) return;
+  const double zeta = (be - al) / (2.0 * ga);
+  const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  const double c = 1.0 / sqrt(1.0 + tt * tt);
+  const double s = c * tt;
+  for (int r = lane; r < n; r += 32) {
+    const double x = ap[r], y = aq[r];
+    ap[r] = c * x - s * y;
+    aq[r] = s * x + c * y;
+  }
+  double* vp = V + (long long)p * n;
+  double* vq = V + (long long)q * n;
+  for (int r = lane; r < n; r += 32) {
+    const double x = vp[r], y = vq[r];
+    vp[r] = c * x - s * y;
+    vq[r] = s * x + c * y;
+  }
+  if (lane == 0) atomicAdd(counter, 1u);
+}
+
+// w_i = v_i . (M v_i)
+__global__ void k_col_dots(const double* __restrict__ V, const double* __restrict__ MV, int n,
+                           double* w) {
+  const int c = blockIdx.x;
+  double s = 0.0;
+  for (int r = threadIdx.x; r < n; r += blockDim.x)
+    s += V[r + (long long)c * n] * MV[r + (long long)c * n];
+  double2 t = block_sum2(s, 0.0);
+  if (threadIdx.x == 0) w[c] = t.x;
+}
+
+// rank sort (ascending, stable) and column permutation
+__global__ void k_sort_ranks(const double* __restrict__ w, int n, int* rank) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double wi = w[i];
+    int r = 0;
+    for (int j = 0; j < n; ++j) {
+      const double wj = w[j];
+      r += (wj < wi || (wj == wi && j < i)) ? 1 : 0;
+    }
+    rank[i] = r;
+  }
+}
+__global__ void k_permute(const double* __restrict__ w, const double* __restrict__ V, int n,
+                          const int* __restrict__ rank, double* W, double* Vout, long long ldv) {
+  const int c = blockIdx.x;
+  const int rc = rank[c];
+  if (threadIdx.x == 0) W[rc] = w[c];
+  for (int r = threadIdx.x; r < n; r += blockDim.x)
+    Vout[r + (long long)rc * ldv] = V[r + (long long)c * n];
+}
+
+cudaError_t eigh(int n, const double* M, long long ldm, double* W, double* V, long long ldv,
+                 EighWork wk, cudaStream_t st, int max_sweeps) {
+  if (n <= 0) return cudaSuccess;
+  ProfScope ps(PC_EIGH, st, 0.0, 0.0);
+  double* sigma = wk.w;  // reuse w[0] for the shift; overwritten later
+  unsigned* counter = reinterpret_cast<unsigned*>(wk.flag + 1);
+  count_launch();
+  k_gershgorin<<<1, 256, 0, st>>>(M, ldm, n, sigma);
+  const long long tot = (long long)n * n;
+  const int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
+  count_launch();
+  k_jacobi_init<<<blocks, 256, 0, st>>>(M, ldm, n, sigma, wk.a, wk.v);
+  const int nn = n + (n & 1);
+  const int warps = nn / 2;
+  const int tpb = 128;
+  const int jb = (warps * 32 + tpb - 1) / tpb;
+  unsigned hcount = 1;
+  for (int sweep = 0; sweep < max_sweeps && hcount != 0; ++sweep) {
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    for (int r = 0; r < nn - 1; ++r) {
+      count_launch();
+      k_jacobi_round<<<jb, tpb, 0, st>>>(wk.a, wk.v, n, nn, r, counter);
+    }
+    if (nn - 1 == 0) break;
+    e = cudaMemcpyAsync(&hcount, counter, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+  }
+  // Rayleigh quotients with the original (symmetrised) matrix
+  cudaError_t e = gemm<double>(false, n, n, n, 1.0, M, ldm, wk.v, n, 0.0, wk.tmp, n, st);
+  if (e != cudaSuccess) return e;
+  { count_launch(); k_col_dots<<<n, 128, 0, st>>>(wk.v, wk.tmp, n, wk.w); }
+  int* rank = reinterpret_cast<int*>(wk.tmp);  // tmp no longer needed
+  count_launch();
+  k_sort_ranks<<<(n + 127) / 128, 128, 0, st>>>(wk.w, n, rank);
+  count_launch();
+  k_permute<<<n, 128, 0, st>>>(wk.w, wk.v, n, rank, W, V, ldv);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_symmetrize(R* M, int n, long long ld) {
+  const long long tot = (long long)n * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    if (i < j) {
+      R a = M[i + (long long)j * ld], b = M[j + (long long)i * ld];
+      R s = R(0.5) * (a + b);
+      M[i + (long long)j * ld] = s;
+      M[j + (long long)i * ld] = s;
+    }
+  }
+}
+template <typename R>
+cudaError_t symmetrize(R* M, int n, long long ld, cudaStream_t st) {
+  const long long tot = (long long)n * n;
+  const int blocks = (int)std::max<long long>(1, std::min<long long>((tot + 255) / 256, 4096));
+  count_launch();
+  k_symmetrize<R><<<blocks, 256, 0, st>>>(M, n, ld);
+  return cudaGetLastError();
+}
+template cudaError_t symmetrize<double>(double*, int, long long, cudaStream_t);
+
+template <typename Rd, typename Rs>
+__global__ void k_convert(Rd* dst, long long ldd, const Rs* __restrict__ src, long long lds,
+                          int rows, int cols) {
+  const long long tot = (long long)rows * cols;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e % rows), c = (int)(e / rows);
+    dst[r + (long long)c * ldd] = (Rd)src[r + (long long)c * lds];
+  }
+}
+template <typename Rd, typename Rs>
+cudaError_t convert(Rd* dst, long long ldd, const Rs* src, long long lds, int rows, int cols,
+                    cudaStream_t st) {
+  const long long tot = (long long)rows * cols;
+  if (tot == 0) return cudaSuccess;
+  const int blocks = (int)std::min<long long>((tot + 255) / 256, 8192);
+  count_launch();
+  k_convert<Rd, Rs><<<blocks, 256, 0, st>>>(dst, ldd, src, lds, rows, cols);
+  return cudaGetLastError();
+}
+template cudaError_t convert<double, double>(double*, long long, const double*, long long, int, int,
+                                             cudaStream_t);
+template cudaError_t convert<float, double>(float*, long long, const double*, long long, int, int,
+                                            cudaStream_t);
+template cudaError_t convert<double, float>(double*, long long, const float*, long long, int, int,
+                                            cudaStream_t);
+
+template <typename R>
+__global__ void k_col_norms(const R* __restrict__ X, long long ld, int rows, double* out) {
+  const int c = blockIdx.x;
+  double s = 0.0;
+  for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+    const double v = (double)X[r + (long long)c * ld];
+    s += v * v;
+  }
+  double2 t = block_sum2(s, 0.0);
+  if (threadIdx.x == 0) out[c] = sqrt(t.x);
+}
+template <typename R>
+cudaError_t col_norms(const R* X, long long ld, int rows, int cols, double* out, cudaStream_t st) {
+  if (cols <= 0) return cudaSuccess;
+  { count_launch(); k_col_norms<R><<<cols, 256, 0, st>>>(X, ld, rows, out); }
+  return cudaGetLastError();
+}
+template cudaError_t col_norms<double>(const double*, long long, int, int, double*, cudaStream_t);
+template cudaError_t col_norms<float>(const float*, long long, int, int, double*, cudaStream_t);
+
+template <typename R>
+__global__ void k_scale_cols(R* X, long long ld, int rows, const double* __restrict__ s, int inv) {
+  const int c = blockIdx.x;
+  double f = s[c];
+  if (inv) f = f != 0.0 ? 1.0 / f : 0.0;
+  for (int r = threadIdx.x; r < rows; r += blockDim.x) X[r + (long long)c * ld] *= (R)f;
+}
+template <typename R>
+cudaError_t scale_cols(R* X, long long ld, int rows, int cols, const double* s, int invert,
+                       cudaStream_t st) {
+  if (cols <= 0) return cudaSuccess;
+  { count_launch(); k_scale_cols<R><<<cols, 256, 0, st>>>(X, ld, rows, s, invert); }
+  return cudaGetLastError();
+}
+template cudaError_t scale_cols<double>(double*, long long, int, int, const double*, int,
+                                        cudaStream_t);
+template cudaError_t scale_cols<float>(float*, long long, int, int, const double*, int,
+                                       cudaStream_t);
+
+__global__ void k_ritz_residual(const double* __restrict__ AX, const double* __restrict__ X,
+                                long long ld, int rows, const double* __restrict__ th, double* Rr) {
+  const int c = blockIdx.x;
+  const double t = th[c];
+  for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+    const long long e = r + (long long)c * ld;
+    Rr[e] = AX[e] - t * X[e];
+  }
+}
+cudaError_t ritz_residual(const double* AX, const double* X, long long ld, int rows, int cols,
+                          const double* theta, double* Rout, cudaStream_t st) {
+  if (cols <= 0) return cudaSuccess;
+  { count_launch(); k_ritz_residual<<<cols, 256, 0, st>>>(AX, X, ld, rows, theta, Rout); }
+  return cudaGetLastError();
+}
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) and Box-Muller
+__device__ __forceinline__ void philox_round(uint32_t (&c)[4], const uint32_t (&k)[2]) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t hi0 = __umulhi(M0, c[0]), lo0 = M0 * c[0];
+  const uint32_t hi1 = __umulhi(M1, c[2]), lo1 = M1 * c[2];
+  uint32_t n0 = hi1 ^ c[1] ^ k[0];
+  uint32_t n2 = hi0 ^ c[3] ^ k[1];
+  c[0] = n0;
+  c[1] = lo1;
+  c[2] = n2;
+  c[3] = lo0;
+}
+__device__ __forceinline__ void philox4x32_10(uint32_t (&c)[4], uint32_t k0, uint32_t k1) {
+  uint32_t k[2] = {k0, k1};
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    philox_round(c, k);
+    k[0] += 0x9E3779B9u;
+    k[1] += 0xBB67AE85u;
+  }
+}
+__global__ void k_philox_normal(double* X, long long ld, int rows, int cols,
+                                unsigned long long seed, unsigned long long offset) {
+  const long long tot = (long long)rows * cols;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long ctr = offset + (unsigned long long)e;
+    uint32_t c[4] = {(uint32_t)ctr, (uint32_t)(ctr >> 32), 0u, 0u};
+    philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+    const unsigned long long a = ((unsigned long long)c[0] << 21) ^ (c[1] >> 11);  // 53 bits
+    const unsigned long long b = ((unsigned long long)c[2] << 21) ^ (c[3] >> 11);
+    const double u1 = ((double)(a & ((1ULL << 53) - 1)) + 1.0) * (1.0 / 9007199254740992.0);
+    const double u2 = (double)(b & ((1ULL << 53) - 1)) * (1.0 / 9007199254740992.0);
+    const int r = (int)(e % rows), cc = (int)(e / rows);
+    X[r + (long long)cc * ld] = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+  }
+}
+cudaError_t philox_normal(double* X, long long ld, int rows, int cols, unsigned long long seed,
+                          unsigned long long offset, cudaStream_t st) {
+  const long long tot = (long long)rows * cols;
+  if (tot == 0) return cudaSuccess;
+  const int blocks = (int)std::min<long long>((tot + 255) / 256, 8192);
+  count_launch();
+  k_philox_normal<<<blocks, 256, 0, st>>>(X, ld, rows, cols, seed, offset);
+  return cudaGetLastError();
+}
+
+__global__ void k_isqrt_clamped(double* Q, long long ldq, int n, const double* __restrict__ d,
+                                double dmin, int* keep) {
+  const int c = blockIdx.x;
+  const double dv = d[c];
+  const bool k = dv > dmin;
+  const double f = k ? 1.0 / sqrt(dv) : 0.0;
+  if (threadIdx.x == 0 && keep) keep[c] = k ? 1 : 0;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) Q[r + (long long)c * ldq] *= f;
+}
+cudaError_t scale_by_isqrt_clamped(double* Q, long long ldq, int n, const double* d, double dmin,
+                                   int* keep, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  { count_launch(); k_isqrt_clamped<<<n, 128, 0, st>>>(Q, ldq, n, d, dmin, keep); }
+  return cudaGetLastError();
+}
+
+cudaError_t fill_zero(void* p, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return cudaSuccess;
+  return cudaMemsetAsync(p, 0, bytes, st);
+}
+
+// ---------------------------------------------------------------------------
+// preconditioned CG on (H - eps_v + alpha P_v) x = b, one CTA per RHS
+// ---------------------------------------------------------------------------
+// Teter-Payne-Allan kinetic preconditioner (Phys. Rev. B 40, 12255 (1989)):
+// K(x) = (27 + 18x + 12x^2 + 8x^3) / (27 + 18x + 12x^2 + 8x^3 + 16x^4),
+// x = (|G|^2/2) / E_kin(v).
+__device__ __forceinline__ double tpa(double x) {
+  const double p = 27.0 + x * (18.0 + x * (12.0 + 8.0 * x));
+  return p / (p + 16.0 * x * x * x * x);
+}
+__device__ __forceinline__ double precond(const double* __restrict__ g2, int n_half, int j,
+                                          double inv_e) {
+  if (j >= 2 * n_half) return 1.0;
+  return tpa(0.5 * g2[j >> 1] * inv_e);
+}
+
+template <typename R>
+__global__ void k_cg_start(CgArgs<R> a, const R* __restrict__ b, long long ldb) {
+  const int i = blockIdx.x;
+  const long long o = (long long)i * a.ld;
+  const double inv_e = 1.0 / a.ekin[i % a.n_occ];
+  double bb = 0.0, rz = 0.0;
+  for (int j = threadIdx.x; j < a.n_pw; j += blockDim.x) {
+    const R bv = b[(long long)i * ldb + j];
+    const double kz = precond(a.g2, a.n_half, j, inv_e);
+    a.x[o + j] = R(0);
+    a.r[o + j] = bv;
+    a.p[o + j] = (R)(kz * (double)bv);
+    bb += (double)bv * bv;
+    rz += kz * (double)bv * bv;
+  }
+  double2 t = block_sum2(bb, rz);
+  if (threadIdx.x == 0) {
+    CgScal s;
+    s.bnorm = sqrt(t.x);
+    s.rnorm = s.bnorm;
+    s.rz = t.y;
+    s.iters = 0;
+    s.active = t.x > 0.0 ? 1 : 0;
+    a.sc[i] = s;
+    if (s.active) atomicAdd(a.n_active, 1);
+  }
+}
+
+template <typename R>
+__global__ void k_cg_step(CgArgs<R> a) {
+  const int i = blockIdx.x;
+  __shared__ CgScal s;
+  if (threadIdx.x == 0) s = a.sc[i];
+  __syncthreads();
+  if (!s.active) return;
+  const long long o = (long long)i * a.ld;
+  const double inv_e = 1.0 / a.ekin[i % a.n_occ];
+  double pap = 0.0;
+  for (int j = threadIdx.x; j < a.n_pw; j += blockDim.x)
+    pap += (double)a.p[o + j] * (double)a.ap[o + j];
+  const double2 t1 = block_sum2(pap, 0.0);
+  const double alpha = s.rz / t1.x;
+  if (!(t1.x > 0.0) || !isfinite(alpha)) {
+    if (threadIdx.x == 0) {
+      atomicOr(a.status, isfinite(t1.x) ? (unsigned)DEV_BREAKDOWN : (unsigned)DEV_NONFINITE);
+      a.sc[i].active = 0;
+    }
+    return;
+  }
+  double rr = 0.0, rkr = 0.0;
+  for (int j = threadIdx.x; j < a.n_pw; j += blockDim.x) {
+    const double pv = (double)a.p[o + j];
+    const double xv = (double)a.x[o + j] + alpha * pv;
+    const double rv = (double)a.r[o + j] - alpha * (double)a.ap[o + j];
+    a.x[o + j] = (R)xv;
+    a.r[o + j] = (R)rv;
+    rr += rv * rv;
+    rkr += precond(a.g2, a.n_half, j, inv_e) * rv * rv;
+  }
+  const double2 t2 = block_sum2(rr, rkr);
+  const double rn = sqrt(t2.x);
+  const bool done = rn <= a.tol * s.bnorm;
+  const double beta = t2.y / s.rz;
+  if (!done) {
+    for (int j = threadIdx.x; j < a.n_pw; j += blockDim.x) {
+      const double z = precond(a.g2, a.n_half, j, inv_e) * (double)a.r[o + j];
+      a.p[o + j] = (R)(z + beta * (double)a.p[o + j]);
+    }
+  }
+  if (threadIdx.x == 0) {
+    CgScal n = s;
+    n.iters = s.iters + 1;
+    n.rnorm = rn;
+    n.rz = t2.y;
+    n.active = done ? 0 : 1;
+    if (!isfinite(rn)) {
+      n.active = 0;
+      atomicOr(a.status, (unsigned)DEV_NONFINITE);
+    }
+    a.sc[i] = n;
+    if (n.active) atomicAdd(a.n_active, 1);
+  }
+}
+
+template <typename R>
+cudaError_t cg_start(const CgArgs<R>& a, const R* b, long long ldb, cudaStream_t st) {
+  if (a.n_rhs <= 0) return cudaSuccess;
+  { count_launch(); k_cg_start<R><<<a.n_rhs, 256, 0, st>>>(a, b, ldb); }
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t cg_step(const CgArgs<R>& a, cudaStream_t st) {
+  if (a.n_rhs <= 0) return cudaSuccess;
+  // x, r, p, Ap read; x, r, p written (plus r, p re-read): ~11 vector passes
+  ProfScope ps(sizeof(R) == 8 ? PC_CG_F64 : PC_CG_F32, st, 20.0 * a.n_rhs * (double)a.n_pw,
+               11.0 * a.n_rhs * (double)a.n_pw * sizeof(R));
+  { count_launch(); k_cg_step<R><<<a.n_rhs, 256, 0, st>>>(a); }
+  return cudaGetLastError();
+}
+template cudaError_t cg_start<double>(const CgArgs<double>&, const double*, long long, cudaStream_t);
+template cudaError_t cg_start<float>(const CgArgs<float>&, const float*, long long, cudaStream_t);
+template cudaError_t cg_step<double>(const CgArgs<double>&, cudaStream_t);
+template cudaError_t cg_step<float>(const CgArgs<float>&, cudaStream_t);
+
+__global__ void k_residual_norms(const double* __restrict__ b, long long ldb, double* ap,
+                                 long long lda, int n_pw, double* rel, const int* __restrict__ list) {
+  const int i = list ? list[blockIdx.x] : blockIdx.x;
+  double rr = 0.0, bb = 0.0;
+  for (int j = threadIdx.x; j < n_pw; j += blockDim.x) {
+    const double bv = b[(long long)i * ldb + j];
+    const double r = bv - ap[(long long)i * lda + j];
+    ap[(long long)i * lda + j] = r;
+    rr += r * r;
+    bb += bv * bv;
+  }
+  double2 t = block_sum2(rr, bb);
+  if (threadIdx.x == 0) rel[i] = t.y > 0.0 ? sqrt(t.x / t.y) : 0.0;
+}
+cudaError_t residual_norms(const double* b, long long ldb, double* ap, long long lda, int n_pw,
+                           int n, double* rel, const int* list, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  { count_launch(); k_residual_norms<<<n, 256, 0, st>>>(b, ldb, ap, lda, n_pw, rel, list); }
+  return cudaGetLastError();
+}
+
+// ordered compaction with one block of 1024 threads (contiguous chunks + scan)
+template <typename Pred>
+__device__ void compact_block(int n, Pred pred, int* list, int* count) {
+  __shared__ int offs[1024];
+  const int T = blockDim.x;
+  const int chunk = (n + T - 1) / T;
+  const int lo = min(n, threadIdx.x * chunk), hi = min(n, lo + chunk);
+  int c = 0;
+  for (int i = lo; i < hi; ++i) c += pred(i) ? 1 : 0;
+  offs[threadIdx.x] = c;
+  __syncthreads();
+  for (int d = 1; d < T; d <<= 1) {
+    int v = threadIdx.x >= d ? offs[threadIdx.x - d] : 0;
+    __syncthreads();
+    offs[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int o = offs[threadIdx.x] - c;
+  for (int i = lo; i < hi; ++i)
+    if (pred(i)) list[o++] = i;
+  if (threadIdx.x == T - 1) *count = offs[T - 1];
+}
+__global__ void k_active_list(const CgScal* __restrict__ sc, int n, int* list, int* count) {
+  compact_block(n, [&](int i) { return sc[i].active != 0; }, list, count);
+}
+__global__ void k_unconv_list(const double* __restrict__ rel, double tol, int n, int* list,
+                              int* count) {
+  compact_block(n, [&](int i) { return rel[i] > tol; }, list, count);
+}
+cudaError_t active_list(const CgScal* sc, int n, int* list, int* count, cudaStream_t st) {
+  count_launch();
+  k_active_list<<<1, 1024, 0, st>>>(sc, n, list, count);
+  return cudaGetLastError();
+}
+cudaError_t unconverged_list(const double* rel, double tol, int n, int* list, int* count,
+                             cudaStream_t st) {
+  count_launch();
+  k_unconv_list<<<1, 1024, 0, st>>>(rel, tol, n, list, count);
+  return cudaGetLastError();
+}
+
+__global__ void k_refine_prepare(const double* __restrict__ r64, long long ld64, int n_pw,
+                                 const double* __restrict__ rel, double tol, float* r32,
+                                 long long ld32, double* rn) {
+  const int i = blockIdx.x;
+  const bool act = rel[i] > tol;
+  double ss = 0.0;
+  if (act)
+    for (int j = threadIdx.x; j < n_pw; j += blockDim.x) {
+      const double v = r64[(long long)i * ld64 + j];
+      ss += v * v;
+    }
+  const double2 t = block_sum2(ss, 0.0);
+  const double nrm = sqrt(t.x);
+  const double f = (act && nrm > 0.0) ? 1.0 / nrm : 0.0;
+  for (int j = threadIdx.x; j < n_pw; j += blockDim.x)
+    r32[(long long)i * ld32 + j] = (float)(f * r64[(long long)i * ld64 + j]);
+  if (threadIdx.x == 0) rn[i] = act ? nrm : 0.0;
+}
+cudaError_t refine_prepare(const double* r64, long long ld64, int n_pw, int n, const double* rel,
+                           double tol, float* r32, long long ld32, double* rn, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  { count_launch(); k_refine_prepare<<<n, 256, 0, st>>>(r64, ld64, n_pw, rel, tol, r32, ld32, rn); }
+  return cudaGetLastError();
+}
+__global__ void k_refine_accumulate(double* x64, long long ld64, const float* __restrict__ d32,
+                                    long long ld32, int n_pw, const double* __restrict__ rn) {
+  const int i = blockIdx.x;
+  const double f = rn[i];
+  if (f == 0.0) return;
+  for (int j = threadIdx.x; j < n_pw; j += blockDim.x)
+    x64[(long long)i * ld64 + j] += f * (double)d32[(long long)i * ld32 + j];
+}
+cudaError_t refine_accumulate(double* x64, long long ld64, const float* d32, long long ld32,
+                              int n_pw, int n, const double* rn, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  { count_launch(); k_refine_accumulate<<<n, 256, 0, st>>>(x64, ld64, d32, ld32, n_pw, rn); }
+  return cudaGetLastError();
+}
+
+__global__ void k_kinetic(const double* __restrict__ X, long long ld, int n_half,
+                          const double* __restrict__ g2, double* out) {
+  const int i = blockIdx.x;
+  double s = 0.0;
+  for (int k = threadIdx.x; k < n_half; k += blockDim.x) {
+    const double a = X[(long long)i * ld + 2 * k], b = X[(long long)i * ld + 2 * k + 1];
+    s += 0.5 * g2[k] * (a * a + b * b);
+  }
+  const double2 t = block_sum2(s, 0.0);
+  if (threadIdx.x == 0) out[i] = t.x;
+}
+cudaError_t kinetic_energy(const double* X, long long ld, int n_half, int n, const double* g2,
+                           double* out, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  { count_launch(); k_kinetic<<<n, 256, 0, st>>>(X, ld, n_half, g2, out); }
+  return cudaGetLastError();
+}
+__global__ void k_precondition(double* T, long long ld, int n_pw, int n_half,
+                               const double* __restrict__ g2, const double* __restrict__ ekin) {
+  const int i = blockIdx.x;
+  const double e = ekin[i] > 1e-3 ? ekin[i] : 1e-3;
+  const double inv_e = 1.0 / e;
+  for (int j = threadIdx.x; j < n_pw; j += blockDim.x)
+    T[(long long)i * ld + j] *= precond(g2, n_half, j, inv_e);
+}
+cudaError_t precondition_tpa(double* T, long long ld, int n_pw, int n_half, int n,
+                             const double* g2, const double* ekin, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  { count_launch(); k_precondition<<<n, 256, 0, st>>>(T, ld, n_pw, n_half, g2, ekin); }
+  return cudaGetLastError();
+}
+__global__ void k_gather_cols(const double* __restrict__ X, long long ldx, double* Y,
+                              long long ldy, int rows, const int* __restrict__ idx) {
+  const int i = blockIdx.x;
+  const int src = idx[i];
+  for (int r = threadIdx.x; r < rows; r += blockDim.x)
+    Y[(long long)i * ldy + r] = X[(long long)src * ldx + r];
+}
+cudaError_t gather_cols(const double* X, long long ldx, double* Y, long long ldy, int rows,
+                        const int* idx, int n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  { count_launch(); k_gather_cols<<<n, 256, 0, st>>>(X, ldx, Y, ldy, rows, idx); }
+  return cudaGetLastError();
+}
+__global__ void k_unit_start(double* X, long long ld, int rows, const int* __restrict__ comp,
+                             double amp) {
+  const int i = blockIdx.x;
+  for (int r = threadIdx.x; r < rows; r += blockDim.x) X[(long long)i * ld + r] *= amp;
+  __syncthreads();
+  if (threadIdx.x == 0) X[(long long)i * ld + comp[i]] += 1.0;
+}
+cudaError_t unit_start(double* X, long long ld, int rows, const int* comp, int n, double amp,
+                       unsigned long long seed, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  cudaError_t e = philox_normal(X, ld, rows, n, seed, 0ULL, st);
+  if (e != cudaSuccess) return e;
+  { count_launch(); k_unit_start<<<n, 256, 0, st>>>(X, ld, rows, comp, amp); }
+  return cudaGetLastError();
+}
+__global__ void k_zero_row(double* X, long long ld, int row, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    X[(long long)i * ld + row] = 0.0;
+}
+cudaError_t zero_row(double* X, long long ld, int row, int n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  { count_launch(); k_zero_row<<<(n + 255) / 256, 256, 0, st>>>(X, ld, row, n); }
+  return cudaGetLastError();
+}
+
+}  // namespace pdep

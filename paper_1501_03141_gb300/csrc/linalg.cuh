@@ -1,0 +1,117 @@
+// Dense linear algebra and vector kernels used by the Sternheimer CG, the
+// Davidson iteration and the setup eigensolver.  All matrices are
+// column-major; a block of vectors stored one per row of a [n][ld] array is
+// the column-major ld x n matrix whose columns are the vectors.
+#pragma once
+
+#include "common.cuh"
+
+namespace pdep {
+
+// C[m x n] = alpha * op(A)[m x k] * B[k x n] + beta * C, op(A) = A^T if transA.
+// Split over k (atomic accumulation) when the tile count is small.
+template <typename R>
+cudaError_t gemm(bool transA, int m, int n, int k, double alpha, const R* A, long long lda,
+                 const R* B, long long ldb, double beta, R* C, long long ldc, cudaStream_t st);
+
+// Symmetric eigendecomposition of the n x n matrix M (lda), FP64:
+// one-sided (Hestenes) Jacobi on M - sigma I (sigma = Gershgorin bound, so
+// the shifted matrix is negative definite), Rayleigh quotients with the
+// original M, ascending sort.  W [n] eigenvalues, V [n x n] (ldv) vectors.
+// Work needs 2 n*n + 4 n doubles of device scratch.
+struct EighWork {
+  double* a;      // n*n
+  double* v;      // n*n
+  double* tmp;    // n*n
+  double* w;      // n (unsorted)
+  int* flag;      // 1 int + 1 unsigned (rotation counter)
+};
+cudaError_t eigh(int n, const double* M, long long ldm, double* W, double* V, long long ldv,
+                 EighWork wk, cudaStream_t st, int max_sweeps = 40);
+
+// elementwise and per-column helpers
+template <typename R>
+cudaError_t symmetrize(R* M, int n, long long ld, cudaStream_t st);
+template <typename Rd, typename Rs>
+cudaError_t convert(Rd* dst, long long ldd, const Rs* src, long long lds, int rows, int cols,
+                    cudaStream_t st);
+template <typename R>
+cudaError_t col_norms(const R* X, long long ld, int rows, int cols, double* out, cudaStream_t st);
+template <typename R>
+cudaError_t scale_cols(R* X, long long ld, int rows, int cols, const double* s, int invert,
+                       cudaStream_t st);
+cudaError_t ritz_residual(const double* AX, const double* X, long long ld, int rows, int cols,
+                          const double* theta, double* Rout, cudaStream_t st);
+cudaError_t philox_normal(double* X, long long ld, int rows, int cols, unsigned long long seed,
+                          unsigned long long offset, cudaStream_t st);
+cudaError_t scale_by_isqrt_clamped(double* Q, long long ldq, int n, const double* d, double dmin,
+                                   int* keep, cudaStream_t st);
+cudaError_t fill_zero(void* p, size_t bytes, cudaStream_t st);
+
+// Per-RHS preconditioned CG kernels (one CTA per RHS vector).
+// State of one RHS: x, r, p (length n_pw, stride ld), scalars in CgScal.
+struct CgScal {
+  double rz;      // r . K r
+  double bnorm;   // ||b||
+  double rnorm;   // ||r||
+  int iters;
+  int active;     // 1 while unconverged
+};
+template <typename R>
+struct CgArgs {
+  R* x;
+  R* r;
+  R* p;
+  const R* ap;
+  long long ld;
+  int n_pw;
+  int n_half;
+  int n_rhs;
+  const double* g2;     // |G_k|^2, [n_half]
+  const double* ekin;   // preconditioner energy per occupied state [n_occ]
+  int n_occ;            // rhs index i uses occupied state i % n_occ
+  CgScal* sc;
+  double tol;
+  unsigned* status;
+  int* n_active;        // counter (atomic) of RHS still active after the step
+};
+template <typename R>
+cudaError_t cg_start(const CgArgs<R>& a, const R* b, long long ldb, cudaStream_t st);
+template <typename R>
+cudaError_t cg_step(const CgArgs<R>& a, cudaStream_t st);
+
+// y[:, i] = b[:, i] - y[:, i] (FP64), with per-column norms ||y_i|| / ||b_i||,
+// for every i < n, or for i in list[0..n) when list is given.
+cudaError_t residual_norms(const double* b, long long ldb, double* ap, long long lda, int n_pw,
+                           int n, double* rel, const int* list, cudaStream_t st);
+
+// Ordered list of the RHS with sc[i].active (list[0..count)), one block.
+cudaError_t active_list(const CgScal* sc, int n, int* list, int* count, cudaStream_t st);
+// Ordered list of i with rel[i] > tol.
+cudaError_t unconverged_list(const double* rel, double tol, int n, int* list, int* count,
+                             cudaStream_t st);
+
+// Mixed-precision refinement: for i with rel[i] > tol, rn[i] = ||r64_i|| and
+// r32_i = r64_i / rn[i]; otherwise rn[i] = 0 and r32_i = 0.
+cudaError_t refine_prepare(const double* r64, long long ld64, int n_pw, int n, const double* rel,
+                           double tol, float* r32, long long ld32, double* rn, cudaStream_t st);
+// x64_i += rn[i] * d32_i
+cudaError_t refine_accumulate(double* x64, long long ld64, const float* d32, long long ld32,
+                              int n_pw, int n, const double* rn, cudaStream_t st);
+
+// Kinetic energy sum_k |G_k|^2/2 (x_2k^2 + x_2k+1^2) of each column.
+cudaError_t kinetic_energy(const double* X, long long ld, int n_half, int n, const double* g2,
+                           double* out, cudaStream_t st);
+// T_i <- K(|G|^2/2 / E_i) T_i with the Teter-Payne-Allan K.
+cudaError_t precondition_tpa(double* T, long long ld, int n_pw, int n_half, int n,
+                             const double* g2, const double* ekin, cudaStream_t st);
+// Y[:, i] = X[:, idx[i]]
+cudaError_t gather_cols(const double* X, long long ldx, double* Y, long long ldy, int rows,
+                        const int* idx, int n, cudaStream_t st);
+// X[comp[i], i] = 1 plus amp * Philox normal noise on every component
+cudaError_t unit_start(double* X, long long ld, int rows, const int* comp, int n, double amp,
+                       unsigned long long seed, cudaStream_t st);
+// X[row, i] = 0 for every column i (e.g. the G = 0 slot of PDEP vectors)
+cudaError_t zero_row(double* X, long long ld, int row, int n, cudaStream_t st);
+
+}  // namespace pdep

@@ -1,0 +1,116 @@
+// Kernel profiler of the library (see profile.cuh and pdep_profile in pdep.h).
+#include <atomic>
+#include <cstring>
+#include <vector>
+
+#include "profile.cuh"
+
+namespace pdep {
+
+namespace {
+struct Rec {
+  int cls;
+  cudaEvent_t a, b;
+  double flops, bytes;
+};
+struct Acc {
+  long long launches = 0;
+  double ms = 0, flops = 0, bytes = 0;
+};
+const char* kNames[PDEP_PROFILE_CLASSES] = {"cols_f64", "cols_f32", "slab_f64", "slab_f32",
+                                            "gemm_f64", "gemm_f32", "cg_f64",   "cg_f32",
+                                            "eigh",     "other"};
+struct Profiler {
+  bool on = false;
+  std::atomic<long long> launches{0};
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> pool;
+  Acc acc[PDEP_PROFILE_CLASSES];
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void resolve() {
+    for (Rec& r : pending) {
+      float ms = 0.f;
+      if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+        Acc& a = acc[r.cls];
+        a.launches += 1;
+        a.ms += ms;
+        a.flops += r.flops;
+        a.bytes += r.bytes;
+      } else {
+        cudaGetLastError();
+      }
+      pool.push_back(r.a);
+      pool.push_back(r.b);
+    }
+    pending.clear();
+  }
+};
+Profiler& prof() {
+  static Profiler p;
+  return p;
+}
+}  // namespace
+
+void count_launch() {
+  Profiler& p = prof();
+  if (p.on) p.launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+ProfScope::ProfScope(int c, cudaStream_t s, double f, double b)
+    : cls(c), st(s), flops(f), bytes(b), slot(-1) {
+  Profiler& p = prof();
+  if (!p.on) return;
+  if (p.pending.size() >= 8192) p.resolve();
+  Rec r;
+  r.cls = c;
+  r.a = p.get();
+  r.b = p.get();
+  r.flops = f;
+  r.bytes = b;
+  cudaEventRecord(r.a, s);
+  p.pending.push_back(r);
+  slot = (int)p.pending.size() - 1;
+}
+
+ProfScope::~ProfScope() {
+  Profiler& p = prof();
+  if (!p.on || slot < 0 || slot >= (int)p.pending.size()) return;
+  cudaEventRecord(p.pending[slot].b, st);
+}
+
+}  // namespace pdep
+
+extern "C" int pdep_profile(int enable, pdep_profile_t* out) {
+  using namespace pdep;
+  Profiler& p = prof();
+  if (enable) {
+    p.resolve();
+    for (auto& a : p.acc) a = Acc();
+    p.launches = 0;
+    p.on = true;
+    return PDEP_OK;
+  }
+  p.resolve();
+  p.on = false;
+  if (out) {
+    memset(out, 0, sizeof(*out));
+    out->launches = p.launches.load();
+    for (int i = 0; i < PDEP_PROFILE_CLASSES; ++i) {
+      strncpy(out->cls[i].name, kNames[i], sizeof(out->cls[i].name) - 1);
+      out->cls[i].launches = p.acc[i].launches;
+      out->cls[i].ms = p.acc[i].ms;
+      out->cls[i].flops = p.acc[i].flops;
+      out->cls[i].bytes = p.acc[i].bytes;
+    }
+  }
+  return PDEP_OK;
+}

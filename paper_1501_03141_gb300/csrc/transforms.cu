@@ -1,0 +1,540 @@
+// Plane-wave sphere <-> grid transforms (see transforms.cuh for the scheme).
+#include "fft.cuh"
+#include "transforms.cuh"
+#include "profile.cuh"
+
+namespace pdep {
+
+
+cudaError_t upload_local_twiddles() {
+  static const int sizes[] = {6, 8, 10, 12, 16, 20, 24, 32, 48, 64};
+  double2 hd[LOCAL_TW_SIZE];
+  float2 hf[LOCAL_TW_SIZE];
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int M : sizes) {
+    int off = local_tw_offset(M);
+    for (int j = 0; j < M; ++j) {
+      double a = two_pi * (double)j / (double)M;
+      hd[off + j] = make_double2(cos(a), sin(a));
+      hf[off + j] = make_float2((float)cos(a), (float)sin(a));
+    }
+  }
+  cudaError_t e = cudaMemcpyToSymbol(c_local_tw_d, hd, sizeof(hd));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(c_local_tw_f, hf, sizeof(hf));
+}
+
+// lanes per line for each supported length (N / TPL registers per lane)
+template <int N>
+struct Tpl;
+template <> struct Tpl<24> { static constexpr int v = 2; };
+template <> struct Tpl<32> { static constexpr int v = 4; };
+template <> struct Tpl<40> { static constexpr int v = 4; };
+template <> struct Tpl<48> { static constexpr int v = 4; };
+template <> struct Tpl<64> { static constexpr int v = 4; };
+template <> struct Tpl<192> { static constexpr int v = 8; };
+
+bool grid_supported(int N1, int N2, int N3) {
+  bool n1 = (N1 == 24 || N1 == 32 || N1 == 40 || N1 == 48 || N1 == 64);
+  bool cube = (N2 == N3) && (N2 == 24 || N2 == 32 || N2 == 40 || N2 == 48 || N2 == 64);
+  bool slab = (N2 == 64 && N3 == 192);
+  return n1 && (cube || slab);
+}
+
+static __device__ __forceinline__ int iabs(int a) { return a < 0 ? -a : a; }
+
+template <typename R>
+__device__ __forceinline__ cpx<R> zero() { return mk(R(0), R(0)); }
+
+template <typename R>
+__device__ __forceinline__ R coef_of(int kind, const double* __restrict__ g2, int k) {
+  if (kind == COEF_SQRT_COULOMB) return (R)sqrt(12.566370614359172953850573533118 / g2[k]);
+  return R(1);
+}
+
+// ---------------------------------------------------------------------------
+// column pass: sphere -> x-lines (inverse transform, S = +1)
+// ---------------------------------------------------------------------------
+template <typename R, int N1>
+__global__ void __launch_bounds__(128) k_cols_fwd(SphereDev<R> s, const R* __restrict__ x,
+                                                  long long ldx, ItemMap map, int n_items,
+                                                  int coef, cpx<R>* __restrict__ b1) {
+  constexpr int TPL = Tpl<N1>::v;
+  constexpr int M = N1 / TPL;
+  const int t = threadIdx.x & (TPL - 1);
+  const long long g = (long long)blockIdx.x * (blockDim.x / TPL) + threadIdx.x / TPL;
+  const long long total = (long long)n_items * s.n_ucol;
+  const bool active = g < total;
+  const int item = active ? (int)(g / s.n_ucol) : 0;
+  const int uc = active ? (int)(g - (long long)item * s.n_ucol) : 0;
+  const UCol c = s.ucol[uc];
+  const bool self = (c.col == c.mcol);
+  const int ia = map.vec(item, 0), ib = map.vec(item, 1);
+  const R* xa = (active && ia >= 0) ? x + (long long)ia * ldx : nullptr;
+  const R* xb = (active && ib >= 0) ? x + (long long)ib * ldx : nullptr;
+  const R rs2 = R(0.70710678118654752440084436210485);
+
+  cpx<R> v0[M], v1[M];
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    v0[i] = zero<R>();
+    v1[i] = zero<R>();
+    const int n1 = freq_of(pos_a<N1, TPL>(t, i), N1);
+    if (!active) continue;
+    if (!self) {
+      if (iabs(n1) <= c.R1) {
+        // line c at n1: member k;  mirror line at n1: conj of member k'
+        const int k = c.h0 + n1 + c.R1;
+        const int k2 = c.h0 - n1 + c.R1;
+        const R w = coef_of<R>(coef, s.g2, k) * rs2;
+        const R w2 = coef_of<R>(coef, s.g2, k2) * rs2;
+        cpx<R> A = xa ? mk(xa[2 * k] * w, xa[2 * k + 1] * w) : zero<R>();
+        cpx<R> B = xb ? mk(xb[2 * k] * w, xb[2 * k + 1] * w) : zero<R>();
+        v0[i] = mk(A.x - B.y, A.y + B.x);
+        cpx<R> A2 = xa ? mk(xa[2 * k2] * w2, xa[2 * k2 + 1] * w2) : zero<R>();
+        cpx<R> B2 = xb ? mk(xb[2 * k2] * w2, xb[2 * k2 + 1] * w2) : zero<R>();
+        v1[i] = mk(A2.x + B2.y, B2.x - A2.y);
+      }
+    } else {
+      if (n1 == 0) {
+        const R w = (coef == COEF_ONE) ? R(1) : R(0);
+        const int k0 = 2 * s.n_half;
+        v0[i] = mk(xa ? xa[k0] * w : R(0), xb ? xb[k0] * w : R(0));
+      } else if (iabs(n1) <= c.R1) {
+        const int k = c.h0 + iabs(n1) - 1;
+        const R w = coef_of<R>(coef, s.g2, k) * rs2;
+        cpx<R> A = xa ? mk(xa[2 * k] * w, xa[2 * k + 1] * w) : zero<R>();
+        cpx<R> B = xb ? mk(xb[2 * k] * w, xb[2 * k + 1] * w) : zero<R>();
+        v0[i] = n1 > 0 ? mk(A.x - B.y, A.y + B.x) : mk(A.x + B.y, B.x - A.y);
+      }
+    }
+  }
+  fft_a2b<R, N1, TPL, +1>(v0, t, s.tw1);
+  fft_a2b<R, N1, TPL, +1>(v1, t, s.tw1);
+  if (!active) return;
+  cpx<R>* base = b1 + (long long)item * N1 * s.n_col;
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    const int i1 = pos_b<N1, TPL>(t, i);
+    base[(long long)i1 * s.n_col + c.col] = v0[i];
+    if (!self) base[(long long)i1 * s.n_col + c.mcol] = v1[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// column pass back: x-lines -> sphere (forward transform, S = -1), Hermitian
+// unpacking of the two real fields and the epilogue
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void write_out(const Epilogue<R>& ep, int vec, int j, R val, R coefv,
+                                          R diag) {
+  R* y = ep.y + (long long)vec * ep.ldy;
+  R r = (R)ep.scale * coefv * val;
+  if (ep.x_in) {
+    const R sh = ep.shift ? (R)ep.shift[vec % ep.shift_period] : R(0);
+    r += (diag + sh) * ep.x_in[(long long)vec * ep.ldx + j];
+  }
+  if (ep.beta != 0.0) r += (R)ep.beta * y[j];
+  y[j] = r;
+}
+
+template <typename R, int N1>
+__global__ void __launch_bounds__(128) k_cols_bwd(SphereDev<R> s, const cpx<R>* __restrict__ b1,
+                                                  ItemMap map, int n_items, Epilogue<R> ep) {
+  constexpr int TPL = Tpl<N1>::v;
+  constexpr int M = N1 / TPL;
+  const int lane = threadIdx.x & 31;
+  const int t = threadIdx.x & (TPL - 1);
+  const long long g = (long long)blockIdx.x * (blockDim.x / TPL) + threadIdx.x / TPL;
+  const long long total = (long long)n_items * s.n_ucol;
+  const bool active = g < total;
+  const int item = active ? (int)(g / s.n_ucol) : 0;
+  const int uc = active ? (int)(g - (long long)item * s.n_ucol) : 0;
+  const UCol c = s.ucol[uc];
+  const bool self = (c.col == c.mcol);
+
+  const cpx<R>* base = b1 + (long long)item * N1 * s.n_col;
+  cpx<R> v0[M], v1[M];
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    const int i1 = pos_b<N1, TPL>(t, i);
+    v0[i] = active ? base[(long long)i1 * s.n_col + c.col] : zero<R>();
+    v1[i] = (active && !self) ? base[(long long)i1 * s.n_col + c.mcol] : zero<R>();
+  }
+  fft_b2a<R, N1, TPL, -1>(v0, t, s.tw1);
+  fft_b2a<R, N1, TPL, -1>(v1, t, s.tw1);
+
+  const int src = (lane & ~(TPL - 1)) | ((TPL - t) & (TPL - 1));
+  const int ia = map.vec(item, 0), ib = map.vec(item, 1);
+  const R rs2 = R(0.70710678118654752440084436210485);
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    // value of the mirror line at position (N1 - p) mod N1
+    cpx<R> send = self ? v0[M - 1 - i] : v1[M - 1 - i];
+    cpx<R> dm = shfl_idx(send, src);
+    if (t == 0) dm = self ? v0[(M - i) % M] : v1[(M - i) % M];
+    if (!active) continue;
+    const int n1 = freq_of(pos_a<N1, TPL>(t, i), N1);
+    int k = -1;
+    if (!self) {
+      if (iabs(n1) <= c.R1) k = c.h0 + n1 + c.R1;
+    } else if (n1 > 0 && n1 <= c.R1) {
+      k = c.h0 + n1 - 1;
+    }
+    const cpx<R> d = v0[i];
+    if (k >= 0) {
+      const cpx<R> sa = d + conj(dm);   // 2 Va
+      const cpx<R> sb = d - conj(dm);   // 2 i Vb
+      const R cf = coef_of<R>(ep.coef, s.g2, k);
+      const R dg = (R)(0.5 * ep.kin * s.g2[k]);
+      if (ia >= 0) {
+        write_out(ep, ia, 2 * k, rs2 * sa.x, cf, dg);
+        write_out(ep, ia, 2 * k + 1, rs2 * sa.y, cf, dg);
+      }
+      if (ib >= 0) {
+        write_out(ep, ib, 2 * k, rs2 * sb.y, cf, dg);
+        write_out(ep, ib, 2 * k + 1, -rs2 * sb.x, cf, dg);
+      }
+    } else if (self && n1 == 0) {
+      const R cf = (ep.coef == COEF_ONE) ? R(1) : R(0);
+      const int j0 = 2 * s.n_half;
+      if (ia >= 0) write_out(ep, ia, j0, d.x, cf, R(0));
+      if (ib >= 0) write_out(ep, ib, j0, d.y, cf, R(0));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// slab pass: one x-plane i1 of one item (or of one group for DENSITY)
+// ---------------------------------------------------------------------------
+template <typename R, int N2>
+__device__ __forceinline__ void y_inverse(const SphereDev<R>& s, const cpx<R>* S1, cpx<R>* T2) {
+  constexpr int TL = Tpl<N2>::v;
+  constexpr int M = N2 / TL;
+  const int nslot = 2 * s.R3 + 1;
+  const int per = blockDim.x / TL;
+  const int t = threadIdx.x & (TL - 1);
+  for (int base = 0; base < nslot; base += per) {
+    const int sl = base + threadIdx.x / TL;
+    const bool act = sl < nslot;
+    const int2 info = act ? s.slot[sl] : make_int2(-1, 0);
+    cpx<R> v[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      const int n2 = freq_of(pos_a<N2, TL>(t, i), N2);
+      v[i] = (act && iabs(n2) <= info.x) ? S1[info.y + n2 + info.x] : zero<R>();
+    }
+    fft_a2b<R, N2, TL, +1>(v, t, s.tw2);
+    if (act) {
+#pragma unroll
+      for (int i = 0; i < M; ++i) T2[sl * N2 + pos_b<N2, TL>(t, i)] = v[i];
+    }
+  }
+}
+
+template <typename R, int N2>
+__device__ __forceinline__ void y_forward(const SphereDev<R>& s, const cpx<R>* T2, cpx<R>* S1) {
+  constexpr int TL = Tpl<N2>::v;
+  constexpr int M = N2 / TL;
+  const int nslot = 2 * s.R3 + 1;
+  const int per = blockDim.x / TL;
+  const int t = threadIdx.x & (TL - 1);
+  for (int base = 0; base < nslot; base += per) {
+    const int sl = base + threadIdx.x / TL;
+    const bool act = sl < nslot;
+    const int2 info = act ? s.slot[sl] : make_int2(-1, 0);
+    cpx<R> v[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) v[i] = act ? T2[sl * N2 + pos_b<N2, TL>(t, i)] : zero<R>();
+    fft_b2a<R, N2, TL, -1>(v, t, s.tw2);
+    if (act) {
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        const int n2 = freq_of(pos_a<N2, TL>(t, i), N2);
+        if (iabs(n2) <= info.x) S1[info.y + n2 + info.x] = v[i];
+      }
+    }
+  }
+}
+
+// largest block a slab of this shape launches with: every z-line (N2 lines)
+// or every y-line (at most N3/2 + 1 planes) in one round
+template <int N2, int N3>
+struct SlabThreads {
+  static constexpr int z = N2 * Tpl<N3>::v;
+  static constexpr int y = (N3 / 2 + 1) * Tpl<N2>::v;
+  static constexpr int v = (((z > y ? z : y) + 31) / 32) * 32;
+};
+
+template <typename R, int N2, int N3>
+__global__ void __launch_bounds__(SlabThreads<N2, N3>::v, 1) k_slab(SphereDev<R> s, SlabArgs<R> a) {
+  constexpr int TL3 = Tpl<N3>::v;
+  constexpr int M3 = N3 / TL3;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<R>* S1 = reinterpret_cast<cpx<R>*>(smem_raw);
+  cpx<R>* T2 = S1 + s.n_col;
+  const int i1 = blockIdx.y;
+  const int R3 = s.R3;
+  const int t3 = threadIdx.x & (TL3 - 1);
+  const int zper = blockDim.x / TL3;
+  const long long plane = (long long)i1 * N2 * N3;
+
+  if (a.mode == SLAB_DENSITY) {
+    // one group (e.g. one perturbation j) per block; z-lines in a single round
+    const int grp = blockIdx.x;
+    const int i2 = threadIdx.x / TL3;
+    const bool act = i2 < N2;
+    R acc[M3];
+#pragma unroll
+    for (int i = 0; i < M3; ++i) acc[i] = R(0);
+    for (int w = 0; w < a.map.items_per_group; ++w) {
+      const int item = grp * a.map.items_per_group + w;
+      const cpx<R>* row = a.b1 + ((long long)item * s.N1 + i1) * s.n_col;
+      for (int j = threadIdx.x; j < s.n_col; j += blockDim.x) S1[j] = row[j];
+      __syncthreads();
+      y_inverse<R, N2>(s, S1, T2);
+      __syncthreads();
+      cpx<R> v[M3];
+#pragma unroll
+      for (int i = 0; i < M3; ++i) {
+        const int n3 = freq_of(pos_a<N3, TL3>(t3, i), N3);
+        v[i] = (act && iabs(n3) <= R3) ? T2[(n3 + R3) * N2 + i2] : zero<R>();
+      }
+      fft_a2b<R, N3, TL3, +1>(v, t3, s.tw3);
+      const int va = 2 * w, vb = 2 * w + 1;
+      if (act) {
+        const R* ga = a.src.g + (long long)va * a.src.g_stride + plane + (long long)i2 * N3;
+        const R* gb = vb < a.map.vecs_per_group
+                          ? a.src.g + (long long)vb * a.src.g_stride + plane + (long long)i2 * N3
+                          : nullptr;
+#pragma unroll
+        for (int i = 0; i < M3; ++i) {
+          const int i3 = pos_b<N3, TL3>(t3, i);
+          acc[i] += v[i].x * ga[i3];
+          if (gb) acc[i] += v[i].y * gb[i3];
+        }
+      }
+      __syncthreads();
+    }
+    if (act) {
+      R* o = a.out + (long long)grp * a.out_stride + plane + (long long)i2 * N3;
+#pragma unroll
+      for (int i = 0; i < M3; ++i) o[pos_b<N3, TL3>(t3, i)] = acc[i] * (R)a.out_scale;
+    }
+    return;
+  }
+
+  const int item = blockIdx.x;
+  cpx<R>* row = a.b1 + ((long long)item * s.N1 + i1) * s.n_col;
+  if (a.mode != SLAB_FROM_GRID) {
+    for (int j = threadIdx.x; j < s.n_col; j += blockDim.x) S1[j] = row[j];
+    __syncthreads();
+    y_inverse<R, N2>(s, S1, T2);
+    __syncthreads();
+  }
+
+  for (int base = 0; base < N2; base += zper) {
+    const int i2 = base + threadIdx.x / TL3;
+    const bool act = i2 < N2;
+    cpx<R> v[M3];
+    if (a.mode == SLAB_FROM_GRID) {
+      const int grp = item / a.map.items_per_group;
+      const int w = item - grp * a.map.items_per_group;
+      const int va = 2 * w, vb = 2 * w + 1;
+      const long long off = plane + (long long)i2 * N3;
+      const R* f = (act && a.src.f) ? a.src.f + (long long)grp * a.src.f_stride + off : nullptr;
+      const R* ga = act ? a.src.g + (long long)va * a.src.g_stride + off : nullptr;
+      const R* gb = (act && vb < a.map.vecs_per_group) ? a.src.g + (long long)vb * a.src.g_stride + off
+                                                        : nullptr;
+#pragma unroll
+      for (int i = 0; i < M3; ++i) {
+        const int i3 = pos_b<N3, TL3>(t3, i);
+        const R fv = f ? f[i3] : R(1);
+        v[i] = act ? mk(fv * ga[i3], gb ? fv * gb[i3] : R(0)) : zero<R>();
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < M3; ++i) {
+        const int n3 = freq_of(pos_a<N3, TL3>(t3, i), N3);
+        v[i] = (act && iabs(n3) <= R3) ? T2[(n3 + R3) * N2 + i2] : zero<R>();
+      }
+      fft_a2b<R, N3, TL3, +1>(v, t3, s.tw3);
+      if (a.mode == SLAB_TO_GRID) {
+        if (act) {
+          const int ia = a.map.vec(item, 0), ib = a.map.vec(item, 1);
+          const long long off = plane + (long long)i2 * N3;
+          R* oa = ia >= 0 ? a.out + (long long)ia * a.out_stride + off : nullptr;
+          R* ob = ib >= 0 ? a.out + (long long)ib * a.out_stride + off : nullptr;
+#pragma unroll
+          for (int i = 0; i < M3; ++i) {
+            const int i3 = pos_b<N3, TL3>(t3, i);
+            if (oa) oa[i3] = v[i].x * (R)a.out_scale;
+            if (ob) ob[i3] = v[i].y * (R)a.out_scale;
+          }
+        }
+        continue;
+      }
+      // SLAB_HPSI: multiply by the local potential on the grid
+      const R* vr = a.v + plane + (long long)i2 * N3;
+#pragma unroll
+      for (int i = 0; i < M3; ++i) v[i] = scale(v[i], act ? vr[pos_b<N3, TL3>(t3, i)] : R(0));
+    }
+    fft_b2a<R, N3, TL3, -1>(v, t3, s.tw3);
+    if (act) {
+#pragma unroll
+      for (int i = 0; i < M3; ++i) {
+        const int n3 = freq_of(pos_a<N3, TL3>(t3, i), N3);
+        if (iabs(n3) <= R3) T2[(n3 + R3) * N2 + i2] = v[i];
+      }
+    }
+  }
+  if (a.mode == SLAB_TO_GRID) return;
+  __syncthreads();
+  y_forward<R, N2>(s, T2, S1);
+  __syncthreads();
+  for (int j = threadIdx.x; j < s.n_col; j += blockDim.x) row[j] = S1[j];
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+size_t slab_smem_bytes(int n_col, int R3, int N2, size_t elem) {
+  return (size_t)(n_col + (2 * R3 + 1) * N2) * 2 * elem;
+}
+
+template <int N>
+static int threads_for(int lines) {
+  int n = lines * Tpl<N>::v;
+  return ((n + 31) / 32) * 32;
+}
+
+template <typename R, int N1>
+static cudaError_t cols_fwd_impl(const SphereDev<R>& s, const R* x, long long ldx, ItemMap map,
+                                 int n_items, int coef, cpx<R>* b1, cudaStream_t st) {
+  const int per = 128 / Tpl<N1>::v;
+  const long long total = (long long)n_items * s.n_ucol;
+  if (total == 0) return cudaSuccess;
+  const long long blocks = (total + per - 1) / per;
+  // one x-line per column (n_col lines per item): 5 L log2 L flops each
+  const double lines = (double)n_items * s.n_col;
+  ProfScope ps(sizeof(R) == 8 ? PC_COLS_F64 : PC_COLS_F32, st, lines * 5.0 * N1 * log2((double)N1),
+               (double)n_items * 2.0 * s.n_pw * sizeof(R) + lines * N1 * 2.0 * sizeof(R));
+  count_launch();
+  k_cols_fwd<R, N1><<<(unsigned)blocks, 128, 0, st>>>(s, x, ldx, map, n_items, coef, b1);
+  return cudaGetLastError();
+}
+
+template <typename R, int N1>
+static cudaError_t cols_bwd_impl(const SphereDev<R>& s, const cpx<R>* b1, ItemMap map,
+                                 int n_items, const Epilogue<R>& ep, cudaStream_t st) {
+  const int per = 128 / Tpl<N1>::v;
+  const long long total = (long long)n_items * s.n_ucol;
+  if (total == 0) return cudaSuccess;
+  const long long blocks = (total + per - 1) / per;
+  const double lines = (double)n_items * s.n_col;
+  const double vecs = (double)n_items * 2.0 * s.n_pw * sizeof(R);
+  ProfScope ps(sizeof(R) == 8 ? PC_COLS_F64 : PC_COLS_F32, st, lines * 5.0 * N1 * log2((double)N1),
+               lines * N1 * 2.0 * sizeof(R) + vecs * (1.0 + (ep.x_in ? 1.0 : 0.0) +
+                                                      (ep.beta != 0.0 ? 1.0 : 0.0)));
+  count_launch();
+  k_cols_bwd<R, N1><<<(unsigned)blocks, 128, 0, st>>>(s, b1, map, n_items, ep);
+  return cudaGetLastError();
+}
+
+template <typename R, int N2, int N3>
+static cudaError_t slab_impl(const SphereDev<R>& s, const SlabArgs<R>& a, cudaStream_t st) {
+  int nt = threads_for<N3>(N2);
+  int ny = threads_for<N2>(2 * s.R3 + 1);
+  if (a.mode != SLAB_DENSITY && ny > nt) nt = ny;
+  if (nt > SlabThreads<N2, N3>::v) return cudaErrorInvalidConfiguration;
+  const size_t smem = slab_smem_bytes(s.n_col, s.R3, N2, sizeof(R));
+  auto kern = k_slab<R, N2, N3>;
+  static bool attr_set = false;  // per instantiation; the limit is raised once
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int gx = a.mode == SLAB_DENSITY ? a.n_items / a.map.items_per_group : a.n_items;
+  if (gx == 0) return cudaSuccess;
+  dim3 grid(gx, s.N1);
+  // algorithmic work: y-lines over the |n3| <= R3 planes and z-lines over the
+  // N2 rows of each x-plane, 5 L log2 L flops per complex line FFT
+  const double ylines = (double)(2 * s.R3 + 1), zlines = (double)N2;
+  const double fy = 5.0 * N2 * log2((double)N2), fz = 5.0 * N3 * log2((double)N3);
+  const double planes = (double)a.n_items * s.N1;
+  const double colb = (double)s.n_col * 2.0 * sizeof(R);     // one plane of B1
+  const double gridb = (double)N2 * N3 * sizeof(R);          // one plane of a real grid
+  double fl = 0, by = 0;
+  switch (a.mode) {
+    case SLAB_HPSI: fl = planes * (2 * ylines * fy + 2 * zlines * fz + 2.0 * N2 * N3);
+                    by = planes * 2 * colb + s.N1 * gridb; break;
+    case SLAB_TO_GRID: fl = planes * (ylines * fy + zlines * fz);
+                       by = planes * (colb + 2 * gridb); break;
+    case SLAB_FROM_GRID: fl = planes * (ylines * fy + zlines * fz + 3.0 * N2 * N3);
+                         by = planes * (colb + 3 * gridb); break;
+    case SLAB_DENSITY: fl = planes * (ylines * fy + zlines * fz + 4.0 * N2 * N3);
+                       by = planes * (colb + 2 * gridb) + (double)gx * s.N1 * gridb; break;
+  }
+  ProfScope ps(sizeof(R) == 8 ? PC_SLAB_F64 : PC_SLAB_F32, st, fl, by);
+  count_launch();
+  kern<<<grid, nt, smem, st>>>(s, a);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_cols_fwd(const SphereDev<R>& s, const R* x, long long ldx, ItemMap map,
+                            int n_items, int coef, cpx<R>* b1, cudaStream_t st) {
+  switch (s.N1) {
+    case 24: return cols_fwd_impl<R, 24>(s, x, ldx, map, n_items, coef, b1, st);
+    case 32: return cols_fwd_impl<R, 32>(s, x, ldx, map, n_items, coef, b1, st);
+    case 40: return cols_fwd_impl<R, 40>(s, x, ldx, map, n_items, coef, b1, st);
+    case 48: return cols_fwd_impl<R, 48>(s, x, ldx, map, n_items, coef, b1, st);
+    case 64: return cols_fwd_impl<R, 64>(s, x, ldx, map, n_items, coef, b1, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename R>
+cudaError_t launch_cols_bwd(const SphereDev<R>& s, const cpx<R>* b1, ItemMap map, int n_items,
+                            const Epilogue<R>& ep, cudaStream_t st) {
+  switch (s.N1) {
+    case 24: return cols_bwd_impl<R, 24>(s, b1, map, n_items, ep, st);
+    case 32: return cols_bwd_impl<R, 32>(s, b1, map, n_items, ep, st);
+    case 40: return cols_bwd_impl<R, 40>(s, b1, map, n_items, ep, st);
+    case 48: return cols_bwd_impl<R, 48>(s, b1, map, n_items, ep, st);
+    case 64: return cols_bwd_impl<R, 64>(s, b1, map, n_items, ep, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename R>
+cudaError_t launch_slab(const SphereDev<R>& s, const SlabArgs<R>& a, cudaStream_t st) {
+  if (s.N2 == s.N3) {
+    switch (s.N2) {
+      case 24: return slab_impl<R, 24, 24>(s, a, st);
+      case 32: return slab_impl<R, 32, 32>(s, a, st);
+      case 40: return slab_impl<R, 40, 40>(s, a, st);
+      case 48: return slab_impl<R, 48, 48>(s, a, st);
+      case 64: return slab_impl<R, 64, 64>(s, a, st);
+    }
+  } else if (s.N2 == 64 && s.N3 == 192) {
+    return slab_impl<R, 64, 192>(s, a, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template cudaError_t launch_cols_fwd<double>(const SphereDev<double>&, const double*, long long,
+                                             ItemMap, int, int, cpx<double>*, cudaStream_t);
+template cudaError_t launch_cols_fwd<float>(const SphereDev<float>&, const float*, long long,
+                                            ItemMap, int, int, cpx<float>*, cudaStream_t);
+template cudaError_t launch_cols_bwd<double>(const SphereDev<double>&, const cpx<double>*, ItemMap,
+                                             int, const Epilogue<double>&, cudaStream_t);
+template cudaError_t launch_cols_bwd<float>(const SphereDev<float>&, const cpx<float>*, ItemMap,
+                                            int, const Epilogue<float>&, cudaStream_t);
+template cudaError_t launch_slab<double>(const SphereDev<double>&, const SlabArgs<double>&,
+                                         cudaStream_t);
+template cudaError_t launch_slab<float>(const SphereDev<float>&, const SlabArgs<float>&,
+                                        cudaStream_t);
+
+}  // namespace pdep

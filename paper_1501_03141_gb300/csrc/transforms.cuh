@@ -1,0 +1,120 @@
+// Plane-wave sphere <-> real-space grid transforms at Gamma (declarations).
+//
+// Two real fields a, b (two vectors of the real-coefficient layout) travel
+// through one complex 3D FFT as C = a + i b.  The transform is pruned to the
+// sphere: x-lines exist only for (n2, n3) columns that meet the sphere, y-lines
+// only for the |n3| <= R3 planes, and the z-lines of a fixed-x slab carry the
+// grid values.  Work is split in three launches:
+//   column pass  : x-lines of every column, sphere <-> B1[item][i1][col]
+//   slab pass    : for one (item, i1): y-lines and z-lines in shared memory,
+//                  optionally with the local potential multiplied in between
+//   column pass back : x-lines back to the sphere, Hermitian unpacking of the
+//                  two real fields and a fused epilogue
+#pragma once
+
+#include "common.cuh"
+
+namespace pdep {
+
+// One upper column (n2, n3) of the half space, with its mirror (-n2, -n3).
+struct UCol {
+  int n2, n3, R1, h0;  // x-extent [-R1, R1]; half index of the first member
+  int col, mcol;       // indices in the full column list (mcol == col for (0,0))
+};
+
+// Device-side description of one system's sphere and grid.
+template <typename R>
+struct SphereDev {
+  int N1, N2, N3, R3;
+  int n_half, n_pw, n_col, n_ucol;
+  const UCol* ucol;         // [n_ucol]
+  const int2* slot;         // [2 R3 + 1]: (R2(n3), first full-column index)
+  const double* g2;         // |G_k|^2, [n_half]
+  const cpx<R>* tw1;        // exp(+2 pi i j/N1), j < N1
+  const cpx<R>* tw2;
+  const cpx<R>* tw3;
+};
+
+// Which real vectors an FFT item packs: vectors are grouped; item w of a
+// group takes members 2w and 2w+1 (the second may be absent).
+struct ItemMap {
+  int vecs_per_group;
+  int items_per_group;
+  const int* list = nullptr;  // optional explicit vector list (pairs of entries)
+  int n_list = 0;
+  __host__ __device__ int vec(int item, int slot) const {
+    if (list) {
+      int idx = 2 * item + slot;
+      return idx < n_list ? list[idx] : -1;
+    }
+    int g = item / items_per_group;
+    int w = item - g * items_per_group;
+    int idx = 2 * w + slot;
+    return idx < vecs_per_group ? g * vecs_per_group + idx : -1;
+  }
+};
+
+// Per-component multiplier applied to sphere data on the way in / out.
+enum CoefKind : int { COEF_ONE = 0, COEF_SQRT_COULOMB = 1 };
+
+// Epilogue of the column pass back:
+//   y = scale * coef(G) * (transform) + (kin * |G|^2/2 + shift[vec]) * x_in
+//       (+ beta * y_old)
+template <typename R>
+struct Epilogue {
+  R* y;                 // output vectors (real layout)
+  long long ldy;
+  const R* x_in;        // vectors for the diagonal term (may be null)
+  long long ldx;
+  const double* shift;  // per vector, indexed vec % shift_period (may be null)
+  int shift_period;
+  double scale;
+  double kin;           // 0 or 1
+  double beta;          // 0: overwrite
+  int coef;             // CoefKind
+};
+
+// Grid source of the grid -> sphere slab pass: field = f(r) * (ga(r) + i gb(r))
+template <typename R>
+struct GridSrc {
+  const R* f;          // may be null (f = 1)
+  long long f_stride;  // per group (item_map group)
+  const R* g;          // ga/gb are vectors of g with stride g_stride
+  long long g_stride;
+};
+
+enum SlabMode : int {
+  SLAB_HPSI = 0,       // cols -> grid -> *V -> cols
+  SLAB_TO_GRID = 1,    // cols -> grid, written as two real fields
+  SLAB_FROM_GRID = 2,  // grid (GridSrc) -> cols
+  SLAB_DENSITY = 3,    // cols -> grid, out += Re*ga + Im*gb over items of a group
+};
+
+template <typename R>
+struct SlabArgs {
+  int mode;
+  cpx<R>* b1;            // [n_items][N1][n_col]
+  int n_items;
+  const R* v;            // local potential [N_r] (HPSI)
+  R* out;                // TO_GRID: two fields per item at vec(item,s)*out_stride
+  long long out_stride;  // DENSITY: group g writes out + g*out_stride
+  double out_scale;
+  GridSrc<R> src;        // FROM_GRID / DENSITY (g = occupied grids)
+  ItemMap map;
+};
+
+// Host launchers (stream-ordered; no synchronisation).
+template <typename R>
+cudaError_t launch_cols_fwd(const SphereDev<R>& s, const R* x, long long ldx, ItemMap map,
+                            int n_items, int coef, cpx<R>* b1, cudaStream_t st);
+template <typename R>
+cudaError_t launch_slab(const SphereDev<R>& s, const SlabArgs<R>& a, cudaStream_t st);
+template <typename R>
+cudaError_t launch_cols_bwd(const SphereDev<R>& s, const cpx<R>* b1, ItemMap map, int n_items,
+                            const Epilogue<R>& ep, cudaStream_t st);
+
+bool grid_supported(int N1, int N2, int N3);
+cudaError_t upload_local_twiddles();
+size_t slab_smem_bytes(int n_col, int R3, int N2, size_t elem);
+
+}  // namespace pdep

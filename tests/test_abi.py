@@ -1,0 +1,52 @@
+"""The C-ABI library builds, loads and exports every symbol of include/pdep.h.
+
+No compute call is made: this runs without a GPU.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "pdep.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?(?:int|void|char)\s*\*?\s*(\w+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1501_03141_gb300 import _abi, build
+    build.build()
+    return _abi.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("pdep_setup", "chi0_apply", "sternheimer_solve", "pdep_solve",
+                     "pdep_destroy"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1501_03141_gb300 import _abi
+    declared = _declared()
+    assert sorted(_abi.EXPORTS) == declared
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_host_only_calls(lib):
+    from paper_1501_03141_gb300 import _abi
+    o = _abi.pdep_options()
+    lib.pdep_default_options(ctypes.byref(o))
+    assert o.precision == _abi.PDEP_FP64 and o.cg_tol == 1e-10
+    assert lib.pdep_status_string(_abi.PDEP_ERR_NO_GAP).decode() == "no gap at the Fermi level"
+    h = ctypes.c_void_p()
+    # a null descriptor is rejected before any device work
+    assert lib.pdep_setup(None, 0, None, None, ctypes.byref(h)) == _abi.PDEP_ERR_INVALID_ARG
+    assert not h.value
