@@ -174,6 +174,32 @@ int pdep_solve(pdep_ctx* ctx, int sys, const double* phi0, double* eigvals, doub
 int pdep_apply_hamiltonian(pdep_ctx* ctx, int sys, const double* x, int n, double* y,
                            int precision, void* stream);
 
+/* y = H x like pdep_apply_hamiltonian (FP64), for callers that cannot
+ * allocate device memory when they need it: code issuing work while a CUDA
+ * graph is being captured on its stream, code running in a host callback or
+ * an allocator hook, and embedders whose memory pool owns the whole device.
+ * The paper has no counterpart to this entry point.
+ *   - It allocates nothing: no cudaMalloc/cudaFree, no allocating library
+ *     call, no staging.  x [n][n_pw] and y [n][n_pw] must be device buffers
+ *     (host pointers are rejected with PDEP_ERR_INVALID_ARG).
+ *   - Its transform scratch is one file-scope device array of 16 MiB
+ *     (16777216 bytes), held by every GPU that loads the library until the
+ *     process exits.  Vectors are processed in chunks of
+ *     2 * floor(16 MiB / (N1 * n_col * 16 bytes)) (n_col: x-columns of the
+ *     sphere); a grid whose single chunk does not fit is rejected with
+ *     PDEP_ERR_UNSUPPORTED.
+ *   - The first call on a device looks up the device address of that array
+ *     (cudaGetSymbolAddress, once per device, with the device current); make
+ *     that first call before any stream capture.
+ *   - All calls share the array and it keeps the last call's contents; the
+ *     transforms overwrite every scratch element before reading it, so
+ *     nothing needs clearing.  Calls that overlap on the GPU (other streams,
+ *     other threads) race on the scratch: serialise them.
+ *   - The call only enqueues work on 'stream'; y is complete once the stream
+ *     has been synchronised. */
+int pdep_apply_hamiltonian_noalloc(pdep_ctx* ctx, int sys, const double* x, int n, double* y,
+                                   void* stream);
+
 /* u [n][n_r]: u(r_k) = sum_G c(G) exp(i G.r_k) for n sphere vectors x
  * [n][n_pw] (so the normalised function is Omega^{-1/2} u). */
 int pdep_to_grid(pdep_ctx* ctx, int sys, const double* x, int n, double* u, void* stream);

@@ -32,6 +32,7 @@ EXPORTS = (
     "pdep_default_options", "pdep_setup", "pdep_get_sizes", "pdep_get_occupied",
     "chi0_apply", "sternheimer_solve", "pdep_solve", "pdep_apply_hamiltonian", "pdep_to_grid",
     "pdep_profile", "pdep_destroy", "pdep_status_string", "pdep_last_error",
+    "pdep_apply_hamiltonian_noalloc",
 )
 
 PDEP_PROFILE_CLASSES = 10
@@ -123,6 +124,8 @@ def load(path: str = LIB_PATH):
     lib.pdep_solve.argtypes = [vp, ip, vp, vp, vp, ctypes.POINTER(pdep_stats), vp]
     lib.pdep_apply_hamiltonian.argtypes = [vp, ip, vp, ip, vp, ip, vp]
     lib.pdep_to_grid.argtypes = [vp, ip, vp, ip, vp, vp]
+    lib.pdep_apply_hamiltonian_noalloc.argtypes = [vp, ip, vp, ip, vp, vp]
+    lib.pdep_apply_hamiltonian_noalloc.restype = ip
     lib.pdep_profile.argtypes = [ip, ctypes.POINTER(pdep_profile_t)]
     lib.pdep_profile.restype = ip
     lib.pdep_destroy.argtypes = [vp]

@@ -972,6 +972,18 @@ int solve_one(pdep_ctx* c, int si, const double* phi0, double* eigvals, double* 
 
 }  // namespace
 
+namespace pdep {
+// Sphere description and potential of one system for pdep_apply_hamiltonian_noalloc.
+int noalloc_sphere(pdep_ctx* c, int sys, SphereDev<double>* sd, const double** v, int* n_pw) {
+  RET(check_sys(c, sys));
+  const SysData& s = c->sys[sys];
+  *sd = s.sd;
+  *v = s.d_v;
+  *n_pw = s.n_pw;
+  return PDEP_OK;
+}
+}  // namespace pdep
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
