@@ -2,11 +2,11 @@
  * pdep.h -- C ABI of the GB300 PDEP library (libpdep.so).
  *
  * The library computes the projective dielectric eigendecomposition (PDEP)
- * of Govoni & Galli, "Large scale GW calculations" (Sec. II D, "Projective
+ * of Govoni & Galli, "Large scale GW calculations" (Sec. II C, "Projective
  * dielectric eigenpotential (PDEP) basis set"): the leading eigenpairs of the
  * symmetrised static irreducible polarizability
  *     chi0bar = v^{1/2} chi0 v^{1/2}          (Eq. symmoperator, omega = 0)
- * by a Davidson iteration (Sec. II D; Fig. pdepscheme) in which every
+ * by a Davidson iteration (Sec. II C; Fig. pdepscheme) in which every
  * application of chi0bar is a batch of Sternheimer solves (Eq. stern)
  *     (H - eps_v) P_c dpsi_v = - P_c dV psi_v,   P_c = 1 - sum_v |v><v|,
  * one per occupied state v and perturbation, followed by the density
@@ -122,6 +122,7 @@ typedef struct {
   double max_cg_residual;       /* largest final ||b - A x|| / ||b||, recomputed in FP64 */
   double max_dav_residual;      /* largest final ||chi0bar x - theta x|| / |theta_1| */
   double seconds;               /* wall time of the call */
+  int cg_variant;               /* CG-step launch shape the autotuner chose (-1: untuned) */
 } pdep_stats;
 
 /* Fill *opt with the defaults (FP64, cg_tol 1e-10, dav_tol 1e-8, ...). */
@@ -129,7 +130,7 @@ void pdep_default_options(pdep_options* opt);
 
 /* Build one context for n_sys systems: sphere tables, potential upload and the
  * FP64 setup eigensolve of the n_occ lowest states (the unperturbed occupied
- * states of Sec. II D), with the gap check.  Returns PDEP_ERR_NO_GAP when
+ * states of Sec. II C), with the gap check.  Returns PDEP_ERR_NO_GAP when
  * eps_{n_occ+1} - eps_{n_occ} < gap_min, PDEP_ERR_INVALID_ARG for an
  * unsupported grid (N1 in {24,32,40,48,64}; N2 = N3 in that set, or
  * N2 = 64 with N3 = 192). */
@@ -158,7 +159,7 @@ int chi0_apply(pdep_ctx* ctx, int sys, const double* phi, int n_pert, double* ch
 int sternheimer_solve(pdep_ctx* ctx, int sys, const double* dv_r, int n_pert, double* dpsi,
                       int* iters, double* resid, void* stream);
 
-/* Davidson PDEP solve (Sec. II D): the n_pdep most negative eigenvalues of
+/* Davidson PDEP solve (Sec. II C): the n_pdep most negative eigenvalues of
  * chi0bar, ascending, into eigvals [n_pdep]; eigvecs [n_pdep][n_pdep_dim]
  * (may be NULL).  phi0 [n_pdep][n_pdep_dim] is the start block (NULL: seeded
  * Philox4x32-10 normal deviates).  sys = -1 solves every system in turn and

@@ -2,7 +2,7 @@
 
 Test infrastructure (see ``oracle/__init__``).
 
-Sec. II D of the paper.  For a perturbing potential dV and each occupied
+Sec. II C of the paper.  For a perturbing potential dV and each occupied
 state v the Sternheimer equation (Eq. stern)
     (H - eps_v) P_c dpsi_v = - P_c dV psi_v,     P_c = 1 - sum_v |v><v|,
 is solved for P_c dpsi_v, here two independent ways:

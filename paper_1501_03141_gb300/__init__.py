@@ -1,6 +1,6 @@
 """GB300 PDEP library: Python front end of libpdep.so.
 
-The hot path (Sec. II D of Govoni & Galli, "Large scale GW calculations"):
+The hot path (Sec. II C of Govoni & Galli, "Large scale GW calculations"):
 Davidson diagonalisation of chi0bar = v^{1/2} chi0 v^{1/2} at omega = 0,
 where every chi0bar application is a batch of Sternheimer solves.  All the
 arithmetic runs in the CUDA kernels of csrc/; this module only marshals

@@ -79,6 +79,7 @@ class pdep_stats(ctypes.Structure):
         ("max_cg_residual", ctypes.c_double),
         ("max_dav_residual", ctypes.c_double),
         ("seconds", ctypes.c_double),
+        ("cg_variant", ctypes.c_int),
     ]
 
 

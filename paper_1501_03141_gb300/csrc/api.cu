@@ -1,4 +1,4 @@
-// C ABI and host orchestration of the PDEP hot path (Sec. II D of Govoni &
+// C ABI and host orchestration of the PDEP hot path (Sec. II C of Govoni &
 // Galli): setup eigensolve, batched Sternheimer CG, density response,
 // chi0bar application and the Davidson iteration.  Everything here only
 // enqueues kernels on the caller's stream and reads small convergence flags
@@ -67,8 +67,13 @@ struct SysData {
   double* d_psi = nullptr;   // [n_occ][ld]
   float* d_psif = nullptr;
   double* d_u = nullptr;     // [n_occ][n_r]  u_v(r) = Omega^{1/2} psi_v(r)
-  double* d_negeps = nullptr;
+  double* d_negeps = nullptr;   // -eps_v
+  float* d_negeps32 = nullptr;
+  double* d_kin64 = nullptr;    // |G_k|^2 / 2
+  float* d_kin32 = nullptr;
   double* d_ekin = nullptr;
+  double* d_kprec64 = nullptr;  // CG preconditioner per occupied state [n_occ][ld]
+  float* d_kprec32 = nullptr;
   std::vector<double> eps;   // n_occ + 1
   double alpha = 0;          // shift of the occupied space in H - eps_v + alpha P_v
   SphereDev<double> sd{};
@@ -93,11 +98,16 @@ struct pdep_ctx {
   std::vector<void*> owned;
   unsigned* d_status = nullptr;
   int* d_counter = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
   int* h_pin = nullptr;  // pinned host scratch (ints)
   // statistics of the current call
   long long st_solves = 0, st_cg_iters = 0;
   int st_cg_max = 0, st_refine_max = 0;
   double st_max_res = 0;
+  // autotuned launch shape of the CG step, per precision (-1: not tuned yet)
+  int cg_variant[2] = {-1, -1};
+  double cg_tune_ms[2][CG_NUM_VARIANTS] = {};
+  int cg_tune_next[2] = {0, 0};
 };
 
 namespace {
@@ -288,6 +298,18 @@ int upload_tables(pdep_ctx* c, SysData& s) {
   CK(cudaMemcpy(s.d_ucol, s.ucol.data(), sizeof(UCol) * s.ucol.size(), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s.d_slot, s.slot.data(), sizeof(int2) * s.slot.size(), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s.d_g2, s.g2.data(), sizeof(double) * s.g2.size(), cudaMemcpyHostToDevice));
+  {
+    std::vector<double> k64(s.g2.size());
+    std::vector<float> k32(s.g2.size());
+    for (size_t k = 0; k < s.g2.size(); ++k) {
+      k64[k] = 0.5 * s.g2[k];
+      k32[k] = (float)k64[k];
+    }
+    RET(persistent(c, &s.d_kin64, k64.size()));
+    RET(persistent(c, &s.d_kin32, k32.size()));
+    CK(cudaMemcpy(s.d_kin64, k64.data(), sizeof(double) * k64.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(s.d_kin32, k32.data(), sizeof(float) * k32.size(), cudaMemcpyHostToDevice));
+  }
   const double two_pi = 6.283185307179586476925286766559;
   for (int a = 0; a < 3; ++a) {
     const int N = s.N[a];
@@ -321,6 +343,8 @@ int upload_tables(pdep_ctx* c, SysData& s) {
   };
   fill(s.sd, s.d_tw64);
   fill(s.sf, s.d_tw32);
+  s.sd.kin = s.d_kin64;
+  s.sf.kin = s.d_kin32;
   return PDEP_OK;
 }
 
@@ -331,17 +355,22 @@ inline const double* vgrid(const SysData& s, double*) { return s.d_v; }
 inline const float* vgrid(const SysData& s, float*) { return s.d_vf; }
 inline const double* psi_of(const SysData& s, double*) { return s.d_psi; }
 inline const float* psi_of(const SysData& s, float*) { return s.d_psif; }
+inline const double* kprec_of(const SysData& s, double*) { return s.d_kprec64; }
+inline const double* negeps_of(const SysData& s, double*) { return s.d_negeps; }
+inline const float* negeps_of(const SysData& s, float*) { return s.d_negeps32; }
+inline const float* kprec_of(const SysData& s, float*) { return s.d_kprec32; }
 
 size_t b1_count(const SysData& s, int n_items) {
   return (size_t)n_items * s.N[0] * s.n_col;
 }
 
-// Y = (H + shift_v) X for the vectors of 'map' (H = -nabla^2/2 + V); shift
-// indexed by vector % period (null: none).  Then, if with_pv, the occupied
-// space is shifted: Y += alpha Psi (Psi^T X) over all n columns.
+// Y = (H - eps_v) X for the vectors of 'map' (H = -nabla^2/2 + V); vector i
+// uses occupied state i % n_occ; without with_shift Y = H X.  Then, if
+// with_pv, the occupied space is shifted: Y += alpha Psi (Psi^T X) on the same
+// columns.
 template <typename R>
 int apply_h(pdep_ctx* c, SysData& s, const R* X, R* Y, int n, const int* d_list, int n_list,
-            const double* shift, int period, bool with_pv, cudaStream_t st) {
+            bool with_shift, bool with_pv, cudaStream_t st) {
   ItemMap map{n, (n + 1) / 2};
   int n_items = (n + 1) / 2;
   if (d_list) {
@@ -366,20 +395,24 @@ int apply_h(pdep_ctx* c, SysData& s, const R* X, R* Y, int n, const int* d_list,
     ep.ldy = s.ld;
     ep.x_in = X;
     ep.ldx = s.ld;
-    ep.shift = shift;
-    ep.shift_period = period > 0 ? period : 1;
-    ep.scale = 1.0 / s.n_r;
-    ep.kin = 1.0;
-    ep.beta = 0.0;
+    ep.shift = with_shift ? negeps_of(s, (R*)nullptr) : nullptr;
+    ep.shift_period = with_shift ? s.n_occ : 1;
+    ep.scale = (R)(1.0 / s.n_r);
+    ep.kin = R(1);
+    ep.beta = R(0);
     ep.coef = COEF_ONE;
     CK(launch_cols_bwd<R>(sd, b1, map, n_items, ep, st));
   }
   if (with_pv) {
+    // only the listed columns when a list is given
+    const int m = d_list ? n_list : n;
     R* S;
-    RET(ws(c, sizeof(R) == 8 ? "pv_64" : "pv_32", (size_t)s.n_occ * n, &S));
+    RET(ws(c, sizeof(R) == 8 ? "pv_64" : "pv_32", (size_t)s.n_occ * std::max(m, 1), &S));
     const R* P = psi_of(s, (R*)nullptr);
-    CK(gemm<R>(true, s.n_occ, n, s.n_pw, 1.0, P, s.ld, X, s.ld, 0.0, S, s.n_occ, st));
-    CK(gemm<R>(false, s.n_pw, n, s.n_occ, s.alpha, P, s.ld, S, s.n_occ, 1.0, Y, s.ld, st));
+    CK(gemm<R>(true, s.n_occ, m, s.n_pw, 1.0, P, s.ld, X, s.ld, 0.0, S, s.n_occ, st, d_list,
+               nullptr));
+    CK(gemm<R>(false, s.n_pw, m, s.n_occ, s.alpha, P, s.ld, S, s.n_occ, 1.0, Y, s.ld, st, nullptr,
+               d_list));
   }
   return PDEP_OK;
 }
@@ -589,7 +622,7 @@ int setup_states(pdep_ctx* c, SysData& s, cudaStream_t st) {
   CK(cudaMemcpyAsync(dcomp, hc.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st));
   CK(unit_start(X0, s.ld, s.n_pw, dcomp, ns, 1e-3, c->opt.seed ^ 0x5eed5eedULL, st));
   OpFn op = [&](const double* in, double* outv, int m) -> int {
-    return apply_h<double>(c, s, in, outv, m, nullptr, 0, nullptr, 1, false, st);
+    return apply_h<double>(c, s, in, outv, m, nullptr, 0, false, false, st);
   };
   double* xt;
   RET(ws(c, "su_xt", (size_t)ns * s.ld, &xt));
@@ -623,7 +656,12 @@ int setup_states(pdep_ctx* c, SysData& s, cudaStream_t st) {
   std::vector<double> ne(nocc);
   for (int v = 0; v < nocc; ++v) ne[v] = -s.eps[v];
   CK(cudaMemcpyAsync(s.d_negeps, ne.data(), sizeof(double) * nocc, cudaMemcpyHostToDevice, st));
+  RET(persistent(c, &s.d_negeps32, nocc));
+  CK((convert<float, double>(s.d_negeps32, nocc, s.d_negeps, nocc, nocc, 1, st)));
   CK(kinetic_energy(s.d_psi, s.ld, s.n_half, nocc, s.d_g2, s.d_ekin, st));
+  RET(persistent(c, &s.d_kprec64, (size_t)nocc * s.ld));
+  RET(persistent(c, &s.d_kprec32, (size_t)nocc * s.ld));
+  CK(build_precond(s.d_g2, s.n_half, s.n_pw, s.d_ekin, nocc, s.d_kprec64, s.d_kprec32, s.ld, st));
   // occupied states on the grid: u_v(r) = sum_G c_v(G) e^{iG.r}
   {
     ItemMap map{nocc, (nocc + 1) / 2};
@@ -670,13 +708,13 @@ int cg_loop(pdep_ctx* c, SysData& s, const R* b, R* x, int n, double tol, int ma
   a.n_pw = s.n_pw;
   a.n_half = s.n_half;
   a.n_rhs = n;
-  a.g2 = s.d_g2;
-  a.ekin = s.d_ekin;
+  a.kprec = kprec_of(s, (R*)nullptr);
   a.n_occ = s.n_occ;
   a.sc = sc;
   a.tol = tol;
   a.status = c->d_status;
   a.n_active = c->d_counter;
+  const int pi = sizeof(R) == 8 ? 1 : 0;
   CK(cudaMemsetAsync(c->d_counter, 0, sizeof(int), st));
   CK(cg_start<R>(a, b, s.ld, st));
   *hit_cap = false;
@@ -689,9 +727,29 @@ int cg_loop(pdep_ctx* c, SysData& s, const R* b, R* x, int n, double tol, int ma
       break;
     }
     CK(active_list(sc, n, list, c->d_counter + 1, st));
-    RET(apply_h<R>(c, s, p, ap, n, list, n_act, s.d_negeps, s.n_occ, true, st));
+    RET(apply_h<R>(c, s, p, ap, n, list, n_act, true, true, st));
     CK(cudaMemsetAsync(c->d_counter, 0, sizeof(int), st));
-    CK(cg_step<R>(a, st));
+    // Autotuner: while untuned, each large step tries the next launch shape
+    // (all shapes compute the same update) and its time per RHS is kept;
+    // afterwards the fastest shape is used.
+    const bool tuning = c->cg_variant[pi] < 0 && n_act >= 256;
+    a.variant = tuning ? c->cg_tune_next[pi]
+                       : (c->cg_variant[pi] >= 0 ? c->cg_variant[pi] : (int)CG_STREAM256);
+    if (tuning) CK(cudaEventRecord(c->ev[0], st));
+    CK(cg_step<R>(a, list, n_act, st));
+    if (tuning) {
+      CK(cudaEventRecord(c->ev[1], st));
+      CK(cudaEventSynchronize(c->ev[1]));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+      c->cg_tune_ms[pi][a.variant] = ms / n_act;
+      if (++c->cg_tune_next[pi] == CG_NUM_VARIANTS) {
+        int best = 0;
+        for (int v = 1; v < CG_NUM_VARIANTS; ++v)
+          if (c->cg_tune_ms[pi][v] < c->cg_tune_ms[pi][best]) best = v;
+        c->cg_variant[pi] = best;
+      }
+    }
   }
   return PDEP_OK;
 }
@@ -763,7 +821,7 @@ int solve_rhs(pdep_ctx* c, SysData& s, const double* b, double* x, int n, int* h
       for (int i = 0; i < n; ++i) its_total[i] += its[i];
       CK(refine_accumulate(x, s.ld, d32, s.ld, s.n_pw, n, rn, st));
       // FP64 residual of the active RHS: ap64 = b - A x
-      RET(apply_h<double>(c, s, x, ap64, n, list, n_un, s.d_negeps, s.n_occ, true, st));
+      RET(apply_h<double>(c, s, x, ap64, n, list, n_un, true, true, st));
       CK(residual_norms(b, s.ld, ap64, s.ld, s.n_pw, n_un, rel, list, st));
     }
     {
@@ -774,10 +832,14 @@ int solve_rhs(pdep_ctx* c, SysData& s, const double* b, double* x, int n, int* h
     }
   }
   c->st_refine_max = std::max(c->st_refine_max, rounds);
-  // remove any occupied component left by rounding, then the FP64 residual
+  if (c->opt.precision == PDEP_FP64) {
+    // FP64 residual of the CG solution (the recursion only tracks its own)
+    RET(apply_h<double>(c, s, x, ap64, n, nullptr, 0, true, true, st));
+    CK(residual_norms(b, s.ld, ap64, s.ld, s.n_pw, n, rel, nullptr, st));
+  }
+  // mixed: rel already holds the FP64 residual of every RHS from its last
+  // refinement round.  Remove the occupied component left by rounding.
   RET(project_pc(c, s, x, n, st));
-  RET(apply_h<double>(c, s, x, ap64, n, nullptr, 0, s.d_negeps, s.n_occ, true, st));
-  CK(residual_norms(b, s.ld, ap64, s.ld, s.n_pw, n, rel, nullptr, st));
   std::vector<double> hr(n);
   CK(cudaMemcpyAsync(hr.data(), rel, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
   RET(sync(st));
@@ -1037,6 +1099,8 @@ void pdep_destroy(pdep_ctx* c) {
   if (c->d_status) cudaFree(c->d_status);
   if (c->d_counter) cudaFree(c->d_counter);
   if (c->h_pin) cudaFreeHost(c->h_pin);
+  for (cudaEvent_t e : c->ev)
+    if (e) cudaEventDestroy(e);
   cudaSetDevice(cur);
   delete c;
 }
@@ -1063,6 +1127,8 @@ int pdep_setup(const pdep_system_desc* sys, int n_sys, const pdep_options* opt, 
       cudaMallocHost(&c->h_pin, 16 * sizeof(int)) != cudaSuccess)
     return bail(fail(PDEP_ERR_OOM, "context allocation"));
   cudaMemset(c->d_status, 0, sizeof(unsigned));
+  if (cudaEventCreate(&c->ev[0]) != cudaSuccess || cudaEventCreate(&c->ev[1]) != cudaSuccess)
+    return bail(fail(PDEP_ERR_CUDA, "event creation"));
   c->sys.resize(n_sys);
   for (int i = 0; i < n_sys; ++i) {
     const pdep_system_desc& d = sys[i];
@@ -1202,13 +1268,13 @@ int pdep_apply_hamiltonian(pdep_ctx* c, int sys, const double* x, int n, double*
   CK(cudaMemcpy2DAsync(in, s.ld * sizeof(double), x, s.n_pw * sizeof(double),
                        s.n_pw * sizeof(double), n, kind_to_dev(x), st));
   if (precision == PDEP_FP64) {
-    RET(apply_h<double>(c, s, in, outv, n, nullptr, 0, nullptr, 1, false, st));
+    RET(apply_h<double>(c, s, in, outv, n, nullptr, 0, false, false, st));
   } else {
     float *in32, *out32;
     RET(ws(c, "api_in32", (size_t)n * s.ld, &in32));
     RET(ws(c, "api_out32", (size_t)n * s.ld, &out32));
     CK((convert<float, double>(in32, s.ld, in, s.ld, s.ld, n, st)));
-    RET(apply_h<float>(c, s, in32, out32, n, nullptr, 0, nullptr, 1, false, st));
+    RET(apply_h<float>(c, s, in32, out32, n, nullptr, 0, false, false, st));
     CK((convert<double, float>(outv, s.ld, out32, s.ld, s.n_pw, n, st)));
   }
   CK(cudaMemcpy2DAsync(y, s.n_pw * sizeof(double), outv, s.ld * sizeof(double),
@@ -1276,6 +1342,7 @@ int pdep_solve(pdep_ctx* c, int sys, const double* phi0, double* eigvals, double
     stats->cg_iterations_max = c->st_cg_max;
     stats->refine_rounds_max = c->st_refine_max;
     stats->max_cg_residual = c->st_max_res;
+    stats->cg_variant = c->cg_variant[c->opt.precision == PDEP_FP64 ? 1 : 0];
     stats->seconds =
         std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }

@@ -24,9 +24,10 @@ __device__ __forceinline__ R warp_sum(R v) {
   return v;
 }
 
-// block-wide sum of up to two values; every thread gets the result
+// block-wide sum of up to two doubles; warp 0 finishes, every thread gets the result
 __device__ __forceinline__ double2 block_sum2(double a, double b) {
   __shared__ double sa[32], sb[32];
+  __shared__ double2 res;
   a = warp_sum(a);
   b = warp_sum(b);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -36,13 +37,42 @@ __device__ __forceinline__ double2 block_sum2(double a, double b) {
     sb[w] = b;
   }
   __syncthreads();
-  const int nw = (blockDim.x + 31) >> 5;
-  double x = 0.0, y = 0.0;
-  for (int i = 0; i < nw; ++i) {
-    x += sa[i];
-    y += sb[i];
+  if (w == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    double x = l < nw ? sa[l] : 0.0, y = l < nw ? sb[l] : 0.0;
+    x = warp_sum(x);
+    y = warp_sum(y);
+    if (l == 0) res = make_double2(x, y);
   }
-  return make_double2(x, y);
+  __syncthreads();
+  return res;
+}
+
+// Block sum of two values: warp sums in the callers' precision R, the
+// per-warp partials summed in FP64 by warp 0 only.  Result in shared memory,
+// valid for every thread after the call.
+template <typename R>
+__device__ __forceinline__ double2 block_sum2_r(R a, R b) {
+  __shared__ double sa[32], sb[32];
+  __shared__ double2 res;
+  a = warp_sum(a);
+  b = warp_sum(b);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) {
+    sa[w] = (double)a;
+    sb[w] = (double)b;
+  }
+  __syncthreads();
+  if (w == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    double x = l < nw ? sa[l] : 0.0, y = l < nw ? sb[l] : 0.0;
+    x = warp_sum(x);
+    y = warp_sum(y);
+    if (l == 0) res = make_double2(x, y);
+  }
+  __syncthreads();
+  return res;
 }
 
 // ---------------------------------------------------------------------------
@@ -52,7 +82,8 @@ template <typename R, bool TA>
 __global__ void __launch_bounds__(256) k_gemm(int m, int n, int k, R alpha, const R* __restrict__ A,
                                               long long lda, const R* __restrict__ B, long long ldb,
                                               R beta, R* __restrict__ C, long long ldc, int kchunk,
-                                              int atomic) {
+                                              int atomic, const int* __restrict__ bmap,
+                                              const int* __restrict__ cmap) {
   constexpr int BM = 64, BN = 64, BK = 16;
   __shared__ R As[BK][BM + 1];
   __shared__ R Bs[BK][BN + 1];
@@ -88,10 +119,11 @@ __global__ void __launch_bounds__(256) k_gemm(int m, int n, int k, R alpha, cons
     {
       const int j = tid >> 2, kk0 = (tid & 3) * 4;
       const int gj = col0 + j;
+      const long long bc = gj < n ? (long long)(bmap ? bmap[gj] : gj) * ldb : 0;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int gk = kb + kk0 + q;
-        Bs[kk0 + q][j] = (gj < n && gk < kend) ? B[gk + (long long)gj * ldb] : R(0);
+        Bs[kk0 + q][j] = (gj < n && gk < kend) ? B[gk + bc] : R(0);
       }
     }
     __syncthreads();
@@ -117,7 +149,7 @@ __global__ void __launch_bounds__(256) k_gemm(int m, int n, int k, R alpha, cons
     for (int b = 0; b < 4; ++b) {
       const int gj = col0 + ty + 16 * b;
       if (gj >= n) continue;
-      R* c = C + gi + (long long)gj * ldc;
+      R* c = C + gi + (long long)(cmap ? cmap[gj] : gj) * ldc;
       if (atomic) {
         atomicAdd(c, alpha * acc[a][b]);
       } else {
@@ -130,19 +162,20 @@ __global__ void __launch_bounds__(256) k_gemm(int m, int n, int k, R alpha, cons
 }
 
 template <typename R>
-__global__ void k_scale_mat(R* C, long long ldc, int m, int n, R beta) {
+__global__ void k_scale_mat(R* C, long long ldc, int m, int n, R beta, const int* cmap) {
   const long long tot = (long long)m * n;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
        e += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(e % m), j = (int)(e / m);
-    R* c = C + i + (long long)j * ldc;
+    R* c = C + i + (long long)(cmap ? cmap[j] : j) * ldc;
     *c = beta == R(0) ? R(0) : beta * *c;
   }
 }
 
 template <typename R>
 cudaError_t gemm(bool transA, int m, int n, int k, double alpha, const R* A, long long lda,
-                 const R* B, long long ldb, double beta, R* C, long long ldc, cudaStream_t st) {
+                 const R* B, long long ldb, double beta, R* C, long long ldc, cudaStream_t st,
+                 const int* bmap, const int* cmap) {
   if (m <= 0 || n <= 0) return cudaSuccess;
   const int tm = (m + 63) / 64, tn = (n + 63) / 64;
   int splits = 1;
@@ -162,7 +195,7 @@ cudaError_t gemm(bool transA, int m, int n, int k, double alpha, const R* A, lon
     const long long tot = (long long)m * n;
     const int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
     count_launch();
-    k_scale_mat<R><<<blocks, 256, 0, st>>>(C, ldc, m, n, (R)beta);
+    k_scale_mat<R><<<blocks, 256, 0, st>>>(C, ldc, m, n, (R)beta, cmap);
     if (k <= 0) return cudaGetLastError();
     atomic = 1;
   }
@@ -172,18 +205,19 @@ cudaError_t gemm(bool transA, int m, int n, int k, double alpha, const R* A, lon
   count_launch();
   if (transA)
     k_gemm<R, true><<<grid, 256, 0, st>>>(m, n, k, (R)alpha, A, lda, B, ldb, (R)beta, C, ldc,
-                                          kchunk, atomic);
+                                          kchunk, atomic, bmap, cmap);
   else
     k_gemm<R, false><<<grid, 256, 0, st>>>(m, n, k, (R)alpha, A, lda, B, ldb, (R)beta, C, ldc,
-                                           kchunk, atomic);
+                                           kchunk, atomic, bmap, cmap);
   return cudaGetLastError();
 }
 
 template cudaError_t gemm<double>(bool, int, int, int, double, const double*, long long,
                                   const double*, long long, double, double*, long long,
-                                  cudaStream_t);
+                                  cudaStream_t, const int*, const int*);
 template cudaError_t gemm<float>(bool, int, int, int, double, const float*, long long,
-                                 const float*, long long, double, float*, long long, cudaStream_t);
+                                 const float*, long long, double, float*, long long, cudaStream_t,
+                                 const int*, const int*);
 
 // ---------------------------------------------------------------------------
 // one-sided Jacobi eigensolver
@@ -245,7 +279,7 @@ __global__ void k_jacobi_round(double* A, double* V, int n, int nn, int round,
   al = warp_sum(al);
   be = warp_sum(be);
   ga = warp_sum(ga);
-  if (ga == 0.0 || fabs(ga) <= 1e-15 * sqrt(al * be)) return;
+  if (ga == 0.0 || fabs(ga) <= 1e-14 * sqrt(al * be)) return;
   const double zeta = (be - al) / (2.0 * ga);
   const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
   const double c = 1.0 / sqrt(1.0 + tt * tt);
@@ -313,13 +347,49 @@ cudaError_t eigh(int n, const double* M, long long ldm, double* W, double* V, lo
   const int warps = nn / 2;
   const int tpb = 128;
   const int jb = (warps * 32 + tpb - 1) / tpb;
+  // One sweep = nn - 1 dependent rounds; they are replayed from a CUDA graph
+  // captured once per (size, buffers) to avoid nn - 1 stream launches.
+  cudaGraphExec_t sweep = nullptr;
+  if (nn - 1 > 8) {
+    struct Key {
+      int n;
+      const void *a, *v, *c;
+      cudaGraphExec_t exec;
+    };
+    static std::vector<Key> cache;
+    for (const Key& k : cache)
+      if (k.n == n && k.a == wk.a && k.v == wk.v && k.c == counter) sweep = k.exec;
+    if (!sweep) {
+      cudaStream_t cap;
+      cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return e;
+      cudaGraph_t g;
+      e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return e;
+      for (int r = 0; r < nn - 1; ++r)
+        k_jacobi_round<<<jb, tpb, 0, cap>>>(wk.a, wk.v, n, nn, r, counter);
+      e = cudaStreamEndCapture(cap, &g);
+      if (e != cudaSuccess) return e;
+      e = cudaGraphInstantiate(&sweep, g, 0);
+      cudaGraphDestroy(g);
+      cudaStreamDestroy(cap);
+      if (e != cudaSuccess) return e;
+      cache.push_back(Key{n, wk.a, wk.v, counter, sweep});
+    }
+  }
   unsigned hcount = 1;
-  for (int sweep = 0; sweep < max_sweeps && hcount != 0; ++sweep) {
+  for (int sweep_i = 0; sweep_i < max_sweeps && hcount != 0; ++sweep_i) {
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
-    for (int r = 0; r < nn - 1; ++r) {
-      count_launch();
-      k_jacobi_round<<<jb, tpb, 0, st>>>(wk.a, wk.v, n, nn, r, counter);
+    if (sweep) {
+      for (int r = 0; r < nn - 1; ++r) count_launch();
+      e = cudaGraphLaunch(sweep, st);
+      if (e != cudaSuccess) return e;
+    } else {
+      for (int r = 0; r < nn - 1; ++r) {
+        count_launch();
+        k_jacobi_round<<<jb, tpb, 0, st>>>(wk.a, wk.v, n, nn, r, counter);
+      }
     }
     if (nn - 1 == 0) break;
     e = cudaMemcpyAsync(&hcount, counter, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
@@ -532,22 +602,42 @@ __device__ __forceinline__ double precond(const double* __restrict__ g2, int n_h
   return tpa(0.5 * g2[j >> 1] * inv_e);
 }
 
+__global__ void k_build_precond(const double* __restrict__ g2, int n_half, int n_pw,
+                                const double* __restrict__ ekin, double* k64, float* k32,
+                                long long ld) {
+  const int v = blockIdx.x;
+  const double e = ekin[v] > 1e-3 ? ekin[v] : 1e-3;
+  const double inv_e = 1.0 / e;
+  for (int j = threadIdx.x; j < n_pw; j += blockDim.x) {
+    const double k = precond(g2, n_half, j, inv_e);
+    k64[(long long)v * ld + j] = k;
+    k32[(long long)v * ld + j] = (float)k;
+  }
+}
+cudaError_t build_precond(const double* g2, int n_half, int n_pw, const double* ekin, int n_occ,
+                          double* k64, float* k32, long long ld, cudaStream_t st) {
+  if (n_occ <= 0) return cudaSuccess;
+  count_launch();
+  k_build_precond<<<n_occ, 256, 0, st>>>(g2, n_half, n_pw, ekin, k64, k32, ld);
+  return cudaGetLastError();
+}
+
 template <typename R>
 __global__ void k_cg_start(CgArgs<R> a, const R* __restrict__ b, long long ldb) {
   const int i = blockIdx.x;
   const long long o = (long long)i * a.ld;
-  const double inv_e = 1.0 / a.ekin[i % a.n_occ];
-  double bb = 0.0, rz = 0.0;
+  const R* K = a.kprec + (long long)(i % a.n_occ) * a.ld;
+  R bb = R(0), rz = R(0);
   for (int j = threadIdx.x; j < a.n_pw; j += blockDim.x) {
     const R bv = b[(long long)i * ldb + j];
-    const double kz = precond(a.g2, a.n_half, j, inv_e);
+    const R kz = K[j];
     a.x[o + j] = R(0);
     a.r[o + j] = bv;
-    a.p[o + j] = (R)(kz * (double)bv);
-    bb += (double)bv * bv;
-    rz += kz * (double)bv * bv;
+    a.p[o + j] = kz * bv;
+    bb += bv * bv;
+    rz += kz * bv * bv;
   }
-  double2 t = block_sum2(bb, rz);
+  double2 t = block_sum2_r<R>(bb, rz);
   if (threadIdx.x == 0) {
     CgScal s;
     s.bnorm = sqrt(t.x);
@@ -560,81 +650,182 @@ __global__ void k_cg_start(CgArgs<R> a, const R* __restrict__ b, long long ldb) 
   }
 }
 
+// finish one RHS's step (thread 0): scalars, convergence, active count
 template <typename R>
-__global__ void k_cg_step(CgArgs<R> a) {
-  const int i = blockIdx.x;
+__device__ __forceinline__ void cg_finish(const CgArgs<R>& a, int i, const CgScal& s, double rn,
+                                          double rkr, bool done) {
+  CgScal n = s;
+  n.iters = s.iters + 1;
+  n.rnorm = rn;
+  n.rz = rkr;
+  n.active = done ? 0 : 1;
+  if (!isfinite(rn)) {
+    n.active = 0;
+    atomicOr(a.status, (unsigned)DEV_NONFINITE);
+  }
+  a.sc[i] = n;
+  if (n.active) atomicAdd(a.n_active, 1);
+}
+
+// Register-cached step: each thread keeps its E elements of p, Ap and r, so
+// the RHS is read once (p, Ap, x, r) and written once (x, r, p).  Element
+// arithmetic runs in R (FP32 costs 1/64 of FP64 on this part); only the
+// per-thread partial sums are promoted to FP64 for the block reductions.
+template <typename R, int E>
+__global__ void __launch_bounds__(512) k_cg_step_reg(CgArgs<R> a, const int* __restrict__ list) {
+  const int i = list ? list[blockIdx.x] : blockIdx.x;
   __shared__ CgScal s;
+  __shared__ R coef[2];  // alpha, then beta
+  __shared__ int flag;   // 1: breakdown, 2: converged
   if (threadIdx.x == 0) s = a.sc[i];
   __syncthreads();
   if (!s.active) return;
   const long long o = (long long)i * a.ld;
-  const double inv_e = 1.0 / a.ekin[i % a.n_occ];
-  double pap = 0.0;
-  for (int j = threadIdx.x; j < a.n_pw; j += blockDim.x)
-    pap += (double)a.p[o + j] * (double)a.ap[o + j];
-  const double2 t1 = block_sum2(pap, 0.0);
-  const double alpha = s.rz / t1.x;
-  if (!(t1.x > 0.0) || !isfinite(alpha)) {
-    if (threadIdx.x == 0) {
+  const R* K = a.kprec + (long long)(i % a.n_occ) * a.ld;
+  R pv[E], av[E], rv[E];
+  R pap = R(0);
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int j = threadIdx.x + e * blockDim.x;
+    if (j < a.n_pw) {
+      pv[e] = a.p[o + j];
+      av[e] = a.ap[o + j];
+      pap += pv[e] * av[e];
+    } else {
+      pv[e] = R(0);
+      av[e] = R(0);
+    }
+  }
+  const double2 t1 = block_sum2_r<R>(pap, R(0));
+  if (threadIdx.x == 0) {
+    const double al = s.rz / t1.x;
+    flag = (!(t1.x > 0.0) || !isfinite(al)) ? 1 : 0;
+    coef[0] = (R)al;
+    if (flag) {
       atomicOr(a.status, isfinite(t1.x) ? (unsigned)DEV_BREAKDOWN : (unsigned)DEV_NONFINITE);
       a.sc[i].active = 0;
     }
-    return;
   }
-  double rr = 0.0, rkr = 0.0;
-  for (int j = threadIdx.x; j < a.n_pw; j += blockDim.x) {
-    const double pv = (double)a.p[o + j];
-    const double xv = (double)a.x[o + j] + alpha * pv;
-    const double rv = (double)a.r[o + j] - alpha * (double)a.ap[o + j];
-    a.x[o + j] = (R)xv;
-    a.r[o + j] = (R)rv;
-    rr += rv * rv;
-    rkr += precond(a.g2, a.n_half, j, inv_e) * rv * rv;
-  }
-  const double2 t2 = block_sum2(rr, rkr);
-  const double rn = sqrt(t2.x);
-  const bool done = rn <= a.tol * s.bnorm;
-  const double beta = t2.y / s.rz;
-  if (!done) {
-    for (int j = threadIdx.x; j < a.n_pw; j += blockDim.x) {
-      const double z = precond(a.g2, a.n_half, j, inv_e) * (double)a.r[o + j];
-      a.p[o + j] = (R)(z + beta * (double)a.p[o + j]);
+  __syncthreads();
+  if (flag) return;
+  const R alpha = coef[0];
+  R rr = R(0), rkr = R(0);
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int j = threadIdx.x + e * blockDim.x;
+    if (j < a.n_pw) {
+      a.x[o + j] = a.x[o + j] + alpha * pv[e];
+      const R r = a.r[o + j] - alpha * av[e];
+      rv[e] = r;
+      rr += r * r;
+      rkr += K[j] * r * r;
+    } else {
+      rv[e] = R(0);
     }
   }
+  const double2 t2 = block_sum2_r<R>(rr, rkr);
   if (threadIdx.x == 0) {
-    CgScal n = s;
-    n.iters = s.iters + 1;
-    n.rnorm = rn;
-    n.rz = t2.y;
-    n.active = done ? 0 : 1;
-    if (!isfinite(rn)) {
-      n.active = 0;
-      atomicOr(a.status, (unsigned)DEV_NONFINITE);
-    }
-    a.sc[i] = n;
-    if (n.active) atomicAdd(a.n_active, 1);
+    const double rn = sqrt(t2.x);
+    const bool done = rn <= a.tol * s.bnorm;
+    flag = done ? 2 : 0;
+    coef[1] = (R)(t2.y / s.rz);
+    cg_finish(a, i, s, rn, t2.y, done);
   }
+  __syncthreads();
+  const bool done = flag == 2;
+  const R beta = coef[1];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int j = threadIdx.x + e * blockDim.x;
+    if (j < a.n_pw) {
+      a.r[o + j] = rv[e];
+      if (!done) a.p[o + j] = K[j] * rv[e] + beta * pv[e];
+    }
+  }
+}
+
+// Streaming step (three passes over the RHS, re-reads served by L1/L2):
+// fewer registers, so more RHS in flight per SM than the cached variant.
+template <typename R>
+__global__ void __launch_bounds__(512) k_cg_step(CgArgs<R> a, const int* __restrict__ list) {
+  const int i = list ? list[blockIdx.x] : blockIdx.x;
+  __shared__ CgScal s;
+  __shared__ R coef[2];
+  __shared__ int flag;
+  if (threadIdx.x == 0) s = a.sc[i];
+  __syncthreads();
+  if (!s.active) return;
+  const long long o = (long long)i * a.ld;
+  const R* K = a.kprec + (long long)(i % a.n_occ) * a.ld;
+  R pap = R(0);
+  for (int j = threadIdx.x; j < a.n_pw; j += blockDim.x) pap += a.p[o + j] * a.ap[o + j];
+  const double2 t1 = block_sum2_r<R>(pap, R(0));
+  if (threadIdx.x == 0) {
+    const double al = s.rz / t1.x;
+    flag = (!(t1.x > 0.0) || !isfinite(al)) ? 1 : 0;
+    coef[0] = (R)al;
+    if (flag) {
+      atomicOr(a.status, isfinite(t1.x) ? (unsigned)DEV_BREAKDOWN : (unsigned)DEV_NONFINITE);
+      a.sc[i].active = 0;
+    }
+  }
+  __syncthreads();
+  if (flag) return;
+  const R alpha = coef[0];
+  R rr = R(0), rkr = R(0);
+  for (int j = threadIdx.x; j < a.n_pw; j += blockDim.x) {
+    a.x[o + j] = a.x[o + j] + alpha * a.p[o + j];
+    const R r = a.r[o + j] - alpha * a.ap[o + j];
+    a.r[o + j] = r;
+    rr += r * r;
+    rkr += K[j] * r * r;
+  }
+  const double2 t2 = block_sum2_r<R>(rr, rkr);
+  if (threadIdx.x == 0) {
+    const double rn = sqrt(t2.x);
+    const bool done = rn <= a.tol * s.bnorm;
+    flag = done ? 2 : 0;
+    coef[1] = (R)(t2.y / s.rz);
+    cg_finish(a, i, s, rn, t2.y, done);
+  }
+  __syncthreads();
+  if (flag == 2) return;
+  const R beta = coef[1];
+  for (int j = threadIdx.x; j < a.n_pw; j += blockDim.x)
+    a.p[o + j] = K[j] * a.r[o + j] + beta * a.p[o + j];
 }
 
 template <typename R>
 cudaError_t cg_start(const CgArgs<R>& a, const R* b, long long ldb, cudaStream_t st) {
   if (a.n_rhs <= 0) return cudaSuccess;
-  { count_launch(); k_cg_start<R><<<a.n_rhs, 256, 0, st>>>(a, b, ldb); }
+  count_launch();
+  k_cg_start<R><<<a.n_rhs, 256, 0, st>>>(a, b, ldb);
   return cudaGetLastError();
 }
 template <typename R>
-cudaError_t cg_step(const CgArgs<R>& a, cudaStream_t st) {
-  if (a.n_rhs <= 0) return cudaSuccess;
-  // x, r, p, Ap read; x, r, p written (plus r, p re-read): ~11 vector passes
-  ProfScope ps(sizeof(R) == 8 ? PC_CG_F64 : PC_CG_F32, st, 20.0 * a.n_rhs * (double)a.n_pw,
-               11.0 * a.n_rhs * (double)a.n_pw * sizeof(R));
-  { count_launch(); k_cg_step<R><<<a.n_rhs, 256, 0, st>>>(a); }
+cudaError_t cg_step(const CgArgs<R>& a, const int* list, int n_list, cudaStream_t st) {
+  const int nb = list ? n_list : a.n_rhs;
+  if (nb <= 0) return cudaSuccess;
+  // x, r, p, Ap read once; x, r, p written once: 7 vector passes per active RHS
+  ProfScope ps(sizeof(R) == 8 ? PC_CG_F64 : PC_CG_F32, st, 12.0 * nb * (double)a.n_pw,
+               7.0 * nb * (double)a.n_pw * sizeof(R));
+  count_launch();
+  int v = a.variant;
+  if ((v == CG_REG256 && a.n_pw > 16 * 256) || (v == CG_REG512 && a.n_pw > 16 * 512))
+    v = CG_STREAM256;
+  switch (v) {
+    case CG_REG256: k_cg_step_reg<R, 16><<<nb, 256, 0, st>>>(a, list); break;
+    case CG_REG512: k_cg_step_reg<R, 16><<<nb, 512, 0, st>>>(a, list); break;
+    case CG_STREAM128: k_cg_step<R><<<nb, 128, 0, st>>>(a, list); break;
+    case CG_STREAM512: k_cg_step<R><<<nb, 512, 0, st>>>(a, list); break;
+    default: k_cg_step<R><<<nb, 256, 0, st>>>(a, list); break;
+  }
   return cudaGetLastError();
 }
 template cudaError_t cg_start<double>(const CgArgs<double>&, const double*, long long, cudaStream_t);
 template cudaError_t cg_start<float>(const CgArgs<float>&, const float*, long long, cudaStream_t);
-template cudaError_t cg_step<double>(const CgArgs<double>&, cudaStream_t);
-template cudaError_t cg_step<float>(const CgArgs<float>&, cudaStream_t);
+template cudaError_t cg_step<double>(const CgArgs<double>&, const int*, int, cudaStream_t);
+template cudaError_t cg_step<float>(const CgArgs<float>&, const int*, int, cudaStream_t);
 
 __global__ void k_residual_norms(const double* __restrict__ b, long long ldb, double* ap,
                                  long long lda, int n_pw, double* rel, const int* __restrict__ list) {

@@ -9,10 +9,12 @@
 namespace pdep {
 
 // C[m x n] = alpha * op(A)[m x k] * B[k x n] + beta * C, op(A) = A^T if transA.
-// Split over k (atomic accumulation) when the tile count is small.
+// Split over k (atomic accumulation) when the tile count is small.  Optional
+// column maps: column j of B is B[:, bmap[j]] and column j of C is C[:, cmap[j]].
 template <typename R>
 cudaError_t gemm(bool transA, int m, int n, int k, double alpha, const R* A, long long lda,
-                 const R* B, long long ldb, double beta, R* C, long long ldc, cudaStream_t st);
+                 const R* B, long long ldb, double beta, R* C, long long ldc, cudaStream_t st,
+                 const int* bmap = nullptr, const int* cmap = nullptr);
 
 // Symmetric eigendecomposition of the n x n matrix M (lda), FP64:
 // one-sided (Hestenes) Jacobi on M - sigma I (sigma = Gershgorin bound, so
@@ -67,18 +69,32 @@ struct CgArgs {
   int n_pw;
   int n_half;
   int n_rhs;
-  const double* g2;     // |G_k|^2, [n_half]
-  const double* ekin;   // preconditioner energy per occupied state [n_occ]
+  const R* kprec;       // preconditioner K(G) per occupied state, [n_occ][ld]
   int n_occ;            // rhs index i uses occupied state i % n_occ
   CgScal* sc;
   double tol;
   unsigned* status;
   int* n_active;        // counter (atomic) of RHS still active after the step
+  int variant;          // CgVariant (picked by the autotuner)
+};
+// launch shapes of one CG step: register-cached (the RHS read once) or
+// streaming (three passes, more RHS resident per SM)
+enum CgVariant : int {
+  CG_REG256 = 0,
+  CG_REG512 = 1,
+  CG_STREAM128 = 2,
+  CG_STREAM256 = 3,
+  CG_STREAM512 = 4,
+  CG_NUM_VARIANTS = 5
 };
 template <typename R>
 cudaError_t cg_start(const CgArgs<R>& a, const R* b, long long ldb, cudaStream_t st);
+// one PCG step for the n_list RHS of list (all n_rhs when list is null)
 template <typename R>
-cudaError_t cg_step(const CgArgs<R>& a, cudaStream_t st);
+cudaError_t cg_step(const CgArgs<R>& a, const int* list, int n_list, cudaStream_t st);
+// K[v][j] = Teter-Payne-Allan K(|G_j|^2/2 / ekin[v]) (1 at G = 0), FP64 and FP32 copies
+cudaError_t build_precond(const double* g2, int n_half, int n_pw, const double* ekin, int n_occ,
+                          double* k64, float* k32, long long ld, cudaStream_t st);
 
 // y[:, i] = b[:, i] - y[:, i] (FP64), with per-column norms ||y_i|| / ||b_i||,
 // for every i < n, or for i in list[0..n) when list is given.

@@ -24,15 +24,17 @@ cudaError_t upload_local_twiddles() {
   return cudaMemcpyToSymbol(c_local_tw_f, hf, sizeof(hf));
 }
 
-// lanes per line for each supported length (N / TPL registers per lane)
-template <int N>
+// Lanes per line for each supported length (N / TPL registers per lane).
+// Four lanes per line up to N = 64 measured faster than two for FP32 too:
+// the extra shuffle stage costs less than the occupancy two-lane lines lose.
+template <typename R, int N>
 struct Tpl;
-template <> struct Tpl<24> { static constexpr int v = 2; };
-template <> struct Tpl<32> { static constexpr int v = 4; };
-template <> struct Tpl<40> { static constexpr int v = 4; };
-template <> struct Tpl<48> { static constexpr int v = 4; };
-template <> struct Tpl<64> { static constexpr int v = 4; };
-template <> struct Tpl<192> { static constexpr int v = 8; };
+template <typename R> struct Tpl<R, 24> { static constexpr int v = 2; };
+template <typename R> struct Tpl<R, 32> { static constexpr int v = 4; };
+template <typename R> struct Tpl<R, 40> { static constexpr int v = 4; };
+template <typename R> struct Tpl<R, 48> { static constexpr int v = 4; };
+template <typename R> struct Tpl<R, 64> { static constexpr int v = 4; };
+template <typename R> struct Tpl<R, 192> { static constexpr int v = 8; };
 
 bool grid_supported(int N1, int N2, int N3) {
   bool n1 = (N1 == 24 || N1 == 32 || N1 == 40 || N1 == 48 || N1 == 64);
@@ -59,7 +61,7 @@ template <typename R, int N1>
 __global__ void __launch_bounds__(128) k_cols_fwd(SphereDev<R> s, const R* __restrict__ x,
                                                   long long ldx, ItemMap map, int n_items,
                                                   int coef, cpx<R>* __restrict__ b1) {
-  constexpr int TPL = Tpl<N1>::v;
+  constexpr int TPL = Tpl<R, N1>::v;
   constexpr int M = N1 / TPL;
   const int t = threadIdx.x & (TPL - 1);
   const long long g = (long long)blockIdx.x * (blockDim.x / TPL) + threadIdx.x / TPL;
@@ -129,19 +131,19 @@ template <typename R>
 __device__ __forceinline__ void write_out(const Epilogue<R>& ep, int vec, int j, R val, R coefv,
                                           R diag) {
   R* y = ep.y + (long long)vec * ep.ldy;
-  R r = (R)ep.scale * coefv * val;
+  R r = ep.scale * coefv * val;
   if (ep.x_in) {
-    const R sh = ep.shift ? (R)ep.shift[vec % ep.shift_period] : R(0);
+    const R sh = ep.shift ? ep.shift[vec % ep.shift_period] : R(0);
     r += (diag + sh) * ep.x_in[(long long)vec * ep.ldx + j];
   }
-  if (ep.beta != 0.0) r += (R)ep.beta * y[j];
+  if (ep.beta != R(0)) r += ep.beta * y[j];
   y[j] = r;
 }
 
 template <typename R, int N1>
 __global__ void __launch_bounds__(128) k_cols_bwd(SphereDev<R> s, const cpx<R>* __restrict__ b1,
                                                   ItemMap map, int n_items, Epilogue<R> ep) {
-  constexpr int TPL = Tpl<N1>::v;
+  constexpr int TPL = Tpl<R, N1>::v;
   constexpr int M = N1 / TPL;
   const int lane = threadIdx.x & 31;
   const int t = threadIdx.x & (TPL - 1);
@@ -186,7 +188,7 @@ __global__ void __launch_bounds__(128) k_cols_bwd(SphereDev<R> s, const cpx<R>* 
       const cpx<R> sa = d + conj(dm);   // 2 Va
       const cpx<R> sb = d - conj(dm);   // 2 i Vb
       const R cf = coef_of<R>(ep.coef, s.g2, k);
-      const R dg = (R)(0.5 * ep.kin * s.g2[k]);
+      const R dg = ep.kin * s.kin[k];
       if (ia >= 0) {
         write_out(ep, ia, 2 * k, rs2 * sa.x, cf, dg);
         write_out(ep, ia, 2 * k + 1, rs2 * sa.y, cf, dg);
@@ -207,9 +209,33 @@ __global__ void __launch_bounds__(128) k_cols_bwd(SphereDev<R> s, const cpx<R>* 
 // ---------------------------------------------------------------------------
 // slab pass: one x-plane i1 of one item (or of one group for DENSITY)
 // ---------------------------------------------------------------------------
+// largest block a slab of this shape launches with: every z-line (N2 lines)
+// or every y-line (at most N3/2 + 1 planes) in one round
+template <typename R, int N2, int N3>
+struct SlabThreads {
+  static constexpr int z = N2 * Tpl<R, N3>::v;
+  static constexpr int y = (N3 / 2 + 1) * Tpl<R, N2>::v;
+  static constexpr int v = (((z > y ? z : y) + 31) / 32) * 32;
+};
+// FP32 slabs keep three blocks of up to 256 threads per SM resident
+// (register budget ~85-110); FP64 slabs are bound by the FP64 pipe at one
+// block per SM.
+template <typename R, int N2, int N3>
+struct SlabMinBlocks {
+  static constexpr int t = SlabThreads<R, N2, N3>::v;
+  static constexpr int v = sizeof(R) != 4 ? 1 : t <= 128 ? 384 / t : t <= 256 ? 3 : 1;
+};
+// Row stride of the (n3, i2) shared-memory plane: FP32 rows are padded by 8
+// complex so that the four n3 rows a warp touches fall on two bank halves.
+template <typename R, int N2>
+struct T2Stride {
+  static constexpr int v = sizeof(R) == 4 ? N2 + 8 : N2;
+};
+
 template <typename R, int N2>
 __device__ __forceinline__ void y_inverse(const SphereDev<R>& s, const cpx<R>* S1, cpx<R>* T2) {
-  constexpr int TL = Tpl<N2>::v;
+  constexpr int TL = Tpl<R, N2>::v;
+  constexpr int TS = T2Stride<R, N2>::v;
   constexpr int M = N2 / TL;
   const int nslot = 2 * s.R3 + 1;
   const int per = blockDim.x / TL;
@@ -227,14 +253,15 @@ __device__ __forceinline__ void y_inverse(const SphereDev<R>& s, const cpx<R>* S
     fft_a2b<R, N2, TL, +1>(v, t, s.tw2);
     if (act) {
 #pragma unroll
-      for (int i = 0; i < M; ++i) T2[sl * N2 + pos_b<N2, TL>(t, i)] = v[i];
+      for (int i = 0; i < M; ++i) T2[sl * TS + pos_b<N2, TL>(t, i)] = v[i];
     }
   }
 }
 
 template <typename R, int N2>
 __device__ __forceinline__ void y_forward(const SphereDev<R>& s, const cpx<R>* T2, cpx<R>* S1) {
-  constexpr int TL = Tpl<N2>::v;
+  constexpr int TL = Tpl<R, N2>::v;
+  constexpr int TS = T2Stride<R, N2>::v;
   constexpr int M = N2 / TL;
   const int nslot = 2 * s.R3 + 1;
   const int per = blockDim.x / TL;
@@ -245,7 +272,7 @@ __device__ __forceinline__ void y_forward(const SphereDev<R>& s, const cpx<R>* T
     const int2 info = act ? s.slot[sl] : make_int2(-1, 0);
     cpx<R> v[M];
 #pragma unroll
-    for (int i = 0; i < M; ++i) v[i] = act ? T2[sl * N2 + pos_b<N2, TL>(t, i)] : zero<R>();
+    for (int i = 0; i < M; ++i) v[i] = act ? T2[sl * TS + pos_b<N2, TL>(t, i)] : zero<R>();
     fft_b2a<R, N2, TL, -1>(v, t, s.tw2);
     if (act) {
 #pragma unroll
@@ -257,19 +284,12 @@ __device__ __forceinline__ void y_forward(const SphereDev<R>& s, const cpx<R>* T
   }
 }
 
-// largest block a slab of this shape launches with: every z-line (N2 lines)
-// or every y-line (at most N3/2 + 1 planes) in one round
-template <int N2, int N3>
-struct SlabThreads {
-  static constexpr int z = N2 * Tpl<N3>::v;
-  static constexpr int y = (N3 / 2 + 1) * Tpl<N2>::v;
-  static constexpr int v = (((z > y ? z : y) + 31) / 32) * 32;
-};
-
 template <typename R, int N2, int N3>
-__global__ void __launch_bounds__(SlabThreads<N2, N3>::v, 1) k_slab(SphereDev<R> s, SlabArgs<R> a) {
-  constexpr int TL3 = Tpl<N3>::v;
+__global__ void __launch_bounds__(SlabThreads<R, N2, N3>::v, (SlabMinBlocks<R, N2, N3>::v))
+    k_slab(SphereDev<R> s, SlabArgs<R> a) {
+  constexpr int TL3 = Tpl<R, N3>::v;
   constexpr int M3 = N3 / TL3;
+  constexpr int TS = T2Stride<R, N2>::v;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* S1 = reinterpret_cast<cpx<R>*>(smem_raw);
   cpx<R>* T2 = S1 + s.n_col;
@@ -298,7 +318,7 @@ __global__ void __launch_bounds__(SlabThreads<N2, N3>::v, 1) k_slab(SphereDev<R>
 #pragma unroll
       for (int i = 0; i < M3; ++i) {
         const int n3 = freq_of(pos_a<N3, TL3>(t3, i), N3);
-        v[i] = (act && iabs(n3) <= R3) ? T2[(n3 + R3) * N2 + i2] : zero<R>();
+        v[i] = (act && iabs(n3) <= R3) ? T2[(n3 + R3) * TS + i2] : zero<R>();
       }
       fft_a2b<R, N3, TL3, +1>(v, t3, s.tw3);
       const int va = 2 * w, vb = 2 * w + 1;
@@ -356,7 +376,7 @@ __global__ void __launch_bounds__(SlabThreads<N2, N3>::v, 1) k_slab(SphereDev<R>
 #pragma unroll
       for (int i = 0; i < M3; ++i) {
         const int n3 = freq_of(pos_a<N3, TL3>(t3, i), N3);
-        v[i] = (act && iabs(n3) <= R3) ? T2[(n3 + R3) * N2 + i2] : zero<R>();
+        v[i] = (act && iabs(n3) <= R3) ? T2[(n3 + R3) * TS + i2] : zero<R>();
       }
       fft_a2b<R, N3, TL3, +1>(v, t3, s.tw3);
       if (a.mode == SLAB_TO_GRID) {
@@ -384,7 +404,7 @@ __global__ void __launch_bounds__(SlabThreads<N2, N3>::v, 1) k_slab(SphereDev<R>
 #pragma unroll
       for (int i = 0; i < M3; ++i) {
         const int n3 = freq_of(pos_a<N3, TL3>(t3, i), N3);
-        if (iabs(n3) <= R3) T2[(n3 + R3) * N2 + i2] = v[i];
+        if (iabs(n3) <= R3) T2[(n3 + R3) * TS + i2] = v[i];
       }
     }
   }
@@ -399,19 +419,20 @@ __global__ void __launch_bounds__(SlabThreads<N2, N3>::v, 1) k_slab(SphereDev<R>
 // host launchers
 // ---------------------------------------------------------------------------
 size_t slab_smem_bytes(int n_col, int R3, int N2, size_t elem) {
-  return (size_t)(n_col + (2 * R3 + 1) * N2) * 2 * elem;
+  const int ts = elem == 4 ? N2 + 8 : N2;  // T2Stride
+  return (size_t)(n_col + (2 * R3 + 1) * ts) * 2 * elem;
 }
 
-template <int N>
+template <typename R, int N>
 static int threads_for(int lines) {
-  int n = lines * Tpl<N>::v;
+  int n = lines * Tpl<R, N>::v;
   return ((n + 31) / 32) * 32;
 }
 
 template <typename R, int N1>
 static cudaError_t cols_fwd_impl(const SphereDev<R>& s, const R* x, long long ldx, ItemMap map,
                                  int n_items, int coef, cpx<R>* b1, cudaStream_t st) {
-  const int per = 128 / Tpl<N1>::v;
+  const int per = 128 / Tpl<R, N1>::v;
   const long long total = (long long)n_items * s.n_ucol;
   if (total == 0) return cudaSuccess;
   const long long blocks = (total + per - 1) / per;
@@ -427,7 +448,7 @@ static cudaError_t cols_fwd_impl(const SphereDev<R>& s, const R* x, long long ld
 template <typename R, int N1>
 static cudaError_t cols_bwd_impl(const SphereDev<R>& s, const cpx<R>* b1, ItemMap map,
                                  int n_items, const Epilogue<R>& ep, cudaStream_t st) {
-  const int per = 128 / Tpl<N1>::v;
+  const int per = 128 / Tpl<R, N1>::v;
   const long long total = (long long)n_items * s.n_ucol;
   if (total == 0) return cudaSuccess;
   const long long blocks = (total + per - 1) / per;
@@ -435,7 +456,7 @@ static cudaError_t cols_bwd_impl(const SphereDev<R>& s, const cpx<R>* b1, ItemMa
   const double vecs = (double)n_items * 2.0 * s.n_pw * sizeof(R);
   ProfScope ps(sizeof(R) == 8 ? PC_COLS_F64 : PC_COLS_F32, st, lines * 5.0 * N1 * log2((double)N1),
                lines * N1 * 2.0 * sizeof(R) + vecs * (1.0 + (ep.x_in ? 1.0 : 0.0) +
-                                                      (ep.beta != 0.0 ? 1.0 : 0.0)));
+                                                      (ep.beta != R(0) ? 1.0 : 0.0)));
   count_launch();
   k_cols_bwd<R, N1><<<(unsigned)blocks, 128, 0, st>>>(s, b1, map, n_items, ep);
   return cudaGetLastError();
@@ -443,10 +464,10 @@ static cudaError_t cols_bwd_impl(const SphereDev<R>& s, const cpx<R>* b1, ItemMa
 
 template <typename R, int N2, int N3>
 static cudaError_t slab_impl(const SphereDev<R>& s, const SlabArgs<R>& a, cudaStream_t st) {
-  int nt = threads_for<N3>(N2);
-  int ny = threads_for<N2>(2 * s.R3 + 1);
+  int nt = threads_for<R, N3>(N2);
+  int ny = threads_for<R, N2>(2 * s.R3 + 1);
   if (a.mode != SLAB_DENSITY && ny > nt) nt = ny;
-  if (nt > SlabThreads<N2, N3>::v) return cudaErrorInvalidConfiguration;
+  if (nt > SlabThreads<R, N2, N3>::v) return cudaErrorInvalidConfiguration;
   const size_t smem = slab_smem_bytes(s.n_col, s.R3, N2, sizeof(R));
   auto kern = k_slab<R, N2, N3>;
   static bool attr_set = false;  // per instantiation; the limit is raised once

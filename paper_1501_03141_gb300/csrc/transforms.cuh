@@ -30,6 +30,7 @@ struct SphereDev {
   const UCol* ucol;         // [n_ucol]
   const int2* slot;         // [2 R3 + 1]: (R2(n3), first full-column index)
   const double* g2;         // |G_k|^2, [n_half]
+  const R* kin;             // |G_k|^2 / 2 in the kernel's precision, [n_half]
   const cpx<R>* tw1;        // exp(+2 pi i j/N1), j < N1
   const cpx<R>* tw2;
   const cpx<R>* tw3;
@@ -66,11 +67,11 @@ struct Epilogue {
   long long ldy;
   const R* x_in;        // vectors for the diagonal term (may be null)
   long long ldx;
-  const double* shift;  // per vector, indexed vec % shift_period (may be null)
+  const R* shift;       // per vector, indexed vec % shift_period (may be null)
   int shift_period;
-  double scale;
-  double kin;           // 0 or 1
-  double beta;          // 0: overwrite
+  R scale;
+  R kin;                // 0 or 1
+  R beta;               // 0: overwrite
   int coef;             // CoefKind
 };
 

@@ -1,4 +1,4 @@
-"""Davidson PDEP solve (Sec. II D) through the C ABI.
+"""Davidson PDEP solve (Sec. II C) through the C ABI.
 
 24^3 workload: the 16 most negative eigenvalues against the oracle's dense
 chi0bar eigendecomposition (1e-8 relative, FP64; 1e-6 mixed), and the

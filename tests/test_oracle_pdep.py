@@ -1,4 +1,4 @@
-"""Pins of the oracle's dense chi0bar and PDEP reference (Secs. II A, II C).
+"""Pins of the oracle's dense chi0bar and PDEP reference (Secs. II A to II C).
 
 * V = 0 closed form, diagonal in G, for closed shells (factors 4, 4 pi,
   Omega, sign and the sqrt(4 pi)/|G| symmetrisation all enter);

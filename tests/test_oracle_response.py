@@ -1,4 +1,4 @@
-"""Pins of the oracle's Sternheimer solution and density response (Sec. II D).
+"""Pins of the oracle's Sternheimer solution and density response (Sec. II C).
 
 * Sternheimer by sum over empty states = Sternheimer by CG (Eq. stern);
 * the SOS solution satisfies Eq. stern itself;
