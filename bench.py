@@ -161,8 +161,9 @@ def csrc_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_for(cls_name):
-    """ncu DRAM bytes per launch of a kernel class, if captured on the current source."""
+def traffic_for(cls_name, algorithmic_bytes_per_launch):
+    """ncu DRAM bytes per launch of a kernel class: the DRAM/algorithmic ratio of a
+    captured launch of the current source, scaled to this class's average launch."""
     try:
         t = json.load(open(TRAFFIC_FILE))
     except (OSError, ValueError):
@@ -170,14 +171,16 @@ def traffic_for(cls_name):
     if t.get("csrc_hash") != csrc_hash():
         return None
     v = t.get("classes", {}).get(cls_name)
-    return None if v is None else float(v["dram_bytes_per_launch"])
+    if v is None:
+        return None
+    return float(v["dram_over_algorithmic"]) * algorithmic_bytes_per_launch
 
 
 def roofline(prof):
     hbm, src = measured_peaks()
     best = None
     for name, c in prof["classes"].items():
-        if c["launches"] == 0 or c["ms"] <= 0:
+        if c["launches"] == 0 or c["ms"] <= 0 or (c["flops"] == 0 and c["bytes"] == 0):
             continue
         if best is None or c["ms"] > best[1]["ms"]:
             best = (name, c)
@@ -190,7 +193,7 @@ def roofline(prof):
     alu_peak = FP64_PEAK_TFLOPS if name.endswith("f64") else FP32_PEAK_TFLOPS
     f_hbm, f_alu = gbs / hbm, tfl / alu_peak
     share = c["ms"] / sum(v["ms"] for v in prof["classes"].values())
-    tr = traffic_for(name)
+    tr = traffic_for(name, c["bytes"] / c["launches"])
     if f_alu >= f_hbm:
         r = {"bound": "alu", "achieved": round(tfl, 3), "peak": round(alu_peak, 3),
              "unit": "TFLOP/s", "frac": round(f_alu, 4),
@@ -436,8 +439,11 @@ def run_small(args):
     with pg.Context(system, precision=prec) as ctx:
         dim = ctx.sizes()["n_pdep_dim"]
         phi = torch.tensor(synthetic.random_vectors(3, 16, dim), device="cuda")
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("small")   # capture filter: kernels of this call only
         out = ctx.chi0_apply(phi, allow_unconverged=True)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         print(json.dumps({"case": args.case, "norm": float(out.norm())}))
 
 
