@@ -76,6 +76,7 @@ struct SysData {
   float* d_kprec32 = nullptr;
   std::vector<double> eps;   // n_occ + 1
   double alpha = 0;          // shift of the occupied space in H - eps_v + alpha P_v
+  double vmax = 0;           // max_r V(r)
   SphereDev<double> sd{};
   SphereDev<float> sf{};
 };
@@ -599,10 +600,115 @@ int davidson(pdep_ctx* c, SysData& s, int nwant, int nconv, int nb_max, const do
 // ---------------------------------------------------------------------------
 // setup: lowest n_occ + 1 eigenpairs of H (FP64)
 // ---------------------------------------------------------------------------
+// Rayleigh-Ritz of the ns orthonormal columns of Y (HY = H Y): Ritz vectors
+// into X, H X into HX, values into theta (host), residual norms into rn (host).
+int ritz(pdep_ctx* c, SysData& s, const double* Y, const double* HY, int ns, double* X,
+         double* HX, double* R, std::vector<double>& theta, std::vector<double>& rn,
+         cudaStream_t st) {
+  double *M, *V, *th, *nr;
+  RET(ws(c, "rz_m", (size_t)ns * ns, &M));
+  RET(ws(c, "rz_v", (size_t)ns * ns, &V));
+  RET(ws(c, "rz_th", (size_t)ns, &th));
+  RET(ws(c, "rz_nr", (size_t)ns, &nr));
+  EighWork wk;
+  RET(eigh_ws(c, ns, &wk));
+  CK(gemm<double>(true, ns, ns, s.n_pw, 1.0, Y, s.ld, HY, s.ld, 0.0, M, ns, st));
+  CK(symmetrize<double>(M, ns, ns, st));
+  CK(eigh(ns, M, ns, th, V, ns, wk, st));
+  CK(gemm<double>(false, s.n_pw, ns, ns, 1.0, Y, s.ld, V, ns, 0.0, X, s.ld, st));
+  CK(gemm<double>(false, s.n_pw, ns, ns, 1.0, HY, s.ld, V, ns, 0.0, HX, s.ld, st));
+  CK(ritz_residual(HX, X, s.ld, s.n_pw, ns, th, R, st));
+  CK(col_norms<double>(R, s.ld, s.n_pw, ns, nr, st));
+  theta.resize(ns);
+  rn.resize(ns);
+  CK(cudaMemcpyAsync(theta.data(), th, sizeof(double) * ns, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(rn.data(), nr, sizeof(double) * ns, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return PDEP_OK;
+}
+
+// Orthonormalise the ns columns of Y in place (into OUT); refill dropped
+// directions with seeded random vectors orthogonal to the kept ones.
+int orthonormalize_full(pdep_ctx* c, SysData& s, double* Y, int ns, double* OUT,
+                        unsigned long long seed, cudaStream_t st) {
+  int kept = 0;
+  RET(orthonormalize(c, s, nullptr, 0, Y, ns, OUT, &kept, st));
+  for (int tries = 0; kept < ns && tries < 4; ++tries) {
+    const int miss = ns - kept;
+    CK(philox_normal(Y, s.ld, s.n_pw, miss, seed + 7919ULL * (tries + 1), 0ULL, st));
+    int k2 = 0;
+    RET(orthonormalize(c, s, OUT, kept, Y, miss, OUT + (size_t)kept * s.ld, &k2, st));
+    kept += k2;
+  }
+  if (kept < ns) return fail(PDEP_ERR_NOT_CONVERGED, "could not complete an orthonormal block");
+  return PDEP_OK;
+}
+
+// Lowest n_occ + 1 eigenpairs of H by Chebyshev-filtered subspace iteration
+// (Zhou, Saad, Tiago, Chelikowsky, J. Comput. Phys. 219, 172 (2006)): each
+// pass applies a degree-m Chebyshev polynomial that damps [a, b] (a = the
+// block's largest Ritz value, b >= the top of the spectrum) to the whole
+// block, then orthonormalises and does Rayleigh-Ritz.
+int chfsi(pdep_ctx* c, SysData& s, int ns, int nconv, double tol, int max_iter, double* X,
+          std::vector<double>& theta, int* iters, cudaStream_t st) {
+  double *Y, *Z, *HY, *HX, *R;
+  RET(ws(c, "cf_y", (size_t)ns * s.ld, &Y));
+  RET(ws(c, "cf_z", (size_t)ns * s.ld, &Z));
+  RET(ws(c, "cf_hy", (size_t)ns * s.ld, &HY));
+  RET(ws(c, "cf_hx", (size_t)ns * s.ld, &HX));
+  RET(ws(c, "cf_r", (size_t)ns * s.ld, &R));
+  // upper bound of the spectrum: max kinetic + max potential
+  double tmax = 0.0;
+  for (double g : s.g2) tmax = std::max(tmax, 0.5 * g);
+  const double b = tmax + s.vmax + 1e-3 * (1.0 + std::fabs(tmax));
+  std::vector<double> rn;
+  // Rayleigh-Ritz of the start block (X is orthonormal on entry)
+  RET(apply_h<double>(c, s, X, HY, ns, nullptr, 0, false, false, st));
+  CK(cudaMemcpy2DAsync(Y, s.ld * sizeof(double), X, s.ld * sizeof(double),
+                       s.n_pw * sizeof(double), ns, cudaMemcpyDeviceToDevice, st));
+  RET(ritz(c, s, Y, HY, ns, X, HX, R, theta, rn, st));
+  const int degree = 10;
+  for (int it = 0; it < max_iter; ++it) {
+    double mres = 0.0;
+    for (int i = 0; i < nconv; ++i) mres = std::max(mres, rn[i]);
+    *iters = it;
+    if (mres <= tol) return PDEP_OK;
+    const double a = theta[ns - 1], a0 = theta[0];
+    const double e = 0.5 * (b - a), cc = 0.5 * (b + a);
+    double sigma = e / (a0 - cc);
+    const double tau = 2.0 / sigma;
+    // Y = (H X - c X) sigma / e   (H X is HX from the last Rayleigh-Ritz)
+    CK(cheb_step(Y, HX, X, nullptr, s.ld, s.n_pw, ns, sigma / e, cc, 0.0, st));
+    double* prev = X;   // X is overwritten as the recurrence advances
+    double* cur = Y;
+    double* nxt = Z;
+    for (int k = 2; k <= degree; ++k) {
+      const double sig2 = 1.0 / (tau - sigma);
+      RET(apply_h<double>(c, s, cur, HY, ns, nullptr, 0, false, false, st));
+      CK(cheb_step(nxt, HY, cur, prev, s.ld, s.n_pw, ns, 2.0 * sig2 / e, cc, -sigma * sig2, st));
+      double* t = prev;
+      prev = cur;
+      cur = nxt;
+      nxt = t;
+      sigma = sig2;
+    }
+    // cur holds the filtered block; orthonormalise it into a buffer that is
+    // neither cur nor X (the Rayleigh-Ritz below writes X)
+    double* out = (cur == Y) ? Z : Y;
+    RET(orthonormalize_full(c, s, cur, ns, out, c->opt.seed + 31ULL * it, st));
+    RET(apply_h<double>(c, s, out, HY, ns, nullptr, 0, false, false, st));
+    RET(ritz(c, s, out, HY, ns, X, HX, R, theta, rn, st));
+  }
+  *iters = max_iter;
+  double mres = 0.0;
+  for (int i = 0; i < nconv; ++i) mres = std::max(mres, rn[i]);
+  return mres <= tol ? PDEP_OK : fail(PDEP_ERR_NOT_CONVERGED, "setup eigensolver did not converge");
+}
+
 int setup_states(pdep_ctx* c, SysData& s, cudaStream_t st) {
   const int nocc = s.n_occ;
-  const int ns = std::min(s.n_pw, nocc + std::max(4, nocc / 8));
   if (nocc + 1 > s.n_pw) return fail(PDEP_ERR_INVALID_ARG, "n_occ too large for the basis");
+  const int ns = std::min(s.n_pw, nocc + std::max(16, nocc / 4));
   // start vectors: plane waves of lowest kinetic energy plus small noise
   std::vector<std::pair<double, int>> comps;
   comps.push_back({0.0, 2 * s.n_half});
@@ -614,32 +720,17 @@ int setup_states(pdep_ctx* c, SysData& s, cudaStream_t st) {
   std::vector<int> hc(ns);
   for (int i = 0; i < ns; ++i) hc[i] = comps[i].second;
   int* dcomp;
-  double *X0, *X, *ek;
+  double *X0, *X;
   RET(ws(c, "su_comp", ns, &dcomp));
   RET(ws(c, "su_x0", (size_t)ns * s.ld, &X0));
   RET(ws(c, "su_x", (size_t)ns * s.ld, &X));
-  RET(ws(c, "su_ek", (size_t)ns, &ek));
   CK(cudaMemcpyAsync(dcomp, hc.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st));
   CK(unit_start(X0, s.ld, s.n_pw, dcomp, ns, 1e-3, c->opt.seed ^ 0x5eed5eedULL, st));
-  OpFn op = [&](const double* in, double* outv, int m) -> int {
-    return apply_h<double>(c, s, in, outv, m, nullptr, 0, false, false, st);
-  };
-  double* xt;
-  RET(ws(c, "su_xt", (size_t)ns * s.ld, &xt));
-  // Teter-Payne-Allan preconditioner scaled by each Ritz vector's kinetic energy
-  PrecFn prec = [&](double* T, int m, const int* d_idx, const double* Xr) -> int {
-    CK(gather_cols(Xr, s.ld, xt, s.ld, s.n_pw, d_idx, m, st));
-    CK(kinetic_energy(xt, s.ld, s.n_half, m, s.d_g2, ek, st));
-    CK(precondition_tpa(T, s.ld, s.n_pw, s.n_half, m, s.d_g2, ek, st));
-    return (int)PDEP_OK;
-  };
-  std::vector<double> th(ns);
-  DavidsonOut dout;
+  RET(orthonormalize_full(c, s, X0, ns, X, c->opt.seed ^ 0x0f0fULL, st));
+  std::vector<double> th;
   const int nwant = nocc + 1;
-  RET(davidson(c, s, ns, nwant, 4 * ns, X0, ns, c->opt.setup_tol, false, c->opt.setup_max_iter,
-               -1, op, prec, X, th.data(), &dout, st));
-  if (!dout.converged)
-    return fail(PDEP_ERR_NOT_CONVERGED, "setup eigensolver did not converge");
+  int its = 0;
+  RET(chfsi(c, s, ns, nwant, c->opt.setup_tol, c->opt.setup_max_iter, X, th, &its, st));
   s.eps.assign(th.begin(), th.begin() + nwant);
   const double gap = s.eps[nocc] - s.eps[nocc - 1];
   if (!(gap >= c->opt.gap_min)) return fail(PDEP_ERR_NO_GAP, "HOMO-LUMO gap below gap_min");
@@ -1162,8 +1253,11 @@ int pdep_setup(const pdep_system_desc* sys, int n_sys, const pdep_options* opt, 
             cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
       return bail(fail(PDEP_ERR_CUDA, "potential check"));
-    for (double v : hv)
+    s.vmax = -1e300;
+    for (double v : hv) {
       if (!std::isfinite(v)) return bail(fail(PDEP_ERR_NONFINITE, "non-finite potential"));
+      s.vmax = std::max(s.vmax, v);
+    }
     r = setup_states(c, s, st);
     if (r != PDEP_OK) return bail(r);
   }

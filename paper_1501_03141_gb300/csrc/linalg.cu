@@ -987,6 +987,25 @@ cudaError_t unit_start(double* X, long long ld, int rows, const int* comp, int n
   { count_launch(); k_unit_start<<<n, 256, 0, st>>>(X, ld, rows, comp, amp); }
   return cudaGetLastError();
 }
+__global__ void k_cheb_step(double* Ynew, const double* __restrict__ HY,
+                            const double* __restrict__ Y, const double* __restrict__ X,
+                            long long ld, int rows, double a1, double c, double b1) {
+  const long long o = (long long)blockIdx.y * ld;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
+    const double xv = X ? X[o + r] : 0.0;
+    Ynew[o + r] = a1 * (HY[o + r] - c * Y[o + r]) + b1 * xv;
+  }
+}
+cudaError_t cheb_step(double* Ynew, const double* HY, const double* Y, const double* X,
+                      long long ld, int rows, int n, double a1, double c, double b1,
+                      cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  dim3 grid((rows + 255) / 256, n);
+  count_launch();
+  k_cheb_step<<<grid, 256, 0, st>>>(Ynew, HY, Y, X, ld, rows, a1, c, b1);
+  return cudaGetLastError();
+}
+
 __global__ void k_zero_row(double* X, long long ld, int row, int n) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     X[(long long)i * ld + row] = 0.0;

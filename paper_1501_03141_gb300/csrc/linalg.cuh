@@ -127,6 +127,10 @@ cudaError_t gather_cols(const double* X, long long ldx, double* Y, long long ldy
 // X[comp[i], i] = 1 plus amp * Philox normal noise on every component
 cudaError_t unit_start(double* X, long long ld, int rows, const int* comp, int n, double amp,
                        unsigned long long seed, cudaStream_t st);
+// Chebyshev filter step: Ynew = a1 * (HY - c Y) + b1 * X  (n columns, rows entries)
+cudaError_t cheb_step(double* Ynew, const double* HY, const double* Y, const double* X,
+                      long long ld, int rows, int n, double a1, double c, double b1,
+                      cudaStream_t st);
 // X[row, i] = 0 for every column i (e.g. the G = 0 slot of PDEP vectors)
 cudaError_t zero_row(double* X, long long ld, int row, int n, cudaStream_t st);
 
