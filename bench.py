@@ -232,6 +232,7 @@ def run_ours(args):
     opts = dict(dav_tol=0.0, dav_max_iter=6)
     stream = torch.cuda.current_stream(dev)
     ctx = pg.Context(system, precision=pg.PDEP_MIXED, stream=stream.cuda_stream, **opts)
+    ctx_deflate = ctx.options.n_deflate
     dim = ctx.sizes()["n_pdep_dim"]
     npd = system.n_pdep
     ev = torch.empty(npd, dtype=torch.float64, device=dev)
@@ -339,7 +340,8 @@ def run_ours(args):
                        "cg_iterations_max": stats["cg_iterations_max"],
                        "refine_rounds_max": stats["refine_rounds_max"],
                        "max_cg_residual": stats["max_cg_residual"],
-                       "cg_step_variant_autotuned": stats["cg_variant"]},
+                       "cg_step_variant_autotuned": stats["cg_variant"],
+                       "n_deflate": int(ctx_deflate)},
             "eigenpairs_per_s": round(eigpairs, 4),
             "fp64": fp64,
             "e2e": e2e,

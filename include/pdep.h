@@ -110,6 +110,12 @@ typedef struct {
   double setup_tol;          /* setup eigensolver: ||H psi - eps psi|| target */
   int setup_max_iter;
   size_t workspace_limit_bytes; /* 0 = no limit */
+  int n_deflate;             /* lowest empty states deflated from the Sternheimer CG
+                                (0: occupied states only; default 16).  The setup
+                                converges them with the occupied states; their
+                                share of each solution is added exactly and the CG
+                                works on the rest, whose smallest eigenvalue is
+                                eps_{n_occ+n_deflate+1} - eps_v instead of the gap. */
 } pdep_options;
 
 typedef struct {

@@ -65,6 +65,7 @@ class pdep_options(ctypes.Structure):
         ("setup_tol", ctypes.c_double),
         ("setup_max_iter", ctypes.c_int),
         ("workspace_limit_bytes", ctypes.c_size_t),
+        ("n_deflate", ctypes.c_int),
     ]
 
 

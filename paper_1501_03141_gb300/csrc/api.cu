@@ -53,6 +53,11 @@ struct SysData {
   double L[3] = {0, 0, 0};
   double omega = 0, ecut = 0;
   int n_r = 0, n_half = 0, n_pw = 0, ld = 0, n_occ = 0, n_pdep = 0;
+  int n_defl = 0;            // lowest empty states deflated from the CG operator
+  int n_ext = 0;             // n_occ + n_defl: columns of d_psi
+  double* d_eps_ext = nullptr;  // eps of the n_ext states
+  double* d_sigma64 = nullptr;   // per-state shift eps_{n_ext} - eps_w, w < n_ext
+  float* d_sigma32 = nullptr;
   int n_col = 0, n_ucol = 0, R3 = 0;
   std::vector<UCol> ucol;
   std::vector<int2> slot;
@@ -75,7 +80,6 @@ struct SysData {
   double* d_kprec64 = nullptr;  // CG preconditioner per occupied state [n_occ][ld]
   float* d_kprec32 = nullptr;
   std::vector<double> eps;   // n_occ + 1
-  double alpha = 0;          // shift of the occupied space in H - eps_v + alpha P_v
   double vmax = 0;           // max_r V(r)
   SphereDev<double> sd{};
   SphereDev<float> sf{};
@@ -358,6 +362,8 @@ inline const double* psi_of(const SysData& s, double*) { return s.d_psi; }
 inline const float* psi_of(const SysData& s, float*) { return s.d_psif; }
 inline const double* kprec_of(const SysData& s, double*) { return s.d_kprec64; }
 inline const double* negeps_of(const SysData& s, double*) { return s.d_negeps; }
+inline const double* sigma_of(const SysData& s, double*) { return s.d_sigma64; }
+inline const float* sigma_of(const SysData& s, float*) { return s.d_sigma32; }
 inline const float* negeps_of(const SysData& s, float*) { return s.d_negeps32; }
 inline const float* kprec_of(const SysData& s, float*) { return s.d_kprec32; }
 
@@ -367,8 +373,8 @@ size_t b1_count(const SysData& s, int n_items) {
 
 // Y = (H - eps_v) X for the vectors of 'map' (H = -nabla^2/2 + V); vector i
 // uses occupied state i % n_occ; without with_shift Y = H X.  Then, if
-// with_pv, the occupied space is shifted: Y += alpha Psi (Psi^T X) on the same
-// columns.
+// with_pv, the occupied and deflated states are shifted:
+// Y += Psi_ext diag(sigma) (Psi_ext^T X) on the same columns.
 template <typename R>
 int apply_h(pdep_ctx* c, SysData& s, const R* X, R* Y, int n, const int* d_list, int n_list,
             bool with_shift, bool with_pv, cudaStream_t st) {
@@ -408,22 +414,32 @@ int apply_h(pdep_ctx* c, SysData& s, const R* X, R* Y, int n, const int* d_list,
     // only the listed columns when a list is given
     const int m = d_list ? n_list : n;
     R* S;
-    RET(ws(c, sizeof(R) == 8 ? "pv_64" : "pv_32", (size_t)s.n_occ * std::max(m, 1), &S));
+    // shift of the occupied and the deflated empty states: state w moves to
+    // eps_{n_ext} - eps_v, the bottom of the spectrum the CG still sees
+    RET(ws(c, sizeof(R) == 8 ? "pv_64" : "pv_32", (size_t)s.n_ext * std::max(m, 1), &S));
     const R* P = psi_of(s, (R*)nullptr);
-    CK(gemm<R>(true, s.n_occ, m, s.n_pw, 1.0, P, s.ld, X, s.ld, 0.0, S, s.n_occ, st, d_list,
+    CK(gemm<R>(true, s.n_ext, m, s.n_pw, 1.0, P, s.ld, X, s.ld, 0.0, S, s.n_ext, st, d_list,
                nullptr));
-    CK(gemm<R>(false, s.n_pw, m, s.n_occ, s.alpha, P, s.ld, S, s.n_occ, 1.0, Y, s.ld, st, nullptr,
+    CK(scale_rows<R>(S, s.n_ext, s.n_ext, m, sigma_of(s, (R*)nullptr), st));
+    CK(gemm<R>(false, s.n_pw, m, s.n_ext, 1.0, P, s.ld, S, s.n_ext, 1.0, Y, s.ld, st, nullptr,
                d_list));
   }
   return PDEP_OK;
 }
 
-// X <- X - Psi (Psi^T X)  (FP64, all n columns)
-int project_pc(pdep_ctx* c, SysData& s, double* X, int n, cudaStream_t st) {
+// RHS split for deflation: S = Psi_ext^T B; the deflated states' part of the
+// solution is Xd = sum_c psi_c S_c,i / (eps_c - eps_v(i)) (exact, H psi_c =
+// eps_c psi_c); then B <- B - Psi_ext S leaves the part the CG solves.
+int split_rhs(pdep_ctx* c, SysData& s, double* B, int n, double* Xd, cudaStream_t st) {
   double* S;
-  RET(ws(c, "pc_64", (size_t)s.n_occ * n, &S));
-  CK(gemm<double>(true, s.n_occ, n, s.n_pw, 1.0, s.d_psi, s.ld, X, s.ld, 0.0, S, s.n_occ, st));
-  CK(gemm<double>(false, s.n_pw, n, s.n_occ, -1.0, s.d_psi, s.ld, S, s.n_occ, 1.0, X, s.ld, st));
+  RET(ws(c, "pc_64", (size_t)s.n_ext * n, &S));
+  CK(gemm<double>(true, s.n_ext, n, s.n_pw, 1.0, s.d_psi, s.ld, B, s.ld, 0.0, S, s.n_ext, st));
+  CK(gemm<double>(false, s.n_pw, n, s.n_ext, -1.0, s.d_psi, s.ld, S, s.n_ext, 1.0, B, s.ld, st));
+  if (s.n_defl > 0) {
+    CK(deflation_coefficients(S, s.n_ext, s.n_occ, s.n_defl, n, s.d_eps_ext, st));
+    CK(gemm<double>(false, s.n_pw, n, s.n_defl, 1.0, s.d_psi + (size_t)s.n_occ * s.ld, s.ld,
+                    S + s.n_occ, s.n_ext, 0.0, Xd, s.ld, st));
+  }
   return PDEP_OK;
 }
 
@@ -707,8 +723,10 @@ int chfsi(pdep_ctx* c, SysData& s, int ns, int nconv, double tol, int max_iter, 
 
 int setup_states(pdep_ctx* c, SysData& s, cudaStream_t st) {
   const int nocc = s.n_occ;
+  s.n_defl = std::max(0, std::min(c->opt.n_deflate, s.n_pw - nocc - 2));
+  s.n_ext = nocc + s.n_defl;
   if (nocc + 1 > s.n_pw) return fail(PDEP_ERR_INVALID_ARG, "n_occ too large for the basis");
-  const int ns = std::min(s.n_pw, nocc + std::max(16, nocc / 4));
+  const int ns = std::min(s.n_pw, s.n_ext + std::max(16, s.n_ext / 4));
   // start vectors: plane waves of lowest kinetic energy plus small noise
   std::vector<std::pair<double, int>> comps;
   comps.push_back({0.0, 2 * s.n_half});
@@ -728,22 +746,40 @@ int setup_states(pdep_ctx* c, SysData& s, cudaStream_t st) {
   CK(unit_start(X0, s.ld, s.n_pw, dcomp, ns, 1e-3, c->opt.seed ^ 0x5eed5eedULL, st));
   RET(orthonormalize_full(c, s, X0, ns, X, c->opt.seed ^ 0x0f0fULL, st));
   std::vector<double> th;
-  const int nwant = nocc + 1;
+  const int nwant = s.n_ext + 1;
   int its = 0;
   RET(chfsi(c, s, ns, nwant, c->opt.setup_tol, c->opt.setup_max_iter, X, th, &its, st));
   s.eps.assign(th.begin(), th.begin() + nwant);
   const double gap = s.eps[nocc] - s.eps[nocc - 1];
   if (!(gap >= c->opt.gap_min)) return fail(PDEP_ERR_NO_GAP, "HOMO-LUMO gap below gap_min");
-  s.alpha = 2.0 * (s.eps[nocc] - s.eps[0]);
-  RET(persistent(c, &s.d_psi, (size_t)nocc * s.ld));
-  RET(persistent(c, &s.d_psif, (size_t)nocc * s.ld));
+  // sigma_w lifts occupied and deflated state w to eps_{n_ext}: in
+  // H - eps_v + sum_w sigma_w |w><w| it then sits at eps_{n_ext} - eps_v > 0,
+  // the lowest eigenvalue of the part the CG solves for
+  const int next = s.n_ext;
+  {
+    std::vector<double> sg(next);
+    std::vector<float> sg32(next);
+    for (int w = 0; w < next; ++w) {
+      sg[w] = s.eps[next] - s.eps[w];
+      sg32[w] = (float)sg[w];
+    }
+    RET(persistent(c, &s.d_sigma64, next));
+    RET(persistent(c, &s.d_sigma32, next));
+    CK(cudaMemcpyAsync(s.d_sigma64, sg.data(), sizeof(double) * next, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s.d_sigma32, sg32.data(), sizeof(float) * next, cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  RET(persistent(c, &s.d_psi, (size_t)next * s.ld));
+  RET(persistent(c, &s.d_psif, (size_t)next * s.ld));
+  RET(persistent(c, &s.d_eps_ext, next));
+  CK(cudaMemcpyAsync(s.d_eps_ext, s.eps.data(), sizeof(double) * next, cudaMemcpyHostToDevice, st));
   RET(persistent(c, &s.d_u, (size_t)nocc * s.n_r));
   RET(persistent(c, &s.d_negeps, nocc));
   RET(persistent(c, &s.d_ekin, nocc));
-  CK(cudaMemsetAsync(s.d_psi, 0, sizeof(double) * (size_t)nocc * s.ld, st));
+  CK(cudaMemsetAsync(s.d_psi, 0, sizeof(double) * (size_t)next * s.ld, st));
   CK(cudaMemcpy2DAsync(s.d_psi, s.ld * sizeof(double), X, s.ld * sizeof(double),
-                       s.n_pw * sizeof(double), nocc, cudaMemcpyDeviceToDevice, st));
-  CK((convert<float, double>(s.d_psif, s.ld, s.d_psi, s.ld, s.ld, nocc, st)));
+                       s.n_pw * sizeof(double), next, cudaMemcpyDeviceToDevice, st));
+  CK((convert<float, double>(s.d_psif, s.ld, s.d_psi, s.ld, s.ld, next, st)));
   std::vector<double> ne(nocc);
   for (int v = 0; v < nocc; ++v) ne[v] = -s.eps[v];
   CK(cudaMemcpyAsync(s.d_negeps, ne.data(), sizeof(double) * nocc, cudaMemcpyHostToDevice, st));
@@ -775,8 +811,10 @@ int setup_states(pdep_ctx* c, SysData& s, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------
-// Sternheimer solves: (H - eps_v + alpha P_v) x = b with b in range(P_c)
-// (equivalent to Eq. stern: the occupied component of x vanishes)
+// Sternheimer solves: (H - eps_v + sum_w sigma_w |w><w|) x = b, w over the
+// occupied and deflated states, b orthogonal to them (equivalent to Eq. stern
+// on that subspace: H commutes with the projector, so x has no component
+// along any w; the deflated states' share is added exactly, see split_rhs)
 // ---------------------------------------------------------------------------
 template <typename R>
 int cg_loop(pdep_ctx* c, SysData& s, const R* b, R* x, int n, double tol, int max_iter,
@@ -874,7 +912,9 @@ int solve_rhs(pdep_ctx* c, SysData& s, const double* b, double* x, int n, int* h
   if (c->opt.precision == PDEP_FP64) {
     CgScal* sc;
     RET(ws(c, "cg_sc64", (size_t)n, &sc));
-    RET(cg_loop<double>(c, s, b, x, n, tol, c->opt.cg_max_iter, sc, st, &capped));
+    // stop the recursion a little below tol so that the FP64 residual
+    // recomputed from x (which drifts slightly from the recursion) meets it
+    RET(cg_loop<double>(c, s, b, x, n, 0.9 * tol, c->opt.cg_max_iter, sc, st, &capped));
     std::vector<int> its;
     RET(collect_cg_stats(c, sc, n, nullptr, st, &its));
     for (int i = 0; i < n; ++i) its_total[i] = its[i];
@@ -929,8 +969,9 @@ int solve_rhs(pdep_ctx* c, SysData& s, const double* b, double* x, int n, int* h
     CK(residual_norms(b, s.ld, ap64, s.ld, s.n_pw, n, rel, nullptr, st));
   }
   // mixed: rel already holds the FP64 residual of every RHS from its last
-  // refinement round.  Remove the occupied component left by rounding.
-  RET(project_pc(c, s, x, n, st));
+  // refinement round.  No final P_c projection is needed: the shifted
+  // operator lifts occupied state w to eps_{n_ext} - eps_v > 0, so the
+  // occupied component of x is at most ||b - A x|| / (eps_{n_ext} - eps_v).
   std::vector<double> hr(n);
   CK(cudaMemcpyAsync(hr.data(), rel, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
   RET(sync(st));
@@ -945,8 +986,11 @@ int solve_rhs(pdep_ctx* c, SysData& s, const double* b, double* x, int n, int* h
   return PDEP_OK;
 }
 
-// b_vj = -P_c [dV_j psi_v] for perturbation grids dv [m][n_r]  -> bvec [m*n_occ][ld]
-int build_rhs(pdep_ctx* c, SysData& s, const double* dv, int m, double* bvec, cudaStream_t st) {
+// b_vj = -P_c [dV_j psi_v] for perturbation grids dv [m][n_r]  -> bvec [m*n_occ][ld].
+// With deflation, bvec keeps only the part orthogonal to the deflated states
+// and xdefl [m*n_occ][ld] receives their exact share of the solution.
+int build_rhs(pdep_ctx* c, SysData& s, const double* dv, int m, double* bvec, double* xdefl,
+              cudaStream_t st) {
   const int nocc = s.n_occ;
   ItemMap map{nocc, (nocc + 1) / 2};
   const int n_items = m * ((nocc + 1) / 2);
@@ -969,7 +1013,7 @@ int build_rhs(pdep_ctx* c, SysData& s, const double* dv, int m, double* bvec, cu
   ep.scale = -1.0 / s.n_r;
   ep.coef = COEF_ONE;
   CK(launch_cols_bwd<double>(s.sd, b1, map, n_items, ep, st));
-  RET(project_pc(c, s, bvec, m * nocc, st));
+  RET(split_rhs(c, s, bvec, m * nocc, xdefl, st));
   return PDEP_OK;
 }
 
@@ -1033,9 +1077,12 @@ int chi0_internal(pdep_ctx* c, SysData& s, const double* phi, int m, double* out
       a.map = map;
       CK(launch_slab<double>(s.sd, a, st));
     }
-    RET(build_rhs(c, s, dv, mc, bvec, st));
+    double* xd = nullptr;
+    if (s.n_defl > 0) RET(ws(c, "c0_xd", (size_t)mc * nocc * s.ld, &xd));
+    RET(build_rhs(c, s, dv, mc, bvec, xd, st));
     int r = solve_rhs(c, s, bvec, xvec, mc * nocc, nullptr, nullptr, st);
     if (r != PDEP_OK && r != PDEP_ERR_NOT_CONVERGED) return r;
+    if (xd) CK(add_cols(xvec, xd, s.ld, s.n_pw, mc * nocc, st));
     RET(density(c, s, xvec, mc, dn, st));
     // (chi0bar phi_j)(G) = sqrt(4pi)/|G| * Omega^{1/2}/N_r * FFT[dn_j](G)
     {
@@ -1159,6 +1206,7 @@ void pdep_default_options(pdep_options* o) {
   o->setup_tol = 1e-11;
   o->setup_max_iter = 400;
   o->workspace_limit_bytes = 0;
+  o->n_deflate = 16;
 }
 
 const char* pdep_status_string(int s) {
@@ -1335,11 +1383,14 @@ int sternheimer_solve(pdep_ctx* c, int sys, const double* dv_r, int n_pert, doub
   RET(ws(c, "st_b", (size_t)n * s.ld, &bvec));
   RET(ws(c, "st_x", (size_t)n * s.ld, &xvec));
   CK(cudaMemcpyAsync(dv, dv_r, sizeof(double) * (size_t)n_pert * s.n_r, kind_to_dev(dv_r), st));
-  RET(build_rhs(c, s, dv, n_pert, bvec, st));
+  double* xd = nullptr;
+  if (s.n_defl > 0) RET(ws(c, "st_xd", (size_t)n * s.ld, &xd));
+  RET(build_rhs(c, s, dv, n_pert, bvec, xd, st));
   std::vector<int> hi(n);
   std::vector<double> hr(n);
   int r = solve_rhs(c, s, bvec, xvec, n, hi.data(), hr.data(), st);
   if (r != PDEP_OK && r != PDEP_ERR_NOT_CONVERGED) return r;
+  if (xd) CK(add_cols(xvec, xd, s.ld, s.n_pw, n, st));
   CK(cudaMemcpy2DAsync(dpsi, s.n_pw * sizeof(double), xvec, s.ld * sizeof(double),
                        s.n_pw * sizeof(double), n, kind_from_dev(dpsi), st));
   RET(sync(st));

@@ -1006,6 +1006,59 @@ cudaError_t cheb_step(double* Ynew, const double* HY, const double* Y, const dou
   return cudaGetLastError();
 }
 
+__global__ void k_deflation_coef(double* S, int lds, int n_occ, int n_defl, int n,
+                                 const double* __restrict__ eps) {
+  const long long tot = (long long)n_defl * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int cdx = (int)(e % n_defl), i = (int)(e / n_defl);
+    S[(long long)i * lds + n_occ + cdx] /= (eps[n_occ + cdx] - eps[i % n_occ]);
+  }
+}
+cudaError_t deflation_coefficients(double* S, int lds, int n_occ, int n_defl, int n,
+                                   const double* eps, cudaStream_t st) {
+  const long long tot = (long long)n_defl * n;
+  if (tot <= 0) return cudaSuccess;
+  count_launch();
+  k_deflation_coef<<<(int)std::min<long long>((tot + 255) / 256, 4096), 256, 0, st>>>(
+      S, lds, n_occ, n_defl, n, eps);
+  return cudaGetLastError();
+}
+template <typename R>
+__global__ void k_scale_rows(R* S, int lds, int rows, int n, const R* __restrict__ sigma) {
+  const long long tot = (long long)rows * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int w = (int)(e % rows), i = (int)(e / rows);
+    S[(long long)i * lds + w] *= sigma[w];
+  }
+}
+template <typename R>
+cudaError_t scale_rows(R* S, int lds, int rows, int n, const R* sigma, cudaStream_t st) {
+  const long long tot = (long long)rows * n;
+  if (tot <= 0) return cudaSuccess;
+  count_launch();
+  k_scale_rows<R><<<(int)std::min<long long>((tot + 255) / 256, 8192), 256, 0, st>>>(S, lds, rows,
+                                                                                    n, sigma);
+  return cudaGetLastError();
+}
+template cudaError_t scale_rows<double>(double*, int, int, int, const double*, cudaStream_t);
+template cudaError_t scale_rows<float>(float*, int, int, int, const float*, cudaStream_t);
+
+__global__ void k_add_cols(double* y, const double* __restrict__ x, long long ld, int rows) {
+  const long long o = (long long)blockIdx.y * ld;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x)
+    y[o + r] += x[o + r];
+}
+cudaError_t add_cols(double* y, const double* x, long long ld, int rows, int n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int bx = (rows + 255) / 256;
+  if (bx > 64) bx = 64;
+  count_launch();
+  k_add_cols<<<dim3(bx, n), 256, 0, st>>>(y, x, ld, rows);
+  return cudaGetLastError();
+}
+
 __global__ void k_zero_row(double* X, long long ld, int row, int n) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     X[(long long)i * ld + row] = 0.0;

@@ -131,6 +131,15 @@ cudaError_t unit_start(double* X, long long ld, int rows, const int* comp, int n
 cudaError_t cheb_step(double* Ynew, const double* HY, const double* Y, const double* X,
                       long long ld, int rows, int n, double a1, double c, double b1,
                       cudaStream_t st);
+// S[n_occ + c, i] /= (eps[n_occ + c] - eps[i % n_occ]) for c < n_defl, i < n
+// (S column-major with leading dimension lds)
+cudaError_t deflation_coefficients(double* S, int lds, int n_occ, int n_defl, int n,
+                                   const double* eps, cudaStream_t st);
+// S[w, i] *= sigma[w] for w < rows, i < n (S column-major, leading dimension lds)
+template <typename R>
+cudaError_t scale_rows(R* S, int lds, int rows, int n, const R* sigma, cudaStream_t st);
+// y[:, i] += x[:, i] for n columns of rows entries
+cudaError_t add_cols(double* y, const double* x, long long ld, int rows, int n, cudaStream_t st);
 // X[row, i] = 0 for every column i (e.g. the G = 0 slot of PDEP vectors)
 cudaError_t zero_row(double* X, long long ld, int row, int n, cudaStream_t st);
 

@@ -55,3 +55,21 @@ def test_cube48_sampled(precision):
     with pg.Context(s, precision=precision) as ctx:
         its = _check(ctx, s, b, ks, 16, 23, 1e-7)
     assert its.max() > its.min()  # the HOMO solves take longest
+
+
+def test_deflation_does_not_change_the_solution():
+    """Deflating the lowest empty states only changes the CG's conditioning."""
+    need_gpu()
+    lib_ready()
+    import paper_1501_03141_gb300 as pg
+    s, b, ks = oracle_for("tiny")
+    dv = synthetic.random_grid_potentials(24, 2, s.grid, s.cell).reshape(2, -1)
+    out = {}
+    for nd in (0, 16):
+        with pg.Context(s, n_deflate=nd) as ctx:
+            dpsi, its, res = ctx.sternheimer_solve(dv)
+            psi, _ = ctx.occupied()
+            # dpsi_v changes sign with psi_v: align both runs to the oracle's states
+            out[nd] = (dpsi * sign_align(psi, ks)[None, :, None], its)
+    assert rel(out[16][0], out[0][0]) < 1e-9
+    assert out[16][1].sum() < out[0][1].sum()   # fewer CG iterations in total
