@@ -347,7 +347,9 @@ def run_ours(args):
             "e2e": e2e,
             "gpu_launches": int(prof["launches"]),
             "roofline": roofline(prof),
-            "kernel_profile": {k: {"launches": v["launches"], "ms": round(v["ms"], 2)}
+            "kernel_profile": {k: {"launches": v["launches"], "ms": round(v["ms"], 2),
+                                   "tflops": round(v["flops"] / v["ms"] / 1e9, 3) if v["ms"] else None,
+                                   "gbs": round(v["bytes"] / v["ms"] / 1e6, 1) if v["ms"] else None}
                                for k, v in prof["classes"].items() if v["launches"]},
             "clocks": clk,
             "cpu_baseline": cpu,

@@ -186,11 +186,25 @@ __device__ __forceinline__ void fft_a2b(cpx<R> (&v)[N / TPL], int t, const cpx<R
       const int L = 2 * half;
       const int j = t & (half - 1);
       const bool up = (t & half) != 0;
-      const cpx<R> W = table_w<R, S>(tw, j * (N / L));
+      const R sgn = up ? R(-1) : R(1);
+      if (L <= 4) {
+        // twiddles of 2- and 4-point butterflies are 1 and S*i: one fused
+        // +-1 multiply-add per component, then a swap for j = 1 (upper lanes)
+        const bool rot = up && j == 1;
 #pragma unroll
-      for (int i = 0; i < M; ++i) {
-        cpx<R> p = shfl_xor(v[i], half);
-        v[i] = up ? (p - v[i]) * W : v[i] + p;
+        for (int i = 0; i < M; ++i) {
+          const cpx<R> p = shfl_xor(v[i], half);
+          const cpx<R> d = mk(p.x + sgn * v[i].x, p.y + sgn * v[i].y);
+          v[i] = rot ? mul_si<R, S>(d) : d;
+        }
+      } else {
+        const cpx<R> W = table_w<R, S>(tw, j * (N / L));
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+          cpx<R> p = shfl_xor(v[i], half);
+          const cpx<R> d = mk(p.x + sgn * v[i].x, p.y + sgn * v[i].y);
+          v[i] = up ? d * W : d;
+        }
       }
     }
   }
@@ -206,12 +220,23 @@ __device__ __forceinline__ void fft_b2a(cpx<R> (&v)[N / TPL], int t, const cpx<R
       const int L = 2 * half;
       const int j = t & (half - 1);
       const bool up = (t & half) != 0;
-      const cpx<R> W = table_w<R, S>(tw, j * (N / L));
+      const R sgn = up ? R(-1) : R(1);
+      if (L <= 4) {
+        const bool rot = up && j == 1;
 #pragma unroll
-      for (int i = 0; i < M; ++i) {
-        cpx<R> own = up ? v[i] * W : v[i];
-        cpx<R> p = shfl_xor(own, half);
-        v[i] = up ? p - own : own + p;
+        for (int i = 0; i < M; ++i) {
+          const cpx<R> own = rot ? mul_si<R, S>(v[i]) : v[i];
+          const cpx<R> p = shfl_xor(own, half);
+          v[i] = mk(p.x + sgn * own.x, p.y + sgn * own.y);
+        }
+      } else {
+        const cpx<R> W = table_w<R, S>(tw, j * (N / L));
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+          const cpx<R> own = up ? v[i] * W : v[i];
+          const cpx<R> p = shfl_xor(own, half);
+          v[i] = mk(p.x + sgn * own.x, p.y + sgn * own.y);
+        }
       }
     }
 #pragma unroll
