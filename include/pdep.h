@@ -174,6 +174,31 @@ int sternheimer_solve(pdep_ctx* ctx, int sys, const double* dv_r, int n_pert, do
 int pdep_solve(pdep_ctx* ctx, int sys, const double* phi0, double* eigvals, double* eigvecs,
                pdep_stats* stats, void* stream);
 
+/* Screening at omega = 0 from PDEP eigenpairs (Sec. II A): with
+ * g_i = lambda_i / (1 - lambda_i), the eigenvalues of the symmetrised
+ * reducible polarizability chibar = (1 - chi0bar)^{-1} chi0bar
+ * (Eq. linearalgebrachichi0), which shares chi0bar's eigenvectors, applies
+ *   PDEP_SCREEN_CHIBAR: out = Phi diag(g) Phi^T f
+ *   PDEP_SCREEN_EPSINV: out = f + Phi diag(g) Phi^T f        (Eq. epsilonandchi)
+ *   PDEP_SCREEN_WP:     out = D Phi diag(g) Phi^T D f,  D = v^{1/2} =
+ *                       sqrt(4 pi)/|G|, the correlation part W^p of the
+ *                       screened interaction (Eq. Wpnondiag with the Coulomb
+ *                       factors 4 pi e^2 written out)
+ * to n vectors f [n][n_pdep_dim] -> out [n][n_pdep_dim]: the rank-n_pdep
+ * (PDEP-basis) form of Eq. eigendecompzerofreq at omega = 0.  eigvals
+ * [n_pdep] and eigvecs [n_pdep][n_pdep_dim] are eigenpairs of chi0bar as
+ * pdep_solve returns them (orthonormal vectors).  Returns
+ * PDEP_ERR_INVALID_ARG for an unknown kind, n_pdep outside [1, n_pdep_dim],
+ * or an eigenvalue that is non-finite or has 1 - lambda <= 1e-12 (chi0bar
+ * is negative semi-definite, so its eigenvalues are <= 0).  The head and
+ * wings (G = 0, Eq. integrationxiq) are not part of the PDEP sphere. */
+#define PDEP_SCREEN_CHIBAR 0
+#define PDEP_SCREEN_EPSINV 1
+#define PDEP_SCREEN_WP 2
+int pdep_screening_apply(pdep_ctx* ctx, int sys, int kind, const double* eigvals,
+                         const double* eigvecs, int n_pdep, const double* f, int n, double* out,
+                         void* stream);
+
 /* y = H x for n sphere vectors x [n][n_pw] -> y [n][n_pw], H = -nabla^2/2 + V
  * (the local-potential Hamiltonian of the setup), evaluated with the pruned
  * sphere <-> grid transforms; precision PDEP_FP64 or PDEP_MIXED (FP32

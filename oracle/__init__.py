@@ -21,6 +21,9 @@ real orbitals:
 * ``pdep``        dense symmetrised chi0bar by the Adler-Wiser sum over states
                   at omega = 0 (Eq. AdlerWiser), its eigendecomposition
                   (Eq. eigendecompzerofreq), and the free-electron closed form.
+* ``screening``   reducible chibar = (1 - chi0bar)^{-1} chi0bar, epsbar^{-1} and
+                  W^p at omega = 0 (Eqs. linearalgebrachichi0, epsilonandchi,
+                  Wpnondiag), dense and in the PDEP basis.
 
 Pins (tests/test_oracle_*.py): free-electron closed form, finite-difference
 density and second-order band-energy response, brute-force matrix elements,
@@ -28,4 +31,4 @@ Sternheimer = sum over states, symmetry, negative semi-definiteness,
 charge neutrality, invariance under V -> V + const.  The paper prints no
 worked numerical example for this path, so no pin uses printed values.
 """
-from . import basis, hamiltonian, response, pdep  # noqa: F401
+from . import basis, hamiltonian, response, pdep, screening  # noqa: F401

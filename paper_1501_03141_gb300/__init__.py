@@ -14,6 +14,9 @@ import numpy as np
 
 from . import _abi
 from ._abi import PDEP_FP64, PDEP_MIXED, PdepError  # noqa: F401
+from ._abi import PDEP_SCREEN_CHIBAR, PDEP_SCREEN_EPSINV, PDEP_SCREEN_WP  # noqa: F401
+
+SCREEN_KINDS = {"chibar": PDEP_SCREEN_CHIBAR, "epsinv": PDEP_SCREEN_EPSINV, "wp": PDEP_SCREEN_WP}
 
 
 def default_options(**kw) -> _abi.pdep_options:
@@ -187,3 +190,16 @@ class Context:
                                         _stream(self.stream)), "pdep_solve", allow)
         stats = {k: getattr(st, k) for k, _ in _abi.pdep_stats._fields_}
         return eigvals, eigvecs, stats
+
+    def screening_apply(self, kind, eigvals, eigvecs, f, sys: int = 0, out=None):
+        """chibar, epsbar^{-1} or W^p at omega = 0 in the PDEP basis applied to f
+        [n, n_pdep_dim]; kind is "chibar", "epsinv" or "wp" (or its integer code)."""
+        k = SCREEN_KINDS[kind] if isinstance(kind, str) else int(kind)
+        n_pdep = int(eigvals.shape[0])
+        if out is None:
+            out = np.empty_like(f) if isinstance(f, np.ndarray) else f.new_empty(f.shape)
+        _abi.check(self._lib.pdep_screening_apply(self._h, sys, k, _abi.ptr(eigvals),
+                                                  _abi.ptr(eigvecs), n_pdep, _abi.ptr(f),
+                                                  int(f.shape[0]), _abi.ptr(out),
+                                                  _stream(self.stream)), "pdep_screening_apply")
+        return out

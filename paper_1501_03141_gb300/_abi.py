@@ -27,12 +27,16 @@ PDEP_ERR_UNSUPPORTED = 8
 PDEP_FP64 = 0
 PDEP_MIXED = 1
 
+PDEP_SCREEN_CHIBAR = 0
+PDEP_SCREEN_EPSINV = 1
+PDEP_SCREEN_WP = 2
+
 #: every symbol declared in include/pdep.h
 EXPORTS = (
     "pdep_default_options", "pdep_setup", "pdep_get_sizes", "pdep_get_occupied",
     "chi0_apply", "sternheimer_solve", "pdep_solve", "pdep_apply_hamiltonian", "pdep_to_grid",
     "pdep_profile", "pdep_destroy", "pdep_status_string", "pdep_last_error",
-    "pdep_apply_hamiltonian_noalloc",
+    "pdep_apply_hamiltonian_noalloc", "pdep_screening_apply",
 )
 
 PDEP_PROFILE_CLASSES = 10
@@ -126,6 +130,7 @@ def load(path: str = LIB_PATH):
     lib.pdep_solve.argtypes = [vp, ip, vp, vp, vp, ctypes.POINTER(pdep_stats), vp]
     lib.pdep_apply_hamiltonian.argtypes = [vp, ip, vp, ip, vp, ip, vp]
     lib.pdep_to_grid.argtypes = [vp, ip, vp, ip, vp, vp]
+    lib.pdep_screening_apply.argtypes = [vp, ip, ip, vp, vp, ip, vp, ip, vp, vp]
     lib.pdep_apply_hamiltonian_noalloc.argtypes = [vp, ip, vp, ip, vp, vp]
     lib.pdep_apply_hamiltonian_noalloc.restype = ip
     lib.pdep_profile.argtypes = [ip, ctypes.POINTER(pdep_profile_t)]
@@ -137,7 +142,8 @@ def load(path: str = LIB_PATH):
     lib.pdep_last_error.argtypes = []
     lib.pdep_last_error.restype = ctypes.c_char_p
     for name in ("pdep_setup", "pdep_get_sizes", "pdep_get_occupied", "chi0_apply",
-                 "sternheimer_solve", "pdep_solve", "pdep_apply_hamiltonian", "pdep_to_grid"):
+                 "sternheimer_solve", "pdep_solve", "pdep_apply_hamiltonian", "pdep_to_grid",
+                 "pdep_screening_apply"):
         getattr(lib, name).restype = ip
     del dp
     _lib = lib

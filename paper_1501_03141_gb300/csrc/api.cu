@@ -480,6 +480,25 @@ int orthonormalize(pdep_ctx* c, SysData& s, const double* B, int nb, double* T, 
       CK(gemm<double>(false, rows, cur, nb, -1.0, B, s.ld, S, nb, 1.0, src, s.ld, st));
     }
     CK(gemm<double>(true, cur, cur, rows, 1.0, src, s.ld, src, s.ld, 0.0, G, cur, st));
+    if (cur <= 128) {
+      // Cholesky QR: OUT = src L^{-T}; ill-conditioned blocks fall through to
+      // the symmetric orthonormalisation below, which drops dependent columns
+      int* fail;
+      RET(ws(c, "on_f", 1, &fail));
+      CK(cholesky_winv(G, cur, 1e-10, Q, fail, st));
+      int hf = 1;
+      CK(cudaMemcpyAsync(&hf, fail, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (hf == 0) {
+        CK(gemm<double>(false, rows, cur, cur, 1.0, src, s.ld, Q, cur, 0.0, OUT, s.ld, st));
+        if (pass == 0) {
+          CK(cudaMemcpy2DAsync(T, s.ld * sizeof(double), OUT, s.ld * sizeof(double),
+                               rows * sizeof(double), cur, cudaMemcpyDeviceToDevice, st));
+          src = T;
+        }
+        continue;
+      }
+    }
     CK(eigh(cur, G, cur, d, Q, cur, wk, st));
     std::vector<double> hd(cur);
     CK(cudaMemcpyAsync(hd.data(), d, sizeof(double) * cur, cudaMemcpyDeviceToHost, st));
@@ -1366,6 +1385,61 @@ int chi0_apply(pdep_ctx* c, int sys, const double* phi, int n_pert, double* chi0
                        st));
   RET(sync(st));
   return r;
+}
+
+// Screening operators at omega = 0 in the PDEP basis (Eqs. linearalgebrachichi0,
+// epsilonandchi, Wpnondiag): Phi diag(lambda/(1-lambda)) Phi^T, plus the identity
+// (epsbar^{-1}) or between v^{1/2} factors (W^p).
+int pdep_screening_apply(pdep_ctx* c, int sys, int kind, const double* eigvals,
+                         const double* eigvecs, int n_pdep, const double* f, int n, double* out,
+                         void* stream) {
+  RET(check_sys(c, sys));
+  SysData& s = c->sys[sys];
+  const int dim = s.n_pw - 1;
+  if (kind < PDEP_SCREEN_CHIBAR || kind > PDEP_SCREEN_WP || n_pdep < 1 || n_pdep > dim ||
+      n < 0 || !eigvals || !eigvecs || (n > 0 && (!f || !out)))
+    return fail(PDEP_ERR_INVALID_ARG, "bad pdep_screening_apply arguments");
+  if (n == 0) return PDEP_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<double> lam(n_pdep), g(n_pdep);
+  if (is_device_ptr(eigvals)) {
+    CK(cudaMemcpyAsync(lam.data(), eigvals, sizeof(double) * n_pdep, cudaMemcpyDeviceToHost, st));
+    RET(sync(st));
+  } else {
+    memcpy(lam.data(), eigvals, sizeof(double) * n_pdep);
+  }
+  for (int i = 0; i < n_pdep; ++i) {
+    // chi0bar is negative semi-definite; 1 - lambda must stay away from 0
+    if (!std::isfinite(lam[i]) || !(1.0 - lam[i] > 1e-12))
+      return fail(PDEP_ERR_INVALID_ARG, "eigenvalue with lambda >= 1 or non-finite");
+    g[i] = lam[i] / (1.0 - lam[i]);
+  }
+  double *phi, *fx, *S, *dg, *o;
+  RET(ws(c, "sc_phi", (size_t)n_pdep * s.ld, &phi));
+  RET(ws(c, "sc_f", (size_t)n * s.ld, &fx));
+  RET(ws(c, "sc_o", (size_t)n * s.ld, &o));
+  RET(ws(c, "sc_s", (size_t)n_pdep * n, &S));
+  RET(ws(c, "sc_g", (size_t)n_pdep, &dg));
+  CK(cudaMemcpyAsync(dg, g.data(), sizeof(double) * n_pdep, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpy2DAsync(phi, s.ld * sizeof(double), eigvecs, dim * sizeof(double),
+                       dim * sizeof(double), n_pdep, kind_to_dev(eigvecs), st));
+  CK(cudaMemcpy2DAsync(fx, s.ld * sizeof(double), f, dim * sizeof(double), dim * sizeof(double), n,
+                       kind_to_dev(f), st));
+  if (kind == PDEP_SCREEN_WP) CK(scale_sqrt_coulomb(fx, s.ld, s.n_half, n, s.sd.g2, st));
+  // S = Phi^T f, scaled per row by lambda/(1-lambda); out = Phi S (+ f)
+  CK(gemm<double>(true, n_pdep, n, dim, 1.0, phi, s.ld, fx, s.ld, 0.0, S, n_pdep, st));
+  CK(scale_rows<double>(S, n_pdep, n_pdep, n, dg, st));
+  double beta = 0.0;
+  if (kind == PDEP_SCREEN_EPSINV) {
+    CK(cudaMemcpyAsync(o, fx, sizeof(double) * (size_t)n * s.ld, cudaMemcpyDeviceToDevice, st));
+    beta = 1.0;
+  }
+  CK(gemm<double>(false, dim, n, n_pdep, 1.0, phi, s.ld, S, n_pdep, beta, o, s.ld, st));
+  if (kind == PDEP_SCREEN_WP) CK(scale_sqrt_coulomb(o, s.ld, s.n_half, n, s.sd.g2, st));
+  CK(cudaMemcpy2DAsync(out, dim * sizeof(double), o, s.ld * sizeof(double), dim * sizeof(double),
+                       n, kind_from_dev(out), st));
+  RET(sync(st));
+  return PDEP_OK;
 }
 
 int sternheimer_solve(pdep_ctx* c, int sys, const double* dv_r, int n_pert, double* dpsi,

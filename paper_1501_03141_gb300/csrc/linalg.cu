@@ -253,6 +253,11 @@ __global__ void k_jacobi_init(const double* __restrict__ M, long long ldm, int n
   }
 }
 
+// One round of the cyclic (round-robin) ordering: warp w rotates the column
+// pair (p, q) of A so that A_p . A_q = 0 and applies the same rotation to V.
+// E > 0: the four columns (n <= 32 E) are loaded into registers up front, so a
+// round costs one memory round trip instead of one per 32 rows; E = 0 streams.
+template <int E>
 __global__ void k_jacobi_round(double* A, double* V, int n, int nn, int round,
                                unsigned* counter) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -269,34 +274,79 @@ __global__ void k_jacobi_round(double* A, double* V, int n, int nn, int round,
   if (p >= n || q >= n) return;
   double* ap = A + (long long)p * n;
   double* aq = A + (long long)q * n;
-  double al = 0.0, be = 0.0, ga = 0.0;
-  for (int r = lane; r < n; r += 32) {
-    const double x = ap[r], y = aq[r];
-    al += x * x;
-    be += y * y;
-    ga += x * y;
-  }
-  al = warp_sum(al);
-  be = warp_sum(be);
-  ga = warp_sum(ga);
-  if (ga == 0.0 || fabs(ga) <= 1e-14 * sqrt(al * be)) return;
-  const double zeta = (be - al) / (2.0 * ga);
-  const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-  const double c = 1.0 / sqrt(1.0 + tt * tt);
-  const double s = c * tt;
-  for (int r = lane; r < n; r += 32) {
-    const double x = ap[r], y = aq[r];
-    ap[r] = c * x - s * y;
-    aq[r] = s * x + c * y;
-  }
   double* vp = V + (long long)p * n;
   double* vq = V + (long long)q * n;
-  for (int r = lane; r < n; r += 32) {
-    const double x = vp[r], y = vq[r];
-    vp[r] = c * x - s * y;
-    vq[r] = s * x + c * y;
+  double al = 0.0, be = 0.0, ga = 0.0;
+  if constexpr (E > 0) {
+    double x[E], y[E], u[E], w[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int r = lane + 32 * e;
+      const bool in = r < n;
+      x[e] = in ? ap[r] : 0.0;
+      y[e] = in ? aq[r] : 0.0;
+      u[e] = in ? vp[r] : 0.0;
+      w[e] = in ? vq[r] : 0.0;
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      al += x[e] * x[e];
+      be += y[e] * y[e];
+      ga += x[e] * y[e];
+    }
+    al = warp_sum(al);
+    be = warp_sum(be);
+    ga = warp_sum(ga);
+    if (ga == 0.0 || fabs(ga) <= 1e-14 * sqrt(al * be)) return;
+    const double zeta = (be - al) / (2.0 * ga);
+    const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+    const double c = 1.0 / sqrt(1.0 + tt * tt);
+    const double s = c * tt;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int r = lane + 32 * e;
+      if (r < n) {
+        ap[r] = c * x[e] - s * y[e];
+        aq[r] = s * x[e] + c * y[e];
+        vp[r] = c * u[e] - s * w[e];
+        vq[r] = s * u[e] + c * w[e];
+      }
+    }
+  } else {
+    for (int r = lane; r < n; r += 32) {
+      const double x = ap[r], y = aq[r];
+      al += x * x;
+      be += y * y;
+      ga += x * y;
+    }
+    al = warp_sum(al);
+    be = warp_sum(be);
+    ga = warp_sum(ga);
+    if (ga == 0.0 || fabs(ga) <= 1e-14 * sqrt(al * be)) return;
+    const double zeta = (be - al) / (2.0 * ga);
+    const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+    const double c = 1.0 / sqrt(1.0 + tt * tt);
+    const double s = c * tt;
+    for (int r = lane; r < n; r += 32) {
+      const double x = ap[r], y = aq[r];
+      ap[r] = c * x - s * y;
+      aq[r] = s * x + c * y;
+    }
+    for (int r = lane; r < n; r += 32) {
+      const double x = vp[r], y = vq[r];
+      vp[r] = c * x - s * y;
+      vq[r] = s * x + c * y;
+    }
   }
   if (lane == 0) atomicAdd(counter, 1u);
+}
+
+using JacobiRound = void (*)(double*, double*, int, int, int, unsigned*);
+static JacobiRound jacobi_round_for(int n) {
+  if (n <= 128) return k_jacobi_round<4>;
+  if (n <= 256) return k_jacobi_round<8>;
+  if (n <= 512) return k_jacobi_round<16>;
+  return k_jacobi_round<0>;
 }
 
 // w_i = v_i . (M v_i)
@@ -347,6 +397,7 @@ cudaError_t eigh(int n, const double* M, long long ldm, double* W, double* V, lo
   const int warps = nn / 2;
   const int tpb = 128;
   const int jb = (warps * 32 + tpb - 1) / tpb;
+  const JacobiRound round_k = jacobi_round_for(n);
   // One sweep = nn - 1 dependent rounds; they are replayed from a CUDA graph
   // captured once per (size, buffers) to avoid nn - 1 stream launches.
   cudaGraphExec_t sweep = nullptr;
@@ -366,8 +417,7 @@ cudaError_t eigh(int n, const double* M, long long ldm, double* W, double* V, lo
       cudaGraph_t g;
       e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
       if (e != cudaSuccess) return e;
-      for (int r = 0; r < nn - 1; ++r)
-        k_jacobi_round<<<jb, tpb, 0, cap>>>(wk.a, wk.v, n, nn, r, counter);
+      for (int r = 0; r < nn - 1; ++r) round_k<<<jb, tpb, 0, cap>>>(wk.a, wk.v, n, nn, r, counter);
       e = cudaStreamEndCapture(cap, &g);
       if (e != cudaSuccess) return e;
       e = cudaGraphInstantiate(&sweep, g, 0);
@@ -388,7 +438,7 @@ cudaError_t eigh(int n, const double* M, long long ldm, double* W, double* V, lo
     } else {
       for (int r = 0; r < nn - 1; ++r) {
         count_launch();
-        k_jacobi_round<<<jb, tpb, 0, st>>>(wk.a, wk.v, n, nn, r, counter);
+        round_k<<<jb, tpb, 0, st>>>(wk.a, wk.v, n, nn, r, counter);
       }
     }
     if (nn - 1 == 0) break;
@@ -578,6 +628,111 @@ cudaError_t scale_by_isqrt_clamped(double* Q, long long ldq, int n, const double
                                    int* keep, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   { count_launch(); k_isqrt_clamped<<<n, 128, 0, st>>>(Q, ldq, n, d, dmin, keep); }
+  return cudaGetLastError();
+}
+
+// Cholesky factor G = L L^T of an m x m Gram matrix (column-major, m <= 128)
+// in shared memory, then W = L^{-T} (upper triangular, column-major m x m):
+// the columns of S W are orthonormal when G = S^T S.  A pivot at or below
+// rel_thr * max_i G_ii leaves W unset and sets *fail = 1.
+constexpr int kCholMax = 128;
+__global__ void __launch_bounds__(512) k_chol_winv(const double* __restrict__ G, int m,
+                                                   double rel_thr, double* W, int* fail) {
+  extern __shared__ __align__(16) double sh[];
+  const int ld = m + 1;  // odd row stride: column-wise walks hit distinct banks
+  double* L = sh;        // row-major, lower triangle = L; upper = rows of L^{-1}^T
+  double* dinv = sh + (size_t)m * ld;
+  __shared__ int s_fail;
+  __shared__ double s_gmax;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < m * m; e += nt) {
+    const int i = e % m, j = e / m;
+    L[i * ld + j] = G[e];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double g = 0.0;
+    for (int i = 0; i < m; ++i) g = fmax(g, L[i * ld + i]);
+    s_gmax = g;
+    s_fail = !(g > 0.0) || !isfinite(g);
+  }
+  __syncthreads();
+  const double thr = rel_thr * s_gmax;
+  for (int k = 0; k < m && !s_fail; ++k) {
+    if (tid == 0) {
+      const double d = L[k * ld + k];
+      if (d > thr && isfinite(d)) {
+        L[k * ld + k] = sqrt(d);
+      } else {
+        s_fail = 1;
+      }
+    }
+    __syncthreads();
+    if (s_fail) break;
+    const double piv = L[k * ld + k];
+    for (int i = k + 1 + tid; i < m; i += nt) L[i * ld + k] /= piv;
+    __syncthreads();
+    const int w = m - k - 1;
+    for (int e = tid; e < w * w; e += nt) {
+      const int i = k + 1 + e / w, j = k + 1 + e % w;
+      if (j <= i) L[i * ld + j] -= L[i * ld + k] * L[j * ld + k];
+    }
+    __syncthreads();
+  }
+  if (s_fail) {
+    if (tid == 0) *fail = 1;
+    return;
+  }
+  // X = L^{-1} by forward substitution, one column j per thread; X[i][j]
+  // (i > j) is kept at L[j * ld + i], the unused upper triangle.
+  if (tid < m) {
+    const int j = tid;
+    dinv[j] = 1.0 / L[j * ld + j];
+    for (int i = j + 1; i < m; ++i) {
+      double acc = L[i * ld + j] * dinv[j];
+      for (int k = j + 1; k < i; ++k) acc += L[i * ld + k] * L[j * ld + k];
+      L[j * ld + i] = -acc / L[i * ld + i];
+    }
+  }
+  __syncthreads();
+  // W = X^T: W[r][c] = X[c][r], nonzero for r <= c
+  for (int e = tid; e < m * m; e += nt) {
+    const int r = e % m, c = e / m;
+    W[e] = r < c ? L[r * ld + c] : (r == c ? dinv[r] : 0.0);
+  }
+  if (tid == 0) *fail = 0;
+}
+
+cudaError_t cholesky_winv(const double* G, int m, double rel_thr, double* W, int* fail,
+                          cudaStream_t st) {
+  if (m <= 0 || m > kCholMax) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(double) * ((size_t)m * (m + 1) + m);
+  cudaError_t e = cudaFuncSetAttribute(k_chol_winv, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(double) * (kCholMax * (kCholMax + 1) + kCholMax)));
+  if (e != cudaSuccess) return e;
+  count_launch();
+  k_chol_winv<<<1, 512, smem, st>>>(G, m, rel_thr, W, fail);
+  return cudaGetLastError();
+}
+
+// X[d][j] *= sqrt(4 pi / |G_{d/2}|^2) for the 2 n_half PDEP components d
+// (v^{1/2} of Eq. symmoperator on the real-coefficient layout)
+__global__ void k_sqrt_coulomb(double* X, long long ld, int n_half, int n,
+                               const double* __restrict__ g2) {
+  const int j = blockIdx.y;
+  const int dim = 2 * n_half;
+  for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < dim; d += gridDim.x * blockDim.x)
+    X[d + (long long)j * ld] *= sqrt(4.0 * 3.14159265358979323846 / g2[d >> 1]);
+}
+cudaError_t scale_sqrt_coulomb(double* X, long long ld, int n_half, int n, const double* g2,
+                               cudaStream_t st) {
+  if (n <= 0 || n_half <= 0) return cudaSuccess;
+  const int bx = std::min((2 * n_half + 255) / 256, 64);
+  for (int j0 = 0; j0 < n; j0 += 65535) {
+    const int nj = std::min(65535, n - j0);
+    count_launch();
+    k_sqrt_coulomb<<<dim3(bx, nj), 256, 0, st>>>(X + (long long)j0 * ld, ld, n_half, nj, g2);
+  }
   return cudaGetLastError();
 }
 

@@ -46,6 +46,13 @@ cudaError_t ritz_residual(const double* AX, const double* X, long long ld, int r
                           const double* theta, double* Rout, cudaStream_t st);
 cudaError_t philox_normal(double* X, long long ld, int rows, int cols, unsigned long long seed,
                           unsigned long long offset, cudaStream_t st);
+// X[d][j] *= sqrt(4 pi)/|G| on the 2 n_half PDEP components of n columns
+cudaError_t scale_sqrt_coulomb(double* X, long long ld, int n_half, int n, const double* g2,
+                               cudaStream_t st);
+// W = L^{-T} for the Cholesky factor of the m x m Gram matrix G (m <= 128);
+// *fail = 1 (device) when a pivot is at or below rel_thr * max_i G_ii.
+cudaError_t cholesky_winv(const double* G, int m, double rel_thr, double* W, int* fail,
+                          cudaStream_t st);
 cudaError_t scale_by_isqrt_clamped(double* Q, long long ldq, int n, const double* d, double dmin,
                                    int* keep, cudaStream_t st);
 cudaError_t fill_zero(void* p, size_t bytes, cudaStream_t st);

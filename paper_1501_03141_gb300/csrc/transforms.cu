@@ -240,7 +240,11 @@ __device__ __forceinline__ void y_inverse(const SphereDev<R>& s, const cpx<R>* S
   const int nslot = 2 * s.R3 + 1;
   const int per = blockDim.x / TL;
   const int t = threadIdx.x & (TL - 1);
+  // first slot of this warp in a round: warps whose slots all lie past the
+  // last (n3) row skip the line FFTs instead of transforming zeros
+  const int wslot0 = (threadIdx.x & ~31) / TL;
   for (int base = 0; base < nslot; base += per) {
+    if (base + wslot0 >= nslot) break;
     const int sl = base + threadIdx.x / TL;
     const bool act = sl < nslot;
     const int2 info = act ? s.slot[sl] : make_int2(-1, 0);
@@ -266,7 +270,9 @@ __device__ __forceinline__ void y_forward(const SphereDev<R>& s, const cpx<R>* T
   const int nslot = 2 * s.R3 + 1;
   const int per = blockDim.x / TL;
   const int t = threadIdx.x & (TL - 1);
+  const int wslot0 = (threadIdx.x & ~31) / TL;
   for (int base = 0; base < nslot; base += per) {
+    if (base + wslot0 >= nslot) break;
     const int sl = base + threadIdx.x / TL;
     const bool act = sl < nslot;
     const int2 info = act ? s.slot[sl] : make_int2(-1, 0);

@@ -80,3 +80,24 @@ def test_cube48_mixed_vs_fp64_and_rayleigh():
     cv = response.chi0bar_apply(b, ks, V[pick])
     rq = np.sum(cv * V[pick], axis=1)
     np.testing.assert_allclose(rq, ev64[pick], rtol=1e-8)
+
+
+def test_ritz_interlacing_and_monotone(tiny_ref):
+    """After k Davidson iterations (no restart yet) the Ritz values interlace:
+    theta_i >= lambda_i (Cauchy), and growing the subspace lowers each one."""
+    need_gpu()
+    lib_ready()
+    import paper_1501_03141_gb300 as pg
+    s, b, ks = oracle_for("tiny")
+    lam, _ = tiny_ref
+    thetas = []
+    for k in (1, 2, 3):
+        with pg.Context(s, dav_tol=0.0, dav_max_iter=k) as ctx:
+            ev, _, st = ctx.pdep_solve(allow_unconverged=True)
+        assert st["dav_iterations"] == k
+        thetas.append(ev)
+    tol = 1e-10 * abs(lam[0])
+    for th in thetas:
+        assert np.all(th >= lam - tol), th - lam
+    assert np.all(thetas[1] <= thetas[0] + tol)
+    assert np.all(thetas[2] <= thetas[1] + tol)
