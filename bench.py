@@ -176,6 +176,37 @@ def traffic_for(cls_name, algorithmic_bytes_per_launch):
     return float(v["dram_over_algorithmic"]) * algorithmic_bytes_per_launch
 
 
+# dense TF32 / dense BF16 tensor rates (nominal 1.1 / 2.25 PFLOP/s): the TF32
+# peak is the measured sustained BF16 GEMM rate times this ratio
+TF32_OVER_BF16 = 1.1 / 2.25
+
+
+def tf32_peak():
+    try:
+        p = json.load(open(PEAKS_FILE))
+        return float(p["bf16_tflops_sustained"]) * TF32_OVER_BF16, "measured"
+    except (OSError, KeyError, ValueError):
+        return 1700.0 * TF32_OVER_BF16, "fallback"
+
+
+def tensor_gemm(prof):
+    """Tensor-pipe figures of the 3xTF32 projection GEMMs (algorithmic 2 M N K
+    flops; the tensor pipe executes three TF32 MMAs per product)."""
+    c = prof["classes"].get("gemm_tf32x3")
+    if not c or not c["launches"] or c["ms"] <= 0:
+        return None
+    peak, src = tf32_peak()
+    tfl = c["flops"] / (c["ms"] / 1e3) / 1e12
+    hbm, hsrc = measured_peaks()
+    gbs = c["bytes"] / (c["ms"] / 1e3) / 1e9
+    return {"bound": "tensor", "achieved": round(tfl, 2), "executed_tf32": round(3 * tfl, 2),
+            "peak": round(peak, 1), "unit": "TFLOP/s", "frac": round(tfl / peak, 4),
+            "executed_frac": round(3 * tfl / peak, 4),
+            "peak_source": f"{src} sustained bf16 x {TF32_OVER_BF16:.3f} (nominal tf32/bf16)",
+            "gbs": round(gbs, 1), "hbm_frac_of_" + hsrc: round(gbs / hbm, 4),
+            "launches": c["launches"], "ms": round(c["ms"], 2)}
+
+
 def roofline(prof):
     hbm, src = measured_peaks()
     best = None
@@ -187,6 +218,10 @@ def roofline(prof):
     if best is None:
         return None
     name, c = best
+    if name == "gemm_tf32x3":
+        r = tensor_gemm(prof)
+        r.update({"kernel": name, "traffic": traffic_for(name, c["bytes"] / c["launches"])})
+        return r
     per = c["ms"] / c["launches"] / 1e3                     # seconds per launch
     gbs = c["bytes"] / c["launches"] / per / 1e9
     tfl = c["flops"] / c["launches"] / per / 1e12
@@ -341,12 +376,15 @@ def run_ours(args):
                        "refine_rounds_max": stats["refine_rounds_max"],
                        "max_cg_residual": stats["max_cg_residual"],
                        "cg_step_variant_autotuned": stats["cg_variant"],
+                       "projection_kernel_autotuned": {0: "cuda-core fp32", 1: "tensor-core 3xtf32"}
+                       .get(stats["proj_variant"], "untuned"),
                        "n_deflate": int(ctx_deflate)},
             "eigenpairs_per_s": round(eigpairs, 4),
             "fp64": fp64,
             "e2e": e2e,
             "gpu_launches": int(prof["launches"]),
             "roofline": roofline(prof),
+            "tensor_gemm": tensor_gemm(prof),
             "kernel_profile": {k: {"launches": v["launches"], "ms": round(v["ms"], 2),
                                    "tflops": round(v["flops"] / v["ms"] / 1e9, 3) if v["ms"] else None,
                                    "gbs": round(v["bytes"] / v["ms"] / 1e6, 1) if v["ms"] else None}

@@ -116,6 +116,10 @@ typedef struct {
                                 share of each solution is added exactly and the CG
                                 works on the rest, whose smallest eigenvalue is
                                 eps_{n_occ+n_deflate+1} - eps_v instead of the gap. */
+  int proj_variant;          /* kernel of the FP32 (mixed-mode CG) projection term
+                                sum_w sigma_w |w><w| x: -1 = autotuned (default; the
+                                first large calls time both), 0 = FP32 CUDA-core GEMMs,
+                                1 = tensor-core 3xTF32 GEMMs (FP32 accuracy). */
 } pdep_options;
 
 typedef struct {
@@ -129,6 +133,7 @@ typedef struct {
   double max_dav_residual;      /* largest final ||chi0bar x - theta x|| / |theta_1| */
   double seconds;               /* wall time of the call */
   int cg_variant;               /* CG-step launch shape the autotuner chose (-1: untuned) */
+  int proj_variant;             /* FP32 projection kernel in use (-1: untuned, 0, 1) */
 } pdep_stats;
 
 /* Fill *opt with the defaults (FP64, cg_tol 1e-10, dav_tol 1e-8, ...). */
@@ -242,7 +247,7 @@ int pdep_to_grid(pdep_ctx* ctx, int sys, const double* x, int n, double* u, void
  * waits for the recorded events and fills *out (may be NULL).  flops and
  * bytes are the algorithmic counts of the launches (complex line FFT:
  * 5 L log2 L flops; bytes: every input read and output written once). */
-#define PDEP_PROFILE_CLASSES 10
+#define PDEP_PROFILE_CLASSES 11
 typedef struct {
   char name[24];
   long long launches;

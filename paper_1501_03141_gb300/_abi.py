@@ -39,7 +39,7 @@ EXPORTS = (
     "pdep_apply_hamiltonian_noalloc", "pdep_screening_apply",
 )
 
-PDEP_PROFILE_CLASSES = 10
+PDEP_PROFILE_CLASSES = 11
 
 
 class pdep_system_desc(ctypes.Structure):
@@ -70,6 +70,7 @@ class pdep_options(ctypes.Structure):
         ("setup_max_iter", ctypes.c_int),
         ("workspace_limit_bytes", ctypes.c_size_t),
         ("n_deflate", ctypes.c_int),
+        ("proj_variant", ctypes.c_int),
     ]
 
 
@@ -85,6 +86,7 @@ class pdep_stats(ctypes.Structure):
         ("max_dav_residual", ctypes.c_double),
         ("seconds", ctypes.c_double),
         ("cg_variant", ctypes.c_int),
+        ("proj_variant", ctypes.c_int),
     ]
 
 

@@ -111,6 +111,11 @@ struct pdep_ctx {
   double st_max_res = 0;
   // autotuned launch shape of the CG step, per precision (-1: not tuned yet)
   int cg_variant[2] = {-1, -1};
+  // autotuned FP32 projection kernel (0 CUDA-core, 1 tensor-core; -1 untuned)
+  int proj_variant = -1;
+  int proj_tune_next = 0;
+  double proj_tune_ms[2] = {0, 0};
+  int proj_tune_calls = 0;
   double cg_tune_ms[2][CG_NUM_VARIANTS] = {};
   int cg_tune_next[2] = {0, 0};
 };
@@ -375,9 +380,12 @@ size_t b1_count(const SysData& s, int n_items) {
 // uses occupied state i % n_occ; without with_shift Y = H X.  Then, if
 // with_pv, the occupied and deflated states are shifted:
 // Y += Psi_ext diag(sigma) (Psi_ext^T X) on the same columns.
+// dn (FP64 only, may be null): the transform also accumulates the density
+// response dn_j(r) += (4/Omega) u_v(r) x_i(r) of every vector i = j n_occ + v
+// it transforms (Eq. deltani); dn must hold the (i / n_occ) perturbations.
 template <typename R>
 int apply_h(pdep_ctx* c, SysData& s, const R* X, R* Y, int n, const int* d_list, int n_list,
-            bool with_shift, bool with_pv, cudaStream_t st) {
+            bool with_shift, bool with_pv, cudaStream_t st, double* dn = nullptr) {
   ItemMap map{n, (n + 1) / 2};
   int n_items = (n + 1) / 2;
   if (d_list) {
@@ -396,6 +404,13 @@ int apply_h(pdep_ctx* c, SysData& s, const R* X, R* Y, int n, const int* d_list,
     a.n_items = n_items;
     a.v = vgrid(s, (R*)nullptr);
     a.map = map;
+    if (dn) {
+      a.dn = dn;
+      a.u = s.d_u;
+      a.dn_nocc = s.n_occ;
+      a.dn_stride = s.n_r;
+      a.dn_scale = 4.0 / s.omega;
+    }
     CK(launch_slab<R>(sd, a, st));
     Epilogue<R> ep{};
     ep.y = Y;
@@ -413,6 +428,43 @@ int apply_h(pdep_ctx* c, SysData& s, const R* X, R* Y, int n, const int* d_list,
   if (with_pv) {
     // only the listed columns when a list is given
     const int m = d_list ? n_list : n;
+    if constexpr (sizeof(R) == 4) {
+      // FP32: CUDA-core GEMMs (variant 0) or tensor-core 3xTF32 (variant 1).
+      // While untuned, calls with many columns alternate the two and keep
+      // their time per column; afterwards the faster one is used.
+      int pv = c->opt.proj_variant >= 0 ? c->opt.proj_variant : c->proj_variant;
+      const bool tuning = pv < 0 && m >= 256;
+      if (pv < 0) pv = tuning ? c->proj_tune_next : 1;
+      if (tuning) CK(cudaEventRecord(c->ev[0], st));
+      if (pv == 1) {
+        const long long lds = (s.n_ext + 3) & ~3;
+        float* S;
+        RET(ws(c, "pv_32", (size_t)lds * std::max(m, 1), &S));
+        CK(tc_proj_coeffs(s.n_ext, m, s.n_pw, s.d_psif, s.ld, X, s.ld, d_list, s.d_sigma32, S, lds,
+                          st));
+        CK(tc_proj_update(s.n_pw, m, s.n_ext, s.d_psif, s.ld, S, lds, Y, s.ld, d_list, st));
+      } else {
+        float* S;
+        RET(ws(c, "pv_32", (size_t)s.n_ext * std::max(m, 1), &S));
+        CK(gemm<float>(true, s.n_ext, m, s.n_pw, 1.0, s.d_psif, s.ld, X, s.ld, 0.0, S, s.n_ext,
+                       st, d_list, nullptr));
+        CK(scale_rows<float>(S, s.n_ext, s.n_ext, m, s.d_sigma32, st));
+        CK(gemm<float>(false, s.n_pw, m, s.n_ext, 1.0, s.d_psif, s.ld, S, s.n_ext, 1.0, Y, s.ld,
+                       st, nullptr, d_list));
+      }
+      if (tuning) {
+        CK(cudaEventRecord(c->ev[1], st));
+        CK(cudaEventSynchronize(c->ev[1]));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+        c->proj_tune_ms[pv] += ms / m;
+        // two timed calls per variant, alternating
+        if (++c->proj_tune_next == 2) c->proj_tune_next = 0;
+        if (++c->proj_tune_calls == 4)
+          c->proj_variant = c->proj_tune_ms[1] <= c->proj_tune_ms[0] ? 1 : 0;
+      }
+      return PDEP_OK;
+    }
     R* S;
     // shift of the occupied and the deflated empty states: state w moves to
     // eps_{n_ext} - eps_v, the bottom of the spectrum the CG still sees
@@ -919,15 +971,20 @@ int collect_cg_stats(pdep_ctx* c, const CgScal* sc, int n, int* iters_out, cudaS
 
 // Solve for n right-hand sides b (FP64, [n][ld]); x out (FP64).  h_iters and
 // h_res (host, may be null) get per-RHS iteration counts and FP64 residuals.
-int solve_rhs(pdep_ctx* c, SysData& s, const double* b, double* x, int n, int* h_iters,
-              double* h_res, cudaStream_t st) {
+int solve_rhs(pdep_ctx* c, SysData& s, const double* b, const double* xd, double* x, int n,
+              double* dn, int* h_iters, double* h_res, cudaStream_t st) {
   const double tol = c->opt.cg_tol;
-  double *rel, *ap64;
+  double *rel, *r64, *ad;
   RET(ws(c, "sv_rel", (size_t)n, &rel));
-  RET(ws(c, "sv_ap64", (size_t)n * s.ld, &ap64));
+  RET(ws(c, "sv_r64", (size_t)n * s.ld, &r64));
+  RET(ws(c, "sv_ap64", (size_t)n * s.ld, &ad));
   std::vector<int> its_total(n, 0);
   bool capped = false;
   int rounds = 0;
+  // r64 = b: the FP64 residual, updated as r -= A delta for every update
+  // delta of x (and checked against b's norm)
+  CK(cudaMemcpyAsync(r64, b, sizeof(double) * (size_t)n * s.ld, cudaMemcpyDeviceToDevice, st));
+  if (dn) CK(cudaMemsetAsync(dn, 0, sizeof(double) * (size_t)(n / s.n_occ) * s.n_r, st));
   if (c->opt.precision == PDEP_FP64) {
     CgScal* sc;
     RET(ws(c, "cg_sc64", (size_t)n, &sc));
@@ -938,10 +995,22 @@ int solve_rhs(pdep_ctx* c, SysData& s, const double* b, double* x, int n, int* h
     RET(collect_cg_stats(c, sc, n, nullptr, st, &its));
     for (int i = 0; i < n; ++i) its_total[i] = its[i];
     rounds = 1;
+    // x += xd (the deflated states' exact share); then the FP64 residual
+    // b - A x of the CG part, with the density response of the whole x
+    // accumulated by the same transform
+    const double* hx = x;
+    if (xd) {
+      double* dl;
+      RET(ws(c, "sv_dl", (size_t)n * s.ld, &dl));
+      CK(refine_delta(x, dl, s.ld, nullptr, 0, s.n_pw, n, nullptr, xd, st));
+      hx = dl;
+    }
+    RET(apply_h<double>(c, s, hx, ad, n, nullptr, 0, true, true, st, dn));
+    CK(residual_update(r64, ad, b, s.ld, s.n_pw, n, rel, nullptr, xd, s.d_sigma64, s.n_occ, st));
   } else {
     // mixed: FP32 inner CG on the scaled residual, FP64 residual refinement
     float *r32, *d32;
-    double* rn;
+    double *rn, *dl;
     CgScal* sc;
     int* list;
     RET(ws(c, "mx_r32", (size_t)n * s.ld, &r32));
@@ -949,9 +1018,8 @@ int solve_rhs(pdep_ctx* c, SysData& s, const double* b, double* x, int n, int* h
     RET(ws(c, "mx_rn", (size_t)n, &rn));
     RET(ws(c, "cg_sc32", (size_t)n, &sc));
     RET(ws(c, "mx_list", (size_t)n, &list));
+    RET(ws(c, "sv_dl", (size_t)n * s.ld, &dl));
     CK(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)n * s.ld, st));
-    // r64 = b initially (x = 0): ap64 holds the residual
-    CK(cudaMemcpyAsync(ap64, b, sizeof(double) * (size_t)n * s.ld, cudaMemcpyDeviceToDevice, st));
     {
       std::vector<double> ones(n, 1.0);
       CK(cudaMemcpyAsync(rel, ones.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
@@ -963,16 +1031,19 @@ int solve_rhs(pdep_ctx* c, SysData& s, const double* b, double* x, int n, int* h
       RET(read_int(c, c->d_counter + 1, &n_un, st));
       if (n_un == 0) break;
       rounds = round + 1;
-      CK(refine_prepare(ap64, s.ld, s.n_pw, n, rel, tol, r32, s.ld, rn, st));
+      CK(refine_prepare(r64, s.ld, s.n_pw, n, rel, tol, r32, s.ld, rn, st));
       bool cap = false;
       RET(cg_loop<float>(c, s, r32, d32, n, c->opt.inner_tol, c->opt.inner_max_iter, sc, st, &cap));
       std::vector<int> its;
       RET(collect_cg_stats(c, sc, n, nullptr, st, &its));
       for (int i = 0; i < n; ++i) its_total[i] += its[i];
-      CK(refine_accumulate(x, s.ld, d32, s.ld, s.n_pw, n, rn, st));
-      // FP64 residual of the active RHS: ap64 = b - A x
-      RET(apply_h<double>(c, s, x, ap64, n, list, n_un, true, true, st));
-      CK(residual_norms(b, s.ld, ap64, s.ld, s.n_pw, n_un, rel, list, st));
+      // delta = rn d32 (+ xd in the first round, when every RHS is listed);
+      // x += delta; r -= A delta in FP64, and the density response of delta
+      // is accumulated by the same transform (dn is linear in x)
+      const double* xr = round == 0 ? xd : nullptr;
+      CK(refine_delta(x, dl, s.ld, d32, s.ld, s.n_pw, n, rn, xr, st));
+      RET(apply_h<double>(c, s, dl, ad, n, list, n_un, true, true, st, dn));
+      CK(residual_update(r64, ad, b, s.ld, s.n_pw, n_un, rel, list, xr, s.d_sigma64, s.n_occ, st));
     }
     {
       CK(unconverged_list(rel, tol, n, list, c->d_counter + 1, st));
@@ -982,13 +1053,8 @@ int solve_rhs(pdep_ctx* c, SysData& s, const double* b, double* x, int n, int* h
     }
   }
   c->st_refine_max = std::max(c->st_refine_max, rounds);
-  if (c->opt.precision == PDEP_FP64) {
-    // FP64 residual of the CG solution (the recursion only tracks its own)
-    RET(apply_h<double>(c, s, x, ap64, n, nullptr, 0, true, true, st));
-    CK(residual_norms(b, s.ld, ap64, s.ld, s.n_pw, n, rel, nullptr, st));
-  }
-  // mixed: rel already holds the FP64 residual of every RHS from its last
-  // refinement round.  No final P_c projection is needed: the shifted
+  // rel holds the FP64 residual of every RHS from its last update.  No final
+  // P_c projection is needed: the shifted
   // operator lifts occupied state w to eps_{n_ext} - eps_v > 0, so the
   // occupied component of x is at most ||b - A x|| / (eps_{n_ext} - eps_v).
   std::vector<double> hr(n);
@@ -1036,28 +1102,6 @@ int build_rhs(pdep_ctx* c, SysData& s, const double* dv, int m, double* bvec, do
   return PDEP_OK;
 }
 
-// dn_j(r) = (4/Omega) sum_v u_v(r) du_vj(r) for x [m*n_occ][ld]  (Eq. deltani)
-int density(pdep_ctx* c, SysData& s, const double* x, int m, double* dn, cudaStream_t st) {
-  const int nocc = s.n_occ;
-  ItemMap map{nocc, (nocc + 1) / 2};
-  const int n_items = m * ((nocc + 1) / 2);
-  cpx<double>* b1;
-  RET(ws(c, "b1_64", b1_count(s, n_items), &b1));
-  CK(launch_cols_fwd<double>(s.sd, x, s.ld, map, n_items, COEF_ONE, b1, st));
-  SlabArgs<double> a{};
-  a.mode = SLAB_DENSITY;
-  a.b1 = b1;
-  a.n_items = n_items;
-  a.out = dn;
-  a.out_stride = s.n_r;
-  a.out_scale = 4.0 / s.omega;
-  a.src.g = s.d_u;
-  a.src.g_stride = s.n_r;
-  a.map = map;
-  CK(launch_slab<double>(s.sd, a, st));
-  return PDEP_OK;
-}
-
 // chi0bar phi for m PDEP vectors (internal layout [m][ld], G=0 slot zero)
 int chi0_internal(pdep_ctx* c, SysData& s, const double* phi, int m, double* out, double* dn_out,
                   cudaStream_t st) {
@@ -1099,10 +1143,10 @@ int chi0_internal(pdep_ctx* c, SysData& s, const double* phi, int m, double* out
     double* xd = nullptr;
     if (s.n_defl > 0) RET(ws(c, "c0_xd", (size_t)mc * nocc * s.ld, &xd));
     RET(build_rhs(c, s, dv, mc, bvec, xd, st));
-    int r = solve_rhs(c, s, bvec, xvec, mc * nocc, nullptr, nullptr, st);
+    // the density response dn (Eq. deltani) is accumulated inside the
+    // solver's FP64 transforms of the solution updates
+    int r = solve_rhs(c, s, bvec, xd, xvec, mc * nocc, dn, nullptr, nullptr, st);
     if (r != PDEP_OK && r != PDEP_ERR_NOT_CONVERGED) return r;
-    if (xd) CK(add_cols(xvec, xd, s.ld, s.n_pw, mc * nocc, st));
-    RET(density(c, s, xvec, mc, dn, st));
     // (chi0bar phi_j)(G) = sqrt(4pi)/|G| * Omega^{1/2}/N_r * FFT[dn_j](G)
     {
       ItemMap map{mc, (mc + 1) / 2};
@@ -1226,6 +1270,7 @@ void pdep_default_options(pdep_options* o) {
   o->setup_max_iter = 400;
   o->workspace_limit_bytes = 0;
   o->n_deflate = 16;
+  o->proj_variant = -1;
 }
 
 const char* pdep_status_string(int s) {
@@ -1462,9 +1507,8 @@ int sternheimer_solve(pdep_ctx* c, int sys, const double* dv_r, int n_pert, doub
   RET(build_rhs(c, s, dv, n_pert, bvec, xd, st));
   std::vector<int> hi(n);
   std::vector<double> hr(n);
-  int r = solve_rhs(c, s, bvec, xvec, n, hi.data(), hr.data(), st);
+  int r = solve_rhs(c, s, bvec, xd, xvec, n, nullptr, hi.data(), hr.data(), st);
   if (r != PDEP_OK && r != PDEP_ERR_NOT_CONVERGED) return r;
-  if (xd) CK(add_cols(xvec, xd, s.ld, s.n_pw, n, st));
   CK(cudaMemcpy2DAsync(dpsi, s.n_pw * sizeof(double), xvec, s.ld * sizeof(double),
                        s.n_pw * sizeof(double), n, kind_from_dev(dpsi), st));
   RET(sync(st));
@@ -1562,6 +1606,7 @@ int pdep_solve(pdep_ctx* c, int sys, const double* phi0, double* eigvals, double
     stats->refine_rounds_max = c->st_refine_max;
     stats->max_cg_residual = c->st_max_res;
     stats->cg_variant = c->cg_variant[c->opt.precision == PDEP_FP64 ? 1 : 0];
+    stats->proj_variant = c->opt.proj_variant >= 0 ? c->opt.proj_variant : c->proj_variant;
     stats->seconds =
         std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }

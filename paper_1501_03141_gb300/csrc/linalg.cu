@@ -982,27 +982,6 @@ template cudaError_t cg_start<float>(const CgArgs<float>&, const float*, long lo
 template cudaError_t cg_step<double>(const CgArgs<double>&, const int*, int, cudaStream_t);
 template cudaError_t cg_step<float>(const CgArgs<float>&, const int*, int, cudaStream_t);
 
-__global__ void k_residual_norms(const double* __restrict__ b, long long ldb, double* ap,
-                                 long long lda, int n_pw, double* rel, const int* __restrict__ list) {
-  const int i = list ? list[blockIdx.x] : blockIdx.x;
-  double rr = 0.0, bb = 0.0;
-  for (int j = threadIdx.x; j < n_pw; j += blockDim.x) {
-    const double bv = b[(long long)i * ldb + j];
-    const double r = bv - ap[(long long)i * lda + j];
-    ap[(long long)i * lda + j] = r;
-    rr += r * r;
-    bb += bv * bv;
-  }
-  double2 t = block_sum2(rr, bb);
-  if (threadIdx.x == 0) rel[i] = t.y > 0.0 ? sqrt(t.x / t.y) : 0.0;
-}
-cudaError_t residual_norms(const double* b, long long ldb, double* ap, long long lda, int n_pw,
-                           int n, double* rel, const int* list, cudaStream_t st) {
-  if (n <= 0) return cudaSuccess;
-  { count_launch(); k_residual_norms<<<n, 256, 0, st>>>(b, ldb, ap, lda, n_pw, rel, list); }
-  return cudaGetLastError();
-}
-
 // ordered compaction with one block of 1024 threads (contiguous chunks + scan)
 template <typename Pred>
 __device__ void compact_block(int n, Pred pred, int* list, int* count) {
@@ -1080,6 +1059,72 @@ cudaError_t refine_accumulate(double* x64, long long ld64, const float* d32, lon
                               int n_pw, int n, const double* rn, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   { count_launch(); k_refine_accumulate<<<n, 256, 0, st>>>(x64, ld64, d32, ld32, n_pw, rn); }
+  return cudaGetLastError();
+}
+
+// One refinement update in FP64.  With d32: delta_i = rn_i d32_i (+ xd_i);
+// vectors with rn_i = 0 and no xd are skipped.  Without d32 (the FP64 path,
+// x holding the whole CG solution): delta_i = x_i + xd_i.  Then x_i += delta_i
+// (x_i = delta_i without d32) and dl_i = delta_i.
+__global__ void k_refine_delta(double* x, double* dl, long long ld, const float* __restrict__ d32,
+                               long long ld32, int n_pw, const double* __restrict__ rn,
+                               const double* __restrict__ xd) {
+  const int i = blockIdx.x;
+  const double f = rn ? rn[i] : 0.0;
+  if (d32 && f == 0.0 && !xd) return;
+  double* xi = x + (long long)i * ld;
+  double* di = dl + (long long)i * ld;
+  const double* xdi = xd ? xd + (long long)i * ld : nullptr;
+  for (int j = threadIdx.x; j < n_pw; j += blockDim.x) {
+    double d;
+    if (d32) {
+      d = (f != 0.0 ? f * (double)d32[(long long)i * ld32 + j] : 0.0) + (xdi ? xdi[j] : 0.0);
+      xi[j] += d;
+    } else {
+      d = xi[j] + (xdi ? xdi[j] : 0.0);
+      xi[j] = d;
+    }
+    di[j] = d;
+  }
+}
+cudaError_t refine_delta(double* x, double* dl, long long ld, const float* d32, long long ld32,
+                         int n_pw, int n, const double* rn, const double* xd, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  { count_launch(); k_refine_delta<<<n, 256, 0, st>>>(x, dl, ld, d32, ld32, n_pw, rn, xd); }
+  return cudaGetLastError();
+}
+
+// r_i -= ad_i (+ s_{i mod n_occ} xd_i), rel_i = ||r_i|| / ||b_i|| for the
+// listed (or all) vectors.  s_v = eps_{n_ext} - eps_v is the shifted
+// operator's eigenvalue on the deflated states, so s_v xd_i = A xd_i.
+__global__ void k_residual_update(double* r, const double* __restrict__ ad,
+                                  const double* __restrict__ b, long long ld, int n_pw,
+                                  double* rel, const int* __restrict__ list,
+                                  const double* __restrict__ xd, const double* __restrict__ sv,
+                                  int n_occ) {
+  const int i = list ? list[blockIdx.x] : blockIdx.x;
+  const long long o = (long long)i * ld;
+  const double s = xd ? sv[i % n_occ] : 0.0;
+  double rr = 0.0, bb = 0.0;
+  for (int j = threadIdx.x; j < n_pw; j += blockDim.x) {
+    double v = r[o + j] - ad[o + j];
+    if (xd) v += s * xd[o + j];
+    r[o + j] = v;
+    const double bv = b[o + j];
+    rr += v * v;
+    bb += bv * bv;
+  }
+  double2 t = block_sum2(rr, bb);
+  if (threadIdx.x == 0) rel[i] = t.y > 0.0 ? sqrt(t.x / t.y) : 0.0;
+}
+cudaError_t residual_update(double* r, const double* ad, const double* b, long long ld, int n_pw,
+                            int n, double* rel, const int* list, const double* xd,
+                            const double* sv, int n_occ, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  {
+    count_launch();
+    k_residual_update<<<n, 256, 0, st>>>(r, ad, b, ld, n_pw, rel, list, xd, sv, n_occ);
+  }
   return cudaGetLastError();
 }
 
@@ -1200,19 +1245,6 @@ cudaError_t scale_rows(R* S, int lds, int rows, int n, const R* sigma, cudaStrea
 template cudaError_t scale_rows<double>(double*, int, int, int, const double*, cudaStream_t);
 template cudaError_t scale_rows<float>(float*, int, int, int, const float*, cudaStream_t);
 
-__global__ void k_add_cols(double* y, const double* __restrict__ x, long long ld, int rows) {
-  const long long o = (long long)blockIdx.y * ld;
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x)
-    y[o + r] += x[o + r];
-}
-cudaError_t add_cols(double* y, const double* x, long long ld, int rows, int n, cudaStream_t st) {
-  if (n <= 0) return cudaSuccess;
-  int bx = (rows + 255) / 256;
-  if (bx > 64) bx = 64;
-  count_launch();
-  k_add_cols<<<dim3(bx, n), 256, 0, st>>>(y, x, ld, rows);
-  return cudaGetLastError();
-}
 
 __global__ void k_zero_row(double* X, long long ld, int row, int n) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)

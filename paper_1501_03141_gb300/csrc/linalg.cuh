@@ -57,6 +57,18 @@ cudaError_t scale_by_isqrt_clamped(double* Q, long long ldq, int n, const double
                                    int* keep, cudaStream_t st);
 cudaError_t fill_zero(void* p, size_t bytes, cudaStream_t st);
 
+// Tensor-core (3xTF32, mma.sync) FP32 projections, all matrices column-major:
+// S (M x N, lds) = diag(sigma) P^T X(:, bmap)      (K = rows of P and X)
+// Y(:, cmap) (M x N) += P (M x K) S (K x N, lds)
+// Rows of P, X, Y and S must start on 16-byte boundaries (ldp, ldx, lds
+// multiples of 4 floats; aligned bases).
+cudaError_t tc_proj_coeffs(int M, int N, int K, const float* P, long long ldp, const float* X,
+                           long long ldx, const int* bmap, const float* sigma, float* S,
+                           long long lds, cudaStream_t st);
+cudaError_t tc_proj_update(int M, int N, int K, const float* P, long long ldp, const float* S,
+                           long long lds, float* Y, long long ldy, const int* cmap,
+                           cudaStream_t st);
+
 // Per-RHS preconditioned CG kernels (one CTA per RHS vector).
 // State of one RHS: x, r, p (length n_pw, stride ld), scalars in CgScal.
 struct CgScal {
@@ -103,11 +115,6 @@ cudaError_t cg_step(const CgArgs<R>& a, const int* list, int n_list, cudaStream_
 cudaError_t build_precond(const double* g2, int n_half, int n_pw, const double* ekin, int n_occ,
                           double* k64, float* k32, long long ld, cudaStream_t st);
 
-// y[:, i] = b[:, i] - y[:, i] (FP64), with per-column norms ||y_i|| / ||b_i||,
-// for every i < n, or for i in list[0..n) when list is given.
-cudaError_t residual_norms(const double* b, long long ldb, double* ap, long long lda, int n_pw,
-                           int n, double* rel, const int* list, cudaStream_t st);
-
 // Ordered list of the RHS with sc[i].active (list[0..count)), one block.
 cudaError_t active_list(const CgScal* sc, int n, int* list, int* count, cudaStream_t st);
 // Ordered list of i with rel[i] > tol.
@@ -122,6 +129,14 @@ cudaError_t refine_prepare(const double* r64, long long ld64, int n_pw, int n, c
 cudaError_t refine_accumulate(double* x64, long long ld64, const float* d32, long long ld32,
                               int n_pw, int n, const double* rn, cudaStream_t st);
 
+// Refinement update in FP64: delta_i = rn_i d32_i (+ xd_i), x_i += delta_i,
+// dl_i = delta_i; with d32 = null, delta_i = x_i + xd_i and x_i = delta_i.
+cudaError_t refine_delta(double* x, double* dl, long long ld, const float* d32, long long ld32,
+                         int n_pw, int n, const double* rn, const double* xd, cudaStream_t st);
+// r_i -= ad_i (+ sv[i % n_occ] xd_i); rel_i = ||r_i|| / ||b_i|| (listed vectors)
+cudaError_t residual_update(double* r, const double* ad, const double* b, long long ld, int n_pw,
+                            int n, double* rel, const int* list, const double* xd,
+                            const double* sv, int n_occ, cudaStream_t st);
 // Kinetic energy sum_k |G_k|^2/2 (x_2k^2 + x_2k+1^2) of each column.
 cudaError_t kinetic_energy(const double* X, long long ld, int n_half, int n, const double* g2,
                            double* out, cudaStream_t st);
@@ -145,8 +160,6 @@ cudaError_t deflation_coefficients(double* S, int lds, int n_occ, int n_defl, in
 // S[w, i] *= sigma[w] for w < rows, i < n (S column-major, leading dimension lds)
 template <typename R>
 cudaError_t scale_rows(R* S, int lds, int rows, int n, const R* sigma, cudaStream_t st);
-// y[:, i] += x[:, i] for n columns of rows entries
-cudaError_t add_cols(double* y, const double* x, long long ld, int rows, int n, cudaStream_t st);
 // X[row, i] = 0 for every column i (e.g. the G = 0 slot of PDEP vectors)
 cudaError_t zero_row(double* X, long long ld, int row, int n, cudaStream_t st);
 

@@ -19,7 +19,7 @@ struct Acc {
 };
 const char* kNames[PDEP_PROFILE_CLASSES] = {"cols_f64", "cols_f32", "slab_f64", "slab_f32",
                                             "gemm_f64", "gemm_f32", "cg_f64",   "cg_f32",
-                                            "eigh",     "other"};
+                                            "eigh",     "other",    "gemm_tf32x3"};
 struct Profiler {
   bool on = false;
   std::atomic<long long> launches{0};

@@ -16,6 +16,7 @@ enum ProfClass : int {
   PC_CG_F32 = 7,
   PC_EIGH = 8,
   PC_OTHER = 9,
+  PC_GEMM_TF32 = 10,  // tensor-core (3xTF32) FP32 projections
 };
 
 // counts one kernel launch (always cheap)

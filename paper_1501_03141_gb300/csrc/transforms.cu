@@ -305,51 +305,6 @@ __global__ void __launch_bounds__(SlabThreads<R, N2, N3>::v, (SlabMinBlocks<R, N
   const int zper = blockDim.x / TL3;
   const long long plane = (long long)i1 * N2 * N3;
 
-  if (a.mode == SLAB_DENSITY) {
-    // one group (e.g. one perturbation j) per block; z-lines in a single round
-    const int grp = blockIdx.x;
-    const int i2 = threadIdx.x / TL3;
-    const bool act = i2 < N2;
-    R acc[M3];
-#pragma unroll
-    for (int i = 0; i < M3; ++i) acc[i] = R(0);
-    for (int w = 0; w < a.map.items_per_group; ++w) {
-      const int item = grp * a.map.items_per_group + w;
-      const cpx<R>* row = a.b1 + ((long long)item * s.N1 + i1) * s.n_col;
-      for (int j = threadIdx.x; j < s.n_col; j += blockDim.x) S1[j] = row[j];
-      __syncthreads();
-      y_inverse<R, N2>(s, S1, T2);
-      __syncthreads();
-      cpx<R> v[M3];
-#pragma unroll
-      for (int i = 0; i < M3; ++i) {
-        const int n3 = freq_of(pos_a<N3, TL3>(t3, i), N3);
-        v[i] = (act && iabs(n3) <= R3) ? T2[(n3 + R3) * TS + i2] : zero<R>();
-      }
-      fft_a2b<R, N3, TL3, +1>(v, t3, s.tw3);
-      const int va = 2 * w, vb = 2 * w + 1;
-      if (act) {
-        const R* ga = a.src.g + (long long)va * a.src.g_stride + plane + (long long)i2 * N3;
-        const R* gb = vb < a.map.vecs_per_group
-                          ? a.src.g + (long long)vb * a.src.g_stride + plane + (long long)i2 * N3
-                          : nullptr;
-#pragma unroll
-        for (int i = 0; i < M3; ++i) {
-          const int i3 = pos_b<N3, TL3>(t3, i);
-          acc[i] += v[i].x * ga[i3];
-          if (gb) acc[i] += v[i].y * gb[i3];
-        }
-      }
-      __syncthreads();
-    }
-    if (act) {
-      R* o = a.out + (long long)grp * a.out_stride + plane + (long long)i2 * N3;
-#pragma unroll
-      for (int i = 0; i < M3; ++i) o[pos_b<N3, TL3>(t3, i)] = acc[i] * (R)a.out_scale;
-    }
-    return;
-  }
-
   const int item = blockIdx.x;
   cpx<R>* row = a.b1 + ((long long)item * s.N1 + i1) * s.n_col;
   if (a.mode != SLAB_FROM_GRID) {
@@ -399,6 +354,38 @@ __global__ void __launch_bounds__(SlabThreads<R, N2, N3>::v, (SlabMinBlocks<R, N
           }
         }
         continue;
+      }
+      if constexpr (sizeof(R) == 8) {
+        if (a.dn && act) {
+          // density response of the two vectors of the item on this z-line
+          // (Eq. deltani), accumulated over the occupied states v
+          const int ia = a.map.vec(item, 0), ib = a.map.vec(item, 1);
+          const long long off = plane + (long long)i2 * N3;
+          const int ja = ia / a.dn_nocc, vb_a = ia - ja * a.dn_nocc;
+          const double* ua = a.u + (long long)vb_a * a.dn_stride + off;
+          double* da = a.dn + (long long)ja * a.dn_stride + off;
+          const int jb = ib >= 0 ? ib / a.dn_nocc : -1;
+          const double* ub = ib >= 0 ? a.u + (long long)(ib - jb * a.dn_nocc) * a.dn_stride + off
+                                     : nullptr;
+          double* db = ib >= 0 ? a.dn + (long long)jb * a.dn_stride + off : nullptr;
+          const double sc = a.dn_scale;
+#pragma unroll
+          for (int i = 0; i < M3; ++i) {
+            const int i3 = pos_b<N3, TL3>(t3, i);
+            const double ca = sc * v[i].x * ua[i3];
+            if (ub) {
+              const double cb = sc * v[i].y * ub[i3];
+              if (jb == ja) {
+                atomicAdd(da + i3, ca + cb);
+              } else {
+                atomicAdd(da + i3, ca);
+                atomicAdd(db + i3, cb);
+              }
+            } else {
+              atomicAdd(da + i3, ca);
+            }
+          }
+        }
       }
       // SLAB_HPSI: multiply by the local potential on the grid
       const R* vr = a.v + plane + (long long)i2 * N3;
@@ -472,7 +459,7 @@ template <typename R, int N2, int N3>
 static cudaError_t slab_impl(const SphereDev<R>& s, const SlabArgs<R>& a, cudaStream_t st) {
   int nt = threads_for<R, N3>(N2);
   int ny = threads_for<R, N2>(2 * s.R3 + 1);
-  if (a.mode != SLAB_DENSITY && ny > nt) nt = ny;
+  if (ny > nt) nt = ny;
   if (nt > SlabThreads<R, N2, N3>::v) return cudaErrorInvalidConfiguration;
   const size_t smem = slab_smem_bytes(s.n_col, s.R3, N2, sizeof(R));
   auto kern = k_slab<R, N2, N3>;
@@ -482,7 +469,7 @@ static cudaError_t slab_impl(const SphereDev<R>& s, const SlabArgs<R>& a, cudaSt
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  const int gx = a.mode == SLAB_DENSITY ? a.n_items / a.map.items_per_group : a.n_items;
+  const int gx = a.n_items;
   if (gx == 0) return cudaSuccess;
   dim3 grid(gx, s.N1);
   // algorithmic work: y-lines over the |n3| <= R3 planes and z-lines over the
@@ -495,13 +482,19 @@ static cudaError_t slab_impl(const SphereDev<R>& s, const SlabArgs<R>& a, cudaSt
   double fl = 0, by = 0;
   switch (a.mode) {
     case SLAB_HPSI: fl = planes * (2 * ylines * fy + 2 * zlines * fz + 2.0 * N2 * N3);
-                    by = planes * 2 * colb + s.N1 * gridb; break;
+                    by = planes * 2 * colb + s.N1 * gridb;
+                    if (a.dn) {
+                      // density response: 2 products per point and vector; dn
+                      // read and written once per perturbation, u read once
+                      fl += planes * 4.0 * N2 * N3;
+                      by += (2.0 * a.n_items / a.dn_nocc) * s.N1 * 2.0 * gridb +
+                            (double)a.dn_nocc * s.N1 * gridb;
+                    }
+                    break;
     case SLAB_TO_GRID: fl = planes * (ylines * fy + zlines * fz);
                        by = planes * (colb + 2 * gridb); break;
     case SLAB_FROM_GRID: fl = planes * (ylines * fy + zlines * fz + 3.0 * N2 * N3);
                          by = planes * (colb + 3 * gridb); break;
-    case SLAB_DENSITY: fl = planes * (ylines * fy + zlines * fz + 4.0 * N2 * N3);
-                       by = planes * (colb + 2 * gridb) + (double)gx * s.N1 * gridb; break;
   }
   ProfScope ps(sizeof(R) == 8 ? PC_SLAB_F64 : PC_SLAB_F32, st, fl, by);
   count_launch();

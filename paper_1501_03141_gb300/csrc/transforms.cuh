@@ -88,7 +88,6 @@ enum SlabMode : int {
   SLAB_HPSI = 0,       // cols -> grid -> *V -> cols
   SLAB_TO_GRID = 1,    // cols -> grid, written as two real fields
   SLAB_FROM_GRID = 2,  // grid (GridSrc) -> cols
-  SLAB_DENSITY = 3,    // cols -> grid, out += Re*ga + Im*gb over items of a group
 };
 
 template <typename R>
@@ -98,10 +97,17 @@ struct SlabArgs {
   int n_items;
   const R* v;            // local potential [N_r] (HPSI)
   R* out;                // TO_GRID: two fields per item at vec(item,s)*out_stride
-  long long out_stride;  // DENSITY: group g writes out + g*out_stride
+  long long out_stride;
   double out_scale;
-  GridSrc<R> src;        // FROM_GRID / DENSITY (g = occupied grids)
+  GridSrc<R> src;        // FROM_GRID (f: one grid per group, g: per-vector grids)
   ItemMap map;
+  // HPSI (FP64 only): also accumulate dn_j(r) += dn_scale u_v(r) x_vj(r) for
+  // every vector i = j * dn_nocc + v of the item (atomically; dn may be null)
+  double* dn = nullptr;
+  const double* u = nullptr;  // occupied grids [dn_nocc][dn_stride]
+  int dn_nocc = 1;
+  long long dn_stride = 0;
+  double dn_scale = 0.0;
 };
 
 // Host launchers (stream-ordered; no synchronisation).
