@@ -153,25 +153,30 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def csrc_hash():
+def sources_hash(names):
+    """Hash of the CUDA sources a kernel class is built from."""
     h = hashlib.sha256()
-    for name in sorted(os.listdir(CSRC)):
-        if name.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(CSRC, name), "rb").read())
+    for name in sorted(names):
+        h.update(name.encode())
+        h.update(open(os.path.join(CSRC, name), "rb").read())
     return h.hexdigest()[:16]
 
 
 def traffic_for(cls_name, algorithmic_bytes_per_launch):
     """ncu DRAM bytes per launch of a kernel class: the DRAM/algorithmic ratio of a
-    captured launch of the current source, scaled to this class's average launch."""
+    captured launch, scaled to this class's average launch; None once any source
+    file of the class has changed since the capture."""
     try:
         t = json.load(open(TRAFFIC_FILE))
     except (OSError, ValueError):
         return None
-    if t.get("csrc_hash") != csrc_hash():
-        return None
     v = t.get("classes", {}).get(cls_name)
     if v is None:
+        return None
+    try:
+        if sources_hash(v["sources"]) != v["sources_hash"]:
+            return None
+    except (OSError, KeyError):
         return None
     return float(v["dram_over_algorithmic"]) * algorithmic_bytes_per_launch
 
