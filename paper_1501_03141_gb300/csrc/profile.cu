@@ -1,6 +1,8 @@
 // Kernel profiler of the library (see profile.cuh and pdep_profile in pdep.h).
 #include <atomic>
 #include <cstring>
+#include <list>
+#include <mutex>
 #include <vector>
 
 #include "profile.cuh"
@@ -12,6 +14,7 @@ struct Rec {
   int cls;
   cudaEvent_t a, b;
   double flops, bytes;
+  bool closed;  // the end event has been recorded
 };
 struct Acc {
   long long launches = 0;
@@ -20,10 +23,14 @@ struct Acc {
 const char* kNames[PDEP_PROFILE_CLASSES] = {"cols_f64", "cols_f32", "slab_f64", "slab_f32",
                                             "gemm_f64", "gemm_f32", "cg_f64",   "cg_f32",
                                             "eigh",     "other",    "gemm_tf32x3"};
+// Shared by every host thread that launches library kernels (the lanes of a
+// chi0bar application): the record list and the event pool are guarded by mu;
+// list nodes keep their addresses, so a scope can close its record later.
 struct Profiler {
-  bool on = false;
+  std::atomic<bool> on{false};
   std::atomic<long long> launches{0};
-  std::vector<Rec> pending;
+  std::mutex mu;
+  std::list<Rec> pending;
   std::vector<cudaEvent_t> pool;
   Acc acc[PDEP_PROFILE_CLASSES];
   cudaEvent_t get() {
@@ -36,8 +43,14 @@ struct Profiler {
     cudaEventCreate(&e);
     return e;
   }
+  // folds the closed records into acc (caller holds mu)
   void resolve() {
-    for (Rec& r : pending) {
+    for (auto it = pending.begin(); it != pending.end();) {
+      if (!it->closed) {
+        ++it;
+        continue;
+      }
+      Rec& r = *it;
       float ms = 0.f;
       if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
         Acc& a = acc[r.cls];
@@ -50,8 +63,8 @@ struct Profiler {
       }
       pool.push_back(r.a);
       pool.push_back(r.b);
+      it = pending.erase(it);
     }
-    pending.clear();
   }
 };
 Profiler& prof() {
@@ -66,9 +79,10 @@ void count_launch() {
 }
 
 ProfScope::ProfScope(int c, cudaStream_t s, double f, double b)
-    : cls(c), st(s), flops(f), bytes(b), slot(-1) {
+    : cls(c), st(s), flops(f), bytes(b), rec(nullptr) {
   Profiler& p = prof();
   if (!p.on) return;
+  std::lock_guard<std::mutex> g(p.mu);
   if (p.pending.size() >= 8192) p.resolve();
   Rec r;
   r.cls = c;
@@ -76,15 +90,19 @@ ProfScope::ProfScope(int c, cudaStream_t s, double f, double b)
   r.b = p.get();
   r.flops = f;
   r.bytes = b;
+  r.closed = false;
   cudaEventRecord(r.a, s);
   p.pending.push_back(r);
-  slot = (int)p.pending.size() - 1;
+  rec = &p.pending.back();
 }
 
 ProfScope::~ProfScope() {
+  if (!rec) return;
   Profiler& p = prof();
-  if (!p.on || slot < 0 || slot >= (int)p.pending.size()) return;
-  cudaEventRecord(p.pending[slot].b, st);
+  Rec* r = static_cast<Rec*>(rec);
+  cudaEventRecord(r->b, st);
+  std::lock_guard<std::mutex> g(p.mu);
+  r->closed = true;
 }
 
 }  // namespace pdep
@@ -92,6 +110,7 @@ ProfScope::~ProfScope() {
 extern "C" int pdep_profile(int enable, pdep_profile_t* out) {
   using namespace pdep;
   Profiler& p = prof();
+  std::lock_guard<std::mutex> g(p.mu);
   if (enable) {
     p.resolve();
     for (auto& a : p.acc) a = Acc();

@@ -29,7 +29,7 @@ struct ProfScope {
   int cls;
   cudaStream_t st;
   double flops, bytes;
-  int slot;
+  void* rec;  // the open record, or null while not profiling
 };
 
 }  // namespace pdep
