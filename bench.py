@@ -483,7 +483,9 @@ def run_small(args):
     import synthetic
     system = synthetic.make_system("cube48")
     prec = pg.PDEP_FP64 if args.case == "small64" else pg.PDEP_MIXED
-    with pg.Context(system, precision=prec) as ctx:
+    # the projection kernel is fixed here: timing-based autotuning is not
+    # meaningful under a profiler that serialises and replays launches
+    with pg.Context(system, precision=prec, proj_variant=args.proj) as ctx:
         dim = ctx.sizes()["n_pdep_dim"]
         phi = torch.tensor(synthetic.random_vectors(3, 16, dim), device="cuda")
         torch.cuda.synchronize()
@@ -505,6 +507,8 @@ def main(argv=None):
     ap.add_argument("--fp64-warmup", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--proj", type=int, default=1, choices=[0, 1],
+                    help="small cases: FP32 projection kernel (0 CUDA cores, 1 tensor cores)")
     ap.add_argument("--case", choices=["bench", "small", "small64"], default="bench",
                     help="small/small64: one chi0bar application of 16 perturbations "
                          "(mixed/FP64), for profiler captures")

@@ -204,6 +204,48 @@ int pdep_screening_apply(pdep_ctx* ctx, int sys, int kind, const double* eigvals
                          const double* eigvecs, int n_pdep, const double* f, int n, double* out,
                          void* stream);
 
+/* Body of chi0bar at imaginary frequencies in the PDEP basis (Sec. II B,
+ * Eq. finalB) and its RPA screening (Eq. Bfinal without head and wings):
+ *     B_ij(i nu) = phi_i^T chi0bar(i nu) phi_j
+ *               = 4 sum_v Re <xi_iv| P_c O(eps_v - i nu) P_c |xi_jv>,
+ *     xi_jv = dV_j psi_v, dV_j = v^{1/2} phi_j, O(w) = -(H - w)^{-1},
+ * each matrix element taken from the poles and weights of a Lanczos chain of
+ * P_c H P_c started on P_c xi_jv (n_steps steps, 1..64; Sec. II D, Eq.
+ * MCfinal), and
+ *     Lambda(i nu) = (1 - B)^{-1} B.
+ * phi [n_pdep][n_pdep_dim] (e.g. the eigenvectors from pdep_solve), nu
+ * [n_freq] (Ha, real, usually >= 0); B and Lambda [n_freq][n_pdep][n_pdep]
+ * (Lambda may be NULL).  B is symmetrised, (B + B^T)/2.  At nu = 0, B equals
+ * phi^T chi0bar phi up to the chains' truncation error.  Returns
+ * PDEP_ERR_INVALID_ARG for n_steps outside [1, 64] or n_pdep outside
+ * [1, n_pdep_dim], PDEP_ERR_NONFINITE if B has an eigenvalue >= 1. */
+int pdep_chi0_imag(pdep_ctx* ctx, int sys, const double* phi, int n_pdep, const double* nu,
+                   int n_freq, int n_steps, double* B, double* Lambda, void* stream);
+
+/* Batched Lanczos chains of the deflated Hamiltonian H~ = P_c H P_c
+ * (Sec. II D, Eqs. MCdef and MCfinal), FP64.  For each of n start vectors
+ * R [n][n_pw]: q_1 = P_c R / ||P_c R||, then n_steps (1..64; the paper uses
+ * 40) steps of the three-term recursion
+ *     alpha_k = <q_k|H~|q_k>,
+ *     beta_{k+1} q_{k+1} = (H~ - alpha_k) q_k - beta_k q_{k-1},
+ * without reorthogonalisation.  The tridiagonal T = tridiag(beta, alpha,
+ * beta) is diagonalised, T = U diag(d) U^T, and for n_L vectors L
+ * [n_L][n_pw] the omega-independent poles and weights of Eq. MCfinal are
+ * returned:
+ *     poles [n][n_steps]          d_k, ascending,
+ *     weights [n][n_L][n_steps]   ||P_c R|| sum_m <L|q_m> U_{m k} U_{1 k},
+ * so that for any complex omega off the spectrum
+ *     M_c,LR(omega) = -<L|(H~ - omega)^{-1}|R> ~ sum_k weights[k] / (omega - poles[k]).
+ * alpha and beta [n][n_steps] (may be NULL) receive the recursion: beta[0] =
+ * ||P_c R||, beta[k] (k >= 1) the off-diagonal T[k-1][k].  A chain that
+ * reaches an invariant subspace (beta_{k+1} <= 1e-12 ||H~ q_k||) stops; its
+ * later alphas, betas and weights are 0; a start vector with ||P_c R|| <=
+ * 1e-12 ||R|| gives an empty chain (all 0).  L and weights may be NULL when
+ * n_L = 0.  Returns PDEP_ERR_INVALID_ARG for n_steps outside [1, 64]. */
+int pdep_lanczos(pdep_ctx* ctx, int sys, const double* R, int n, int n_steps, const double* L,
+                 int n_L, double* poles, double* weights, double* alpha, double* beta,
+                 void* stream);
+
 /* y = H x for n sphere vectors x [n][n_pw] -> y [n][n_pw], H = -nabla^2/2 + V
  * (the local-potential Hamiltonian of the setup), evaluated with the pruned
  * sphere <-> grid transforms; precision PDEP_FP64 or PDEP_MIXED (FP32

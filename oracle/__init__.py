@@ -24,6 +24,9 @@ real orbitals:
 * ``screening``   reducible chibar = (1 - chi0bar)^{-1} chi0bar, epsbar^{-1} and
                   W^p at omega = 0 (Eqs. linearalgebrachichi0, epsilonandchi,
                   Wpnondiag), dense and in the PDEP basis.
+* ``lanczos``     Lanczos chains of the deflated Hamiltonian P_c H P_c and the
+                  omega-independent poles and weights of M_c(omega) (Sec. II D,
+                  Eqs. MCdef, MCfinal), and the exact sum over empty states.
 
 Pins (tests/test_oracle_*.py): free-electron closed form, finite-difference
 density and second-order band-energy response, brute-force matrix elements,
@@ -31,4 +34,4 @@ Sternheimer = sum over states, symmetry, negative semi-definiteness,
 charge neutrality, invariance under V -> V + const.  The paper prints no
 worked numerical example for this path, so no pin uses printed values.
 """
-from . import basis, hamiltonian, response, pdep, screening  # noqa: F401
+from . import basis, hamiltonian, response, pdep, screening, lanczos  # noqa: F401

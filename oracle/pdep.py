@@ -16,6 +16,12 @@ Test infrastructure (see ``oracle/__init__``).
 * ``free_electron_chi0bar``: the V = 0 closed form, diagonal in G:
       lambda(G) = 16 pi / (Omega |G|^2) sum_{k occ, k+G in S, not occ} 1/(eps_k - eps_{k+G}),
   eps_k = |k|^2 / 2, valid when the occupied set is a closed shell.
+* Imaginary frequencies (argument nu): at omega = i nu the two resonant
+  denominators of Eq. AdlerWiser add to
+      1/(eps_v - eps_c - i nu) + 1/(eps_v - eps_c + i nu)
+          = 2 (eps_v - eps_c) / ((eps_v - eps_c)^2 + nu^2),
+  so every 1/(eps_v - eps_c) above becomes (eps_v - eps_c)/((eps_v - eps_c)^2 + nu^2)
+  (nu = 0 gives the static forms).
 """
 from __future__ import annotations
 
@@ -38,8 +44,8 @@ def pair_coefficients(basis: Basis, u_occ, u_emp_block):
     return c[:, :-1].reshape(nocc, nb, basis.n_pdep_dim)
 
 
-def chi0bar_dense(basis: Basis, ks: KSStates, block: int = 64) -> np.ndarray:
-    """Dense chi0bar on the PDEP sphere, shape (2 n_half, 2 n_half)."""
+def chi0bar_dense(basis: Basis, ks: KSStates, block: int = 64, nu: float = 0.0) -> np.ndarray:
+    """Dense chi0bar(i nu) on the PDEP sphere, shape (2 n_half, 2 n_half)."""
     nocc = ks.n_occ
     u_occ = occupied_grid(basis, ks)
     dim = basis.n_pdep_dim
@@ -50,7 +56,7 @@ def chi0bar_dense(basis: Basis, ks: KSStates, block: int = 64) -> np.ndarray:
         u_emp = basis.coeffs_to_grid(ks.C[:, c0:c1].T)
         p = pair_coefficients(basis, u_occ, u_emp)               # (nocc, nb, dim)
         den = ev[:, None] - ks.eps[c0:c1][None, :]              # eps_v - eps_c
-        pw = p / den[:, :, None]
+        pw = p * (den / (den * den + nu * nu))[:, :, None]
         chi0 += 4.0 * np.einsum("vcg,vch->gh", pw, p, optimize=True)
     vh = basis.sqrt_coulomb()
     chib = vh[:, None] * chi0 * vh[None, :]
@@ -64,8 +70,8 @@ def pdep_reference(chib: np.ndarray, n_pdep: int):
     return lam[:n_pdep], vec[:, :n_pdep]
 
 
-def free_electron_chi0bar(basis: Basis, n_occ: int) -> np.ndarray:
-    """Closed-form eigenvalue of chi0bar per PDEP component for V = 0.
+def free_electron_chi0bar(basis: Basis, n_occ: int, nu: float = 0.0) -> np.ndarray:
+    """Closed-form eigenvalue of chi0bar(i nu) per PDEP component for V = 0.
 
     Requires the n_occ lowest plane waves to be a closed shell.
     Returns an array of length 2 n_half (both real components of G_k).
@@ -86,7 +92,7 @@ def free_electron_chi0bar(basis: Basis, n_occ: int) -> np.ndarray:
             if q in sphere_set and q not in occ_set:
                 ek = 0.5 * np.sum((2 * np.pi * np.asarray(k) / L) ** 2)
                 eq = 0.5 * np.sum((2 * np.pi * np.asarray(q) / L) ** 2)
-                s += 1.0 / (ek - eq)
+                s += (ek - eq) / ((ek - eq) ** 2 + nu * nu)
         G2 = np.sum((2 * np.pi * G / L) ** 2)
         lam[k_idx] = 16.0 * np.pi / (basis.omega * G2) * s
     return np.repeat(lam, 2)

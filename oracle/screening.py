@@ -20,7 +20,15 @@ which is what ``pdep_screening`` applies.  The dense functions take the
 whole chi0bar matrix and are the definition; ``pdep_screening`` is the
 low-rank form the GPU library computes.
 
+Frequency dependence (Sec. II B, Eqs. finalB and Bfinal): the body of chi0bar
+at imaginary frequency i nu in the PDEP basis,
+    B_ij(i nu) = phi_i^T chi0bar(i nu) phi_j,
+and its RPA screening Lambda(i nu) = (1 - B)^{-1} B (Eq. Bfinal without the
+head and wings, which lie outside the PDEP sphere).
+
 Functions
+* ``pdep_body``         B(i nu) = Phi^T chi0bar(i nu) Phi from a dense chi0bar(i nu).
+* ``lambda_body``       (1 - B)^{-1} B by a linear solve.
 * ``chibar_dyson``      dense (1 - chi0bar)^{-1} chi0bar by a linear solve.
 * ``epsinv_dense``      dense 1 + chibar.
 * ``wp_dense``          dense v^{1/2} chibar v^{1/2}.
@@ -75,3 +83,14 @@ def pdep_screening(kind: str, lam, vecs, f, sqrt_coulomb=None) -> np.ndarray:
     if kind == "epsinv":
         out = out + f
     return out
+
+
+def pdep_body(chi0bar_nu: np.ndarray, vecs) -> np.ndarray:
+    """B = Phi^T chi0bar(i nu) Phi for PDEP vectors vecs [dim, n_pdep] (Eq. finalB)."""
+    vecs = np.asarray(vecs, dtype=np.float64)
+    return vecs.T @ chi0bar_nu @ vecs
+
+
+def lambda_body(B: np.ndarray) -> np.ndarray:
+    """Lambda = (1 - B)^{-1} B (Eq. Bfinal, body only), by np.linalg.solve."""
+    return np.linalg.solve(np.eye(B.shape[0]) - B, B)

@@ -203,3 +203,31 @@ class Context:
                                                   int(f.shape[0]), _abi.ptr(out),
                                                   _stream(self.stream)), "pdep_screening_apply")
         return out
+
+    def lanczos(self, R, n_steps, L=None, sys: int = 0):
+        """Lanczos chains of P_c H P_c started on the rows of R [n, n_pw]
+        (Sec. II D).  Returns (poles [n, K], weights [n, n_L, K], alpha, beta);
+        M_c,LR(omega) ~ sum_k weights[., l, k] / (omega - poles[., k])."""
+        n = int(R.shape[0])
+        n_L = 0 if L is None else int(L.shape[0])
+        poles = np.empty((n, n_steps))
+        weights = np.empty((n, n_L, n_steps)) if n_L else None
+        alpha = np.empty((n, n_steps))
+        beta = np.empty((n, n_steps))
+        _abi.check(self._lib.pdep_lanczos(self._h, sys, _abi.ptr(R), n, int(n_steps), _abi.ptr(L),
+                                          n_L, _abi.ptr(poles), _abi.ptr(weights), _abi.ptr(alpha),
+                                          _abi.ptr(beta), _stream(self.stream)), "pdep_lanczos")
+        return poles, weights, alpha, beta
+
+    def chi0_imag(self, phi, nu, n_steps=40, sys: int = 0, with_lambda=True):
+        """B(i nu) = phi^T chi0bar(i nu) phi from Lanczos chains and Lambda =
+        (1 - B)^{-1} B for phi [n_pdep, n_pdep_dim] and frequencies nu [n_freq]
+        (Sec. II B); returns (B, Lambda) of shape [n_freq, n_pdep, n_pdep]."""
+        nu = np.ascontiguousarray(np.atleast_1d(np.asarray(nu, dtype=np.float64)))
+        n_pdep = int(phi.shape[0])
+        B = np.empty((nu.shape[0], n_pdep, n_pdep))
+        L = np.empty_like(B) if with_lambda else None
+        _abi.check(self._lib.pdep_chi0_imag(self._h, sys, _abi.ptr(phi), n_pdep, _abi.ptr(nu),
+                                            int(nu.shape[0]), int(n_steps), _abi.ptr(B),
+                                            _abi.ptr(L), _stream(self.stream)), "pdep_chi0_imag")
+        return B, L

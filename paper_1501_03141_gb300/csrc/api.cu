@@ -1074,8 +1074,10 @@ int solve_rhs(pdep_ctx* c, SysData& s, const double* b, const double* xd, double
 // b_vj = -P_c [dV_j psi_v] for perturbation grids dv [m][n_r]  -> bvec [m*n_occ][ld].
 // With deflation, bvec keeps only the part orthogonal to the deflated states
 // and xdefl [m*n_occ][ld] receives their exact share of the solution.
+// occupied_only: bvec = -P_c [dV_j psi_v] with P_c over the occupied states
+// alone (no deflation split; xdefl unused).
 int build_rhs(pdep_ctx* c, SysData& s, const double* dv, int m, double* bvec, double* xdefl,
-              cudaStream_t st) {
+              cudaStream_t st, bool occupied_only = false) {
   const int nocc = s.n_occ;
   ItemMap map{nocc, (nocc + 1) / 2};
   const int n_items = m * ((nocc + 1) / 2);
@@ -1098,7 +1100,36 @@ int build_rhs(pdep_ctx* c, SysData& s, const double* dv, int m, double* bvec, do
   ep.scale = -1.0 / s.n_r;
   ep.coef = COEF_ONE;
   CK(launch_cols_bwd<double>(s.sd, b1, map, n_items, ep, st));
+  if (occupied_only) {
+    double* S;
+    RET(ws(c, "po_S", (size_t)nocc * m * nocc, &S));
+    CK(gemm<double>(true, nocc, m * nocc, s.n_pw, 1.0, s.d_psi, s.ld, bvec, s.ld, 0.0, S, nocc, st));
+    CK(gemm<double>(false, s.n_pw, m * nocc, nocc, -1.0, s.d_psi, s.ld, S, nocc, 1.0, bvec, s.ld,
+                    st));
+    return PDEP_OK;
+  }
   RET(split_rhs(c, s, bvec, m * nocc, xdefl, st));
+  return PDEP_OK;
+}
+
+// dV_j(r) = Omega^{-1/2} sum_G sqrt(4pi)/|G| phi_j(G) e^{iG.r} for m PDEP
+// vectors phi [m][ld] -> dv [m][n_r]
+int perturbation_grids(pdep_ctx* c, SysData& s, const double* phi, int m, double* dv,
+                       cudaStream_t st) {
+  ItemMap map{m, (m + 1) / 2};
+  const int n_items = (m + 1) / 2;
+  cpx<double>* b1;
+  RET(ws(c, "b1_64", b1_count(s, n_items), &b1));
+  CK(launch_cols_fwd<double>(s.sd, phi, s.ld, map, n_items, COEF_SQRT_COULOMB, b1, st));
+  SlabArgs<double> a{};
+  a.mode = SLAB_TO_GRID;
+  a.b1 = b1;
+  a.n_items = n_items;
+  a.out = dv;
+  a.out_stride = s.n_r;
+  a.out_scale = 1.0 / std::sqrt(s.omega);
+  a.map = map;
+  CK(launch_slab<double>(s.sd, a, st));
   return PDEP_OK;
 }
 
@@ -1123,23 +1154,7 @@ int chi0_internal(pdep_ctx* c, SysData& s, const double* phi, int m, double* out
     else
       RET(ws(c, "c0_dn", (size_t)mc * s.n_r, &dn));
     // dV_j(r) = Omega^{-1/2} sum_G sqrt(4pi)/|G| phi_j(G) e^{iG.r}
-    {
-      ItemMap map{mc, (mc + 1) / 2};
-      const int n_items = (mc + 1) / 2;
-      cpx<double>* b1;
-      RET(ws(c, "b1_64", b1_count(s, n_items), &b1));
-      CK(launch_cols_fwd<double>(s.sd, phi + (size_t)j0 * s.ld, s.ld, map, n_items,
-                                 COEF_SQRT_COULOMB, b1, st));
-      SlabArgs<double> a{};
-      a.mode = SLAB_TO_GRID;
-      a.b1 = b1;
-      a.n_items = n_items;
-      a.out = dv;
-      a.out_stride = s.n_r;
-      a.out_scale = 1.0 / std::sqrt(s.omega);
-      a.map = map;
-      CK(launch_slab<double>(s.sd, a, st));
-    }
+    RET(perturbation_grids(c, s, phi + (size_t)j0 * s.ld, mc, dv, st));
     double* xd = nullptr;
     if (s.n_defl > 0) RET(ws(c, "c0_xd", (size_t)mc * nocc * s.ld, &xd));
     RET(build_rhs(c, s, dv, mc, bvec, xd, st));
@@ -1250,6 +1265,41 @@ int noalloc_sphere(pdep_ctx* c, int sys, SphereDev<double>* sd, const double** v
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
+// Lanczos chains of H~ = P_c H P_c on the nc vectors of W ([nc][ld], already
+// projected with P_c; W is overwritten), whose norms before the projection
+// are r0 [nc]: Q [K][nc][ld] (step-major), alpha and beta [nc][K], and the
+// tridiagonal eigen-decompositions d [nc][K], U [nc][K][K].
+int lanczos_core(pdep_ctx* c, SysData& s, double* W, const double* r0, int nc, int K, double* Q,
+                 double* da, double* db, double* dd, double* dU, cudaStream_t st) {
+  double* S;
+  RET(ws(c, "lz_S", (size_t)s.n_occ * nc, &S));
+  CK(cudaMemsetAsync(da, 0, sizeof(double) * (size_t)nc * K, st));
+  CK(cudaMemsetAsync(db, 0, sizeof(double) * (size_t)nc * K, st));
+  CK(lanczos_start(W, s.ld, s.n_pw, nc, K, r0, Q, db, st));
+  for (int k = 0; k < K; ++k) {
+    double* Qk = Q + (size_t)k * nc * s.ld;
+    // W = P_c H q_k (q_k lies in range(P_c), so this is H~ q_k)
+    RET(apply_h<double>(c, s, Qk, W, nc, nullptr, 0, false, false, st));
+    CK(gemm<double>(true, s.n_occ, nc, s.n_pw, 1.0, s.d_psi, s.ld, W, s.ld, 0.0, S, s.n_occ, st));
+    CK(gemm<double>(false, s.n_pw, nc, s.n_occ, -1.0, s.d_psi, s.ld, S, s.n_occ, 1.0, W, s.ld,
+                    st));
+    const double* Qkm1 = k > 0 ? Q + (size_t)(k - 1) * nc * s.ld : nullptr;
+    double* Qk1 = k + 1 < K ? Q + (size_t)(k + 1) * nc * s.ld : nullptr;
+    CK(lanczos_step(W, Qk, Qkm1, Qk1, s.ld, s.n_pw, nc, K, k, da, db, st));
+  }
+  CK(tridiag_eig(da, db, nc, K, dd, dU, st));
+  return PDEP_OK;
+}
+
+// P_c X for the n columns of X [n][ld] with the occupied states only
+int project_occupied(pdep_ctx* c, SysData& s, double* X, int n, cudaStream_t st) {
+  double* S;
+  RET(ws(c, "po_S", (size_t)s.n_occ * n, &S));
+  CK(gemm<double>(true, s.n_occ, n, s.n_pw, 1.0, s.d_psi, s.ld, X, s.ld, 0.0, S, s.n_occ, st));
+  CK(gemm<double>(false, s.n_pw, n, s.n_occ, -1.0, s.d_psi, s.ld, S, s.n_occ, 1.0, X, s.ld, st));
+  return PDEP_OK;
+}
+
 extern "C" {
 
 void pdep_default_options(pdep_options* o) {
@@ -1484,6 +1534,180 @@ int pdep_screening_apply(pdep_ctx* c, int sys, int kind, const double* eigvals,
   CK(cudaMemcpy2DAsync(out, dim * sizeof(double), o, s.ld * sizeof(double), dim * sizeof(double),
                        n, kind_from_dev(out), st));
   RET(sync(st));
+  return PDEP_OK;
+}
+
+// Body of chi0bar at imaginary frequencies in the PDEP basis (Eq. finalB,
+// Sec. II B) from Lanczos chains (Sec. II D, Eq. MCfinal), and the RPA body
+// Lambda = (1 - B)^{-1} B (Eq. Bfinal without head and wings).
+int pdep_chi0_imag(pdep_ctx* c, int sys, const double* phi, int n_pdep, const double* nu,
+                   int n_freq, int n_steps, double* B, double* Lambda, void* stream) {
+  RET(check_sys(c, sys));
+  SysData& s = c->sys[sys];
+  const int dim = s.n_pw - 1;
+  if (n_pdep < 1 || n_pdep > dim || n_freq < 0 || n_steps < 1 || n_steps > 64 ||
+      (n_freq > 0 && (!phi || !nu || !B)))
+    return fail(PDEP_ERR_INVALID_ARG, "bad pdep_chi0_imag arguments");
+  if (n_freq == 0) return PDEP_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int K = n_steps, nocc = s.n_occ, np = n_pdep;
+  std::vector<double> hnu(n_freq);
+  if (is_device_ptr(nu)) {
+    CK(cudaMemcpyAsync(hnu.data(), nu, sizeof(double) * n_freq, cudaMemcpyDeviceToHost, st));
+    RET(sync(st));
+  } else {
+    memcpy(hnu.data(), nu, sizeof(double) * n_freq);
+  }
+  for (double x : hnu)
+    if (!std::isfinite(x)) return fail(PDEP_ERR_INVALID_ARG, "non-finite frequency");
+  double *dphi, *dv, *R, *dnu, *Bd;
+  RET(ws(c, "fq_phi", (size_t)np * s.ld, &dphi));
+  RET(ws(c, "fq_dv", (size_t)np * s.n_r, &dv));
+  RET(ws(c, "fq_R", (size_t)np * nocc * s.ld, &R));
+  RET(ws(c, "fq_nu", (size_t)n_freq, &dnu));
+  RET(ws(c, "fq_B", (size_t)n_freq * np * np, &Bd));
+  CK(cudaMemcpyAsync(dnu, hnu.data(), sizeof(double) * n_freq, cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(dphi, 0, sizeof(double) * (size_t)np * s.ld, st));
+  CK(cudaMemcpy2DAsync(dphi, s.ld * sizeof(double), phi, dim * sizeof(double),
+                       dim * sizeof(double), np, kind_to_dev(phi), st));
+  CK(cudaMemsetAsync(Bd, 0, sizeof(double) * (size_t)n_freq * np * np, st));
+  // R_{j v} = -P_c [dV_j psi_v] (row j n_occ + v): the chains' start vectors
+  // and, for fixed v, the left vectors L_i of Eq. finalB
+  RET(perturbation_grids(c, s, dphi, np, dv, st));
+  RET(build_rhs(c, s, dv, np, R, nullptr, st, true));
+  // chains of a group of occupied states at a time
+  const size_t per_state = (size_t)np * ((size_t)K + 2) * s.ld * sizeof(double);
+  size_t budget = (size_t)16 << 30;
+  if (c->opt.workspace_limit_bytes) budget = c->opt.workspace_limit_bytes / 2;
+  const int nv_max = (int)std::max<size_t>(1, std::min<size_t>(budget / per_state, nocc));
+  std::vector<int> hidx, hmap((size_t)K * np);
+  for (int v0 = 0; v0 < nocc; v0 += nv_max) {
+    const int nvg = std::min(nv_max, nocc - v0);
+    const int ng = np * nvg;
+    double *Q, *W, *da, *db, *dd, *dU, *r0, *G, *z;
+    int *idx, *bmap;
+    RET(ws(c, "fq_Q", (size_t)K * ng * s.ld, &Q));
+    RET(ws(c, "fq_W", (size_t)ng * s.ld, &W));
+    RET(ws(c, "fq_a", (size_t)ng * K, &da));
+    RET(ws(c, "fq_b", (size_t)ng * K, &db));
+    RET(ws(c, "fq_d", (size_t)ng * K, &dd));
+    RET(ws(c, "fq_U", (size_t)ng * K * K, &dU));
+    RET(ws(c, "fq_r0", (size_t)ng, &r0));
+    RET(ws(c, "fq_G", (size_t)np * K * np, &G));
+    RET(ws(c, "fq_z", (size_t)n_freq * np * K, &z));
+    RET(ws(c, "fq_idx", (size_t)ng, &idx));
+    RET(ws(c, "fq_map", (size_t)K * np, &bmap));
+    // chain (j, v) of the group sits at j nvg + (v - v0)
+    hidx.resize(ng);
+    for (int j = 0; j < np; ++j)
+      for (int v = v0; v < v0 + nvg; ++v) hidx[(size_t)j * nvg + (v - v0)] = j * nocc + v;
+    CK(cudaMemcpyAsync(idx, hidx.data(), sizeof(int) * ng, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(W, 0, sizeof(double) * (size_t)ng * s.ld, st));
+    CK(gather_cols(R, s.ld, W, s.ld, s.n_pw, idx, ng, st));
+    CK(col_norms<double>(W, s.ld, s.n_pw, ng, r0, st));
+    RET(lanczos_core(c, s, W, r0, ng, K, Q, da, db, dd, dU, st));
+    for (int v = v0; v < v0 + nvg; ++v) {
+      // G[i][k np + j] = <R_{i v} | q_k of chain (j, v)>
+      for (int k = 0; k < K; ++k)
+        for (int j = 0; j < np; ++j) hmap[(size_t)k * np + j] = k * ng + j * nvg + (v - v0);
+      CK(cudaMemcpyAsync(bmap, hmap.data(), sizeof(int) * K * np, cudaMemcpyHostToDevice, st));
+      CK(gemm<double>(true, np, K * np, s.n_pw, 1.0, R + (size_t)v * s.ld, (long long)nocc * s.ld,
+                      Q, s.ld, 0.0, G, np, st, bmap, nullptr));
+      CK(lanczos_z(dU, dd, db, np, K, nvg, v - v0, s.eps[v], dnu, n_freq, z, st));
+      // B_ij += 2 (spin) x 2 (the two frequencies eps_v -+ i nu, equal in
+      // their real parts) x the chain sum
+      CK(body_accum(G, np, np, K, z, n_freq, 4.0, Bd, st));
+      RET(sync(st));  // hmap is reused for the next v
+    }
+  }
+  for (int f = 0; f < n_freq; ++f) CK(symmetrize<double>(Bd + (size_t)f * np * np, np, np, st));
+  CK(cudaMemcpyAsync(B, Bd, sizeof(double) * (size_t)n_freq * np * np, kind_from_dev(B), st));
+  if (Lambda) {
+    double *w, *V, *Ld;
+    RET(ws(c, "fq_w", (size_t)np, &w));
+    RET(ws(c, "fq_V", (size_t)np * np, &V));
+    RET(ws(c, "fq_L", (size_t)n_freq * np * np, &Ld));
+    EighWork wk;
+    RET(eigh_ws(c, np, &wk));
+    std::vector<double> hw(np);
+    for (int f = 0; f < n_freq; ++f) {
+      CK(eigh(np, Bd + (size_t)f * np * np, np, w, V, np, wk, st));
+      CK(cudaMemcpyAsync(hw.data(), w, sizeof(double) * np, cudaMemcpyDeviceToHost, st));
+      RET(sync(st));
+      for (double x : hw)
+        if (!(1.0 - x > 1e-12)) return fail(PDEP_ERR_NONFINITE, "B(i nu) has an eigenvalue >= 1");
+      CK(lambda_from_eig(V, w, np, Ld + (size_t)f * np * np, st));
+    }
+    CK(cudaMemcpyAsync(Lambda, Ld, sizeof(double) * (size_t)n_freq * np * np,
+                       kind_from_dev(Lambda), st));
+  }
+  RET(sync(st));
+  return PDEP_OK;
+}
+
+// Batched Lanczos chains of the deflated Hamiltonian P_c H P_c (Sec. II D):
+// poles and omega-independent weights of M_c,LR(omega) (Eq. MCfinal).
+int pdep_lanczos(pdep_ctx* c, int sys, const double* R, int n, int n_steps, const double* L,
+                 int n_L, double* poles, double* weights, double* alpha, double* beta,
+                 void* stream) {
+  RET(check_sys(c, sys));
+  if (n < 0 || n_steps < 1 || n_steps > 64 || n_L < 0 ||
+      (n > 0 && (!R || !poles || (n_L > 0 && (!L || !weights)))))
+    return fail(PDEP_ERR_INVALID_ARG, "bad pdep_lanczos arguments");
+  if (n == 0) return PDEP_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  SysData& s = c->sys[sys];
+  const int K = n_steps;
+  const int nocc = s.n_occ;
+  double* dL = nullptr;
+  if (n_L > 0) {
+    RET(ws(c, "lz_L", (size_t)n_L * s.ld, &dL));
+    CK(cudaMemsetAsync(dL, 0, sizeof(double) * (size_t)n_L * s.ld, st));
+    CK(cudaMemcpy2DAsync(dL, s.ld * sizeof(double), L, s.n_pw * sizeof(double),
+                         s.n_pw * sizeof(double), n_L, kind_to_dev(L), st));
+  }
+  // chains in chunks: Q holds K blocks of nc vectors (step-major)
+  const size_t per_chain = (size_t)(K + 3) * s.ld * sizeof(double);
+  size_t budget = (size_t)16 << 30;
+  if (c->opt.workspace_limit_bytes) budget = c->opt.workspace_limit_bytes / 2;
+  const int nc_max = (int)std::max<size_t>(1, std::min<size_t>(budget / per_chain, 65535));
+  for (int j0 = 0; j0 < n; j0 += nc_max) {
+    const int nc = std::min(nc_max, n - j0);
+    double *Q, *W, *da, *db, *dd, *dU, *r0, *G = nullptr, *dw = nullptr;
+    RET(ws(c, "lz_Q", (size_t)K * nc * s.ld, &Q));
+    RET(ws(c, "lz_W", (size_t)nc * s.ld, &W));
+    RET(ws(c, "lz_a", (size_t)nc * K, &da));
+    RET(ws(c, "lz_b", (size_t)nc * K, &db));
+    RET(ws(c, "lz_d", (size_t)nc * K, &dd));
+    RET(ws(c, "lz_U", (size_t)nc * K * K, &dU));
+    RET(ws(c, "lz_r0", (size_t)nc, &r0));
+    CK(cudaMemsetAsync(W, 0, sizeof(double) * (size_t)nc * s.ld, st));
+    CK(cudaMemcpy2DAsync(W, s.ld * sizeof(double), R + (size_t)j0 * s.n_pw,
+                         s.n_pw * sizeof(double), s.n_pw * sizeof(double), nc, kind_to_dev(R),
+                         st));
+    // P_c R (norms kept for the empty-chain test), then the chains
+    CK(col_norms<double>(W, s.ld, s.n_pw, nc, r0, st));
+    RET(project_occupied(c, s, W, nc, st));
+    RET(lanczos_core(c, s, W, r0, nc, K, Q, da, db, dd, dU, st));
+    if (n_L > 0) {
+      RET(ws(c, "lz_G", (size_t)n_L * K * nc, &G));
+      RET(ws(c, "lz_w", (size_t)nc * n_L * K, &dw));
+      // G[l][k nc + j] = <L_l | q_k of chain j>
+      CK(gemm<double>(true, n_L, K * nc, s.n_pw, 1.0, dL, s.ld, Q, s.ld, 0.0, G, n_L, st));
+      CK(lanczos_weights(G, n_L, nc, K, dU, db, dw, 1, 0, st));
+      CK(cudaMemcpyAsync(weights + (size_t)j0 * n_L * K, dw, sizeof(double) * (size_t)nc * n_L * K,
+                         kind_from_dev(weights), st));
+    }
+    CK(cudaMemcpyAsync(poles + (size_t)j0 * K, dd, sizeof(double) * (size_t)nc * K,
+                       kind_from_dev(poles), st));
+    if (alpha)
+      CK(cudaMemcpyAsync(alpha + (size_t)j0 * K, da, sizeof(double) * (size_t)nc * K,
+                         kind_from_dev(alpha), st));
+    if (beta)
+      CK(cudaMemcpyAsync(beta + (size_t)j0 * K, db, sizeof(double) * (size_t)nc * K,
+                         kind_from_dev(beta), st));
+    RET(sync(st));
+  }
   return PDEP_OK;
 }
 

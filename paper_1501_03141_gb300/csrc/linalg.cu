@@ -236,12 +236,14 @@ __global__ void k_gershgorin(const double* __restrict__ M, long long ldm, int n,
   if (threadIdx.x == 0) {
     double m2 = 0.0;
     for (int w = 0; w < (int)((blockDim.x + 31) / 32); ++w) m2 = fmax(m2, sm[w]);
-    *out = m2 > 0.0 ? m2 * (1.0 + 1e-3) : 1.0;
+    // twice the Gershgorin bound: M - sigma I is negative definite with every
+    // |lambda_i - sigma| in [sigma/2, 3 sigma/2]
+    *out = m2 > 0.0 ? 2.0 * m2 * (1.0 + 1e-3) : 1.0;
   }
 }
 
 __global__ void k_jacobi_init(const double* __restrict__ M, long long ldm, int n,
-                              const double* __restrict__ sigma, double* A, double* V) {
+                              const double* __restrict__ sigma, double* A) {
   const long long tot = (long long)n * n;
   const double s = *sigma;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
@@ -249,44 +251,44 @@ __global__ void k_jacobi_init(const double* __restrict__ M, long long ldm, int n
     const int i = (int)(e % n), j = (int)(e / n);
     double m = 0.5 * (M[i + (long long)j * ldm] + M[j + (long long)i * ldm]);
     A[e] = (i == j) ? m - s : m;
-    V[e] = (i == j) ? 1.0 : 0.0;
   }
 }
 
-// One round of the cyclic (round-robin) ordering: warp w rotates the column
-// pair (p, q) of A so that A_p . A_q = 0 and applies the same rotation to V.
-// E > 0: the four columns (n <= 32 E) are loaded into registers up front, so a
-// round costs one memory round trip instead of one per 32 rows; E = 0 streams.
+// One round of the cyclic (round-robin) ordering, one CTA of two warps per
+// column pair (p, q): the pair is rotated so that A_p . A_q = 0.  V is not
+// carried: at convergence the columns of A = (M - sigma I) V are the
+// eigenvectors scaled by lambda_i - sigma, and with sigma twice the
+// Gershgorin bound every |lambda_i - sigma| lies in [sigma/2, 3 sigma/2]
+// (condition number at most 3), so normalising them gives V to working
+// accuracy.  E > 0: the
+// two columns (n <= 64 E) are held in registers, one memory round trip per
+// round; E = 0 streams them.
 template <int E>
-__global__ void k_jacobi_round(double* A, double* V, int n, int nn, int round,
-                               unsigned* counter) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (warp >= nn / 2) return;
+__global__ void __launch_bounds__(64) k_jacobi_pair(double* A, int n, int nn, int round,
+                                                    unsigned* counter) {
+  const int pair = blockIdx.x;
   int p, q;
-  if (warp == 0) {
+  if (pair == 0) {
     p = nn - 1;
     q = round;
   } else {
-    p = (round + warp) % (nn - 1);
-    q = (round - warp + (nn - 1)) % (nn - 1);
+    p = (round + pair) % (nn - 1);
+    q = (round - pair + (nn - 1)) % (nn - 1);
   }
   if (p >= n || q >= n) return;
   double* ap = A + (long long)p * n;
   double* aq = A + (long long)q * n;
-  double* vp = V + (long long)p * n;
-  double* vq = V + (long long)q * n;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  __shared__ double red[2][3];
   double al = 0.0, be = 0.0, ga = 0.0;
+  double x[E > 0 ? E : 1], y[E > 0 ? E : 1];
   if constexpr (E > 0) {
-    double x[E], y[E], u[E], w[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-      const int r = lane + 32 * e;
+      const int r = t + 64 * e;
       const bool in = r < n;
       x[e] = in ? ap[r] : 0.0;
       y[e] = in ? aq[r] : 0.0;
-      u[e] = in ? vp[r] : 0.0;
-      w[e] = in ? vq[r] : 0.0;
     }
 #pragma unroll
     for (int e = 0; e < E; ++e) {
@@ -294,59 +296,71 @@ __global__ void k_jacobi_round(double* A, double* V, int n, int nn, int round,
       be += y[e] * y[e];
       ga += x[e] * y[e];
     }
-    al = warp_sum(al);
-    be = warp_sum(be);
-    ga = warp_sum(ga);
-    if (ga == 0.0 || fabs(ga) <= 1e-14 * sqrt(al * be)) return;
-    const double zeta = (be - al) / (2.0 * ga);
-    const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-    const double c = 1.0 / sqrt(1.0 + tt * tt);
-    const double s = c * tt;
+  } else {
+    for (int r = t; r < n; r += 64) {
+      const double u = ap[r], w = aq[r];
+      al += u * u;
+      be += w * w;
+      ga += u * w;
+    }
+  }
+  al = warp_sum(al);
+  be = warp_sum(be);
+  ga = warp_sum(ga);
+  if (lane == 0) {
+    red[warp][0] = al;
+    red[warp][1] = be;
+    red[warp][2] = ga;
+  }
+  __syncthreads();
+  al = red[0][0] + red[1][0];
+  be = red[0][1] + red[1][1];
+  ga = red[0][2] + red[1][2];
+  // every thread holds the same sums, so this exit is uniform
+  if (ga == 0.0 || ga * ga <= 1e-28 * (al * be)) return;
+  const double zeta = (be - al) / (2.0 * ga);
+  const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  const double c = rsqrt(1.0 + tt * tt);
+  const double s = c * tt;
+  if constexpr (E > 0) {
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-      const int r = lane + 32 * e;
+      const int r = t + 64 * e;
       if (r < n) {
         ap[r] = c * x[e] - s * y[e];
         aq[r] = s * x[e] + c * y[e];
-        vp[r] = c * u[e] - s * w[e];
-        vq[r] = s * u[e] + c * w[e];
       }
     }
   } else {
-    for (int r = lane; r < n; r += 32) {
-      const double x = ap[r], y = aq[r];
-      al += x * x;
-      be += y * y;
-      ga += x * y;
-    }
-    al = warp_sum(al);
-    be = warp_sum(be);
-    ga = warp_sum(ga);
-    if (ga == 0.0 || fabs(ga) <= 1e-14 * sqrt(al * be)) return;
-    const double zeta = (be - al) / (2.0 * ga);
-    const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-    const double c = 1.0 / sqrt(1.0 + tt * tt);
-    const double s = c * tt;
-    for (int r = lane; r < n; r += 32) {
-      const double x = ap[r], y = aq[r];
-      ap[r] = c * x - s * y;
-      aq[r] = s * x + c * y;
-    }
-    for (int r = lane; r < n; r += 32) {
-      const double x = vp[r], y = vq[r];
-      vp[r] = c * x - s * y;
-      vq[r] = s * x + c * y;
+    for (int r = t; r < n; r += 64) {
+      const double u = ap[r], w = aq[r];
+      ap[r] = c * u - s * w;
+      aq[r] = s * u + c * w;
     }
   }
-  if (lane == 0) atomicAdd(counter, 1u);
+  if (t == 0) atomicAdd(counter, 1u);
 }
 
-using JacobiRound = void (*)(double*, double*, int, int, int, unsigned*);
+using JacobiRound = void (*)(double*, int, int, int, unsigned*);
 static JacobiRound jacobi_round_for(int n) {
-  if (n <= 128) return k_jacobi_round<4>;
-  if (n <= 256) return k_jacobi_round<8>;
-  if (n <= 512) return k_jacobi_round<16>;
-  return k_jacobi_round<0>;
+  if (n <= 128) return k_jacobi_pair<2>;
+  if (n <= 256) return k_jacobi_pair<4>;
+  if (n <= 512) return k_jacobi_pair<8>;
+  return k_jacobi_pair<0>;
+}
+
+// V_i = -A_i / ||A_i|| (one block per column)
+__global__ void k_jacobi_vectors(const double* __restrict__ A, int n, double* V) {
+  const int c = blockIdx.x;
+  double ss = 0.0;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    const double a = A[r + (long long)c * n];
+    ss += a * a;
+  }
+  const double2 t = block_sum2(ss, 0.0);
+  const double f = t.x > 0.0 ? -rsqrt(t.x) : 0.0;
+  for (int r = threadIdx.x; r < n; r += blockDim.x)
+    V[r + (long long)c * n] = f * A[r + (long long)c * n];
 }
 
 // w_i = v_i . (M v_i)
@@ -392,11 +406,10 @@ cudaError_t eigh(int n, const double* M, long long ldm, double* W, double* V, lo
   const long long tot = (long long)n * n;
   const int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
   count_launch();
-  k_jacobi_init<<<blocks, 256, 0, st>>>(M, ldm, n, sigma, wk.a, wk.v);
+  k_jacobi_init<<<blocks, 256, 0, st>>>(M, ldm, n, sigma, wk.a);
   const int nn = n + (n & 1);
-  const int warps = nn / 2;
-  const int tpb = 128;
-  const int jb = (warps * 32 + tpb - 1) / tpb;
+  const int jb = nn / 2;  // one CTA per column pair
+  const int tpb = 64;
   const JacobiRound round_k = jacobi_round_for(n);
   // One sweep = nn - 1 dependent rounds; they are replayed from a CUDA graph
   // captured once per (size, buffers) to avoid nn - 1 stream launches.
@@ -417,7 +430,7 @@ cudaError_t eigh(int n, const double* M, long long ldm, double* W, double* V, lo
       cudaGraph_t g;
       e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
       if (e != cudaSuccess) return e;
-      for (int r = 0; r < nn - 1; ++r) round_k<<<jb, tpb, 0, cap>>>(wk.a, wk.v, n, nn, r, counter);
+      for (int r = 0; r < nn - 1; ++r) round_k<<<jb, tpb, 0, cap>>>(wk.a, n, nn, r, counter);
       e = cudaStreamEndCapture(cap, &g);
       if (e != cudaSuccess) return e;
       e = cudaGraphInstantiate(&sweep, g, 0);
@@ -438,7 +451,7 @@ cudaError_t eigh(int n, const double* M, long long ldm, double* W, double* V, lo
     } else {
       for (int r = 0; r < nn - 1; ++r) {
         count_launch();
-        round_k<<<jb, tpb, 0, st>>>(wk.a, wk.v, n, nn, r, counter);
+        round_k<<<jb, tpb, 0, st>>>(wk.a, n, nn, r, counter);
       }
     }
     if (nn - 1 == 0) break;
@@ -447,6 +460,7 @@ cudaError_t eigh(int n, const double* M, long long ldm, double* W, double* V, lo
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return e;
   }
+  { count_launch(); k_jacobi_vectors<<<n, 128, 0, st>>>(wk.a, n, wk.v); }
   // Rayleigh quotients with the original (symmetrised) matrix
   cudaError_t e = gemm<double>(false, n, n, n, 1.0, M, ldm, wk.v, n, 0.0, wk.tmp, n, st);
   if (e != cudaSuccess) return e;
@@ -733,6 +747,299 @@ cudaError_t scale_sqrt_coulomb(double* X, long long ld, int n_half, int n, const
     count_launch();
     k_sqrt_coulomb<<<dim3(bx, nj), 256, 0, st>>>(X + (long long)j0 * ld, ld, n_half, nj, g2);
   }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Lanczos chains of the deflated Hamiltonian (Sec. II D), one block per chain
+// ---------------------------------------------------------------------------
+// q_0 = r / ||r||, beta[j][0] = ||r|| (r already projected with P_c); a
+// start vector whose projection is at or below 1e-12 of its norm before the
+// projection (r0norm) gives an empty chain
+__global__ void k_lanczos_start(const double* __restrict__ R, long long ld, int n_pw, int K,
+                                const double* __restrict__ r0norm, double* Q0, double* beta) {
+  const int j = blockIdx.x;
+  const double* r = R + (long long)j * ld;
+  double ss = 0.0;
+  for (int i = threadIdx.x; i < n_pw; i += blockDim.x) ss += r[i] * r[i];
+  double b = sqrt(block_sum2(ss, 0.0).x);
+  if (!(b > 1e-12 * r0norm[j])) b = 0.0;
+  const double f = b > 0.0 ? 1.0 / b : 0.0;
+  double* q = Q0 + (long long)j * ld;
+  for (int i = threadIdx.x; i < n_pw; i += blockDim.x) q[i] = f * r[i];
+  if (threadIdx.x == 0) beta[(long long)j * K] = b;
+}
+cudaError_t lanczos_start(const double* R, long long ld, int n_pw, int n, int K,
+                          const double* r0norm, double* Q0, double* beta, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  { count_launch(); k_lanczos_start<<<n, 256, 0, st>>>(R, ld, n_pw, K, r0norm, Q0, beta); }
+  return cudaGetLastError();
+}
+
+// Step k of every chain: W = H~ q_k on entry.  alpha_k = q_k . W,
+// r = W - alpha_k q_k - beta_k q_{k-1}; unless k is the last step,
+// beta_{k+1} = ||r|| and q_{k+1} = r / beta_{k+1}, or 0 and 0 when
+// ||r|| <= 1e-12 ||W|| (an invariant subspace: the chain stops there).
+__global__ void k_lanczos_step(const double* __restrict__ W, const double* __restrict__ Qk,
+                               const double* __restrict__ Qkm1, double* Qk1, long long ld,
+                               int n_pw, int K, int k, double* alpha, double* beta) {
+  const int j = blockIdx.x;
+  const long long o = (long long)j * ld;
+  double aw = 0.0, ww = 0.0;
+  for (int i = threadIdx.x; i < n_pw; i += blockDim.x) {
+    const double w = W[o + i];
+    aw += Qk[o + i] * w;
+    ww += w * w;
+  }
+  const double2 t = block_sum2(aw, ww);
+  const double a = t.x, hn = sqrt(t.y);
+  const double bk = k > 0 ? beta[(long long)j * K + k] : 0.0;
+  if (threadIdx.x == 0) alpha[(long long)j * K + k] = a;
+  if (k + 1 >= K) return;
+  double rr = 0.0;
+  for (int i = threadIdx.x; i < n_pw; i += blockDim.x) {
+    double r = W[o + i] - a * Qk[o + i];
+    if (k > 0) r -= bk * Qkm1[o + i];
+    Qk1[o + i] = r;
+    rr += r * r;
+  }
+  const double b = sqrt(block_sum2(rr, 0.0).x);
+  const bool stop = !(b > 1e-12 * hn);
+  const double f = stop ? 0.0 : 1.0 / b;
+  for (int i = threadIdx.x; i < n_pw; i += blockDim.x) Qk1[o + i] *= f;
+  if (threadIdx.x == 0) beta[(long long)j * K + k + 1] = stop ? 0.0 : b;
+}
+cudaError_t lanczos_step(const double* W, const double* Qk, const double* Qkm1, double* Qk1,
+                         long long ld, int n_pw, int n, int K, int k, double* alpha, double* beta,
+                         cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  {
+    count_launch();
+    k_lanczos_step<<<n, 256, 0, st>>>(W, Qk, Qkm1, Qk1, ld, n_pw, K, k, alpha, beta);
+  }
+  return cudaGetLastError();
+}
+
+// Eigen-decomposition of each chain's tridiagonal T (K <= 64) by parallel
+// cyclic two-sided Jacobi in shared memory (Golub & Van Loan, Sec. 8.5):
+// every round rotates K/2 disjoint (p, q) planes, J = [[c, s], [-s, c]] with
+// t = s/c the smaller root of t^2 + 2 tau t - 1 = 0, tau = (a_qq - a_pp)/(2 a_pq).
+// Output: d [n][K] ascending and U [n][K][K] (U[j][m][k]: component m of
+// eigenvector k).  Sweeps stop when the off-diagonal Frobenius norm is at or
+// below 1e-15 of the whole or after 40 sweeps.
+constexpr int kLzMax = 64;
+__global__ void __launch_bounds__(256) k_tridiag_eig(const double* __restrict__ alpha,
+                                                     const double* __restrict__ beta, int K,
+                                                     double* d, double* U) {
+  extern __shared__ __align__(16) double lz_sh[];
+  const int ldk = K + 1;  // odd row stride
+  double* Tm = lz_sh;
+  double* Vm = lz_sh + K * ldk;
+#define T(r, c) Tm[(r) * ldk + (c)]
+#define V(r, c) Vm[(r) * ldk + (c)]
+  __shared__ double cs[kLzMax / 2], sn[kLzMax / 2];
+  __shared__ int pp[kLzMax / 2], qq[kLzMax / 2];
+  __shared__ double dd[kLzMax];
+  const int j = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const double* a = alpha + (long long)j * K;
+  const double* b = beta + (long long)j * K;
+  for (int e = tid; e < K * K; e += nt) {
+    const int r = e / K, c = e % K;
+    T(r, c) = r == c ? a[r] : (c == r + 1 ? b[c] : (r == c + 1 ? b[r] : 0.0));
+    V(r, c) = r == c ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  const int nn = K + (K & 1);
+  const int np = nn / 2;
+  for (int sweep = 0; sweep < 40 && K > 1; ++sweep) {
+    double off = 0.0, all = 0.0;
+    for (int e = tid; e < K * K; e += nt) {
+      const int r = e / K, c = e % K;
+      const double v = T(r, c) * T(r, c);
+      all += v;
+      if (r != c) off += v;
+    }
+    const double2 o = block_sum2(off, all);
+    if (!(o.x > 1e-30 * o.y)) break;
+    for (int round = 0; round < nn - 1; ++round) {
+      if (tid < np) {
+        int p, q;
+        if (tid == 0) {
+          p = nn - 1;
+          q = round;
+        } else {
+          p = (round + tid) % (nn - 1);
+          q = (round - tid + (nn - 1)) % (nn - 1);
+        }
+        if (p > q) {
+          const int x = p;
+          p = q;
+          q = x;
+        }
+        double c = 1.0, s = 0.0;
+        if (q < K) {
+          const double apq = T(p, q);
+          if (apq != 0.0) {
+            const double tau = (T(q, q) - T(p, p)) / (2.0 * apq);
+            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = rsqrt(1.0 + t * t);
+            s = t * c;
+          }
+        }
+        pp[tid] = p;
+        qq[tid] = q;
+        cs[tid] = c;
+        sn[tid] = s;
+      }
+      __syncthreads();
+      // rows: T <- J^T T
+      for (int e = tid; e < np * K; e += nt) {
+        const int w = e / K, col = e % K;
+        const int p = pp[w], q = qq[w];
+        if (q >= K) continue;
+        const double c = cs[w], s = sn[w];
+        const double tp = T(p, col), tq = T(q, col);
+        T(p, col) = c * tp - s * tq;
+        T(q, col) = s * tp + c * tq;
+      }
+      __syncthreads();
+      // columns: T <- T J, V <- V J
+      for (int e = tid; e < np * K; e += nt) {
+        const int w = e / K, row = e % K;
+        const int p = pp[w], q = qq[w];
+        if (q >= K) continue;
+        const double c = cs[w], s = sn[w];
+        const double tp = T(row, p), tq = T(row, q);
+        T(row, p) = c * tp - s * tq;
+        T(row, q) = s * tp + c * tq;
+        const double vp = V(row, p), vq = V(row, q);
+        V(row, p) = c * vp - s * vq;
+        V(row, q) = s * vp + c * vq;
+      }
+      __syncthreads();
+    }
+  }
+  for (int k = tid; k < K; k += nt) dd[k] = T(k, k);
+  __syncthreads();
+  // ascending order (ties by index)
+  for (int k = tid; k < K; k += nt) {
+    int rank = 0;
+    for (int m = 0; m < K; ++m) rank += (dd[m] < dd[k] || (dd[m] == dd[k] && m < k)) ? 1 : 0;
+    d[(long long)j * K + rank] = dd[k];
+    for (int m = 0; m < K; ++m) U[((long long)j * K + m) * K + rank] = V(m, k);
+  }
+}
+#undef T
+#undef V
+
+cudaError_t tridiag_eig(const double* alpha, const double* beta, int n, int K, double* d,
+                        double* U, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (K < 1 || K > kLzMax) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(double) * 2 * K * (K + 1);
+  cudaError_t e = cudaFuncSetAttribute(k_tridiag_eig, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(double) * 2 * kLzMax * (kLzMax + 1)));
+  if (e != cudaSuccess) return e;
+  { count_launch(); k_tridiag_eig<<<n, 256, smem, st>>>(alpha, beta, K, d, U); }
+  return cudaGetLastError();
+}
+
+// weights[c][l][k] = beta[c][0] sum_m G[l][m n + j] U[c][m][k] U[c][0][k] for
+// the chains c = j cs + c0, j < n; G[l][m n + j] = <L_l | q_m of chain c>
+// (column-major n_L x (K n))
+__global__ void k_lanczos_weights(const double* __restrict__ G, int n_L, int n, int K,
+                                  const double* __restrict__ U, const double* __restrict__ beta,
+                                  double* weights, int cs, int c0) {
+  const int j = blockIdx.x;
+  const long long ch = (long long)j * cs + c0;
+  const double b0 = beta[ch * K];
+  const double* u = U + ch * K * K;
+  for (int e = threadIdx.x; e < n_L * K; e += blockDim.x) {
+    const int l = e / K, k = e % K;
+    double acc = 0.0;
+    for (int m = 0; m < K; ++m) acc += G[l + ((long long)m * n + j) * n_L] * u[m * K + k];
+    weights[(ch * n_L + l) * K + k] = b0 * acc * u[k];
+  }
+}
+cudaError_t lanczos_weights(const double* G, int n_L, int n, int K, const double* U,
+                            const double* beta, double* weights, int cs, int c0,
+                            cudaStream_t st) {
+  if (n <= 0 || n_L <= 0) return cudaSuccess;
+  {
+    count_launch();
+    k_lanczos_weights<<<n, 128, 0, st>>>(G, n_L, n, K, U, beta, weights, cs, c0);
+  }
+  return cudaGetLastError();
+}
+
+// z[f][j][k] = beta[c][0] sum_k2 U[c][k][k2] U[c][0][k2] g(eps_v - d[c][k2], nu_f),
+// g(D, nu) = D / (D^2 + nu^2), for the chains c = j cs + c0, j < n: the
+// resolvent sum of Eq. finalB at the two frequencies eps_v -+ i nu, in the
+// chain basis q_k
+__global__ void k_lanczos_z(const double* __restrict__ U, const double* __restrict__ d,
+                            const double* __restrict__ beta, int n, int K, int cs, int c0,
+                            double eps_v, const double* __restrict__ nu, int n_freq, double* z) {
+  const int j = blockIdx.x, f = blockIdx.y;
+  const long long ch = (long long)j * cs + c0;
+  const double b0 = beta[ch * K];
+  const double* u = U + ch * K * K;
+  const double* dd = d + ch * K;
+  const double v2 = nu[f] * nu[f];
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    double acc = 0.0;
+    for (int k2 = 0; k2 < K; ++k2) {
+      const double D = eps_v - dd[k2];
+      const double den = D * D + v2;
+      acc += u[k * K + k2] * u[k2] * (den > 0.0 ? D / den : 0.0);
+    }
+    z[((long long)f * n + j) * K + k] = b0 * acc;
+  }
+}
+cudaError_t lanczos_z(const double* U, const double* d, const double* beta, int n, int K, int cs,
+                      int c0, double eps_v, const double* nu, int n_freq, double* z,
+                      cudaStream_t st) {
+  if (n <= 0 || n_freq <= 0) return cudaSuccess;
+  {
+    count_launch();
+    k_lanczos_z<<<dim3(n, n_freq), 64, 0, st>>>(U, d, beta, n, K, cs, c0, eps_v, nu, n_freq, z);
+  }
+  return cudaGetLastError();
+}
+
+// B[f] (n_L x n, column-major) += scale sum_k G[l][k n + j] z[f][j][k]
+__global__ void k_body_accum(const double* __restrict__ G, int n_L, int n, int K,
+                             const double* __restrict__ z, double scale, double* B) {
+  const int j = blockIdx.x, f = blockIdx.y;
+  const double* zz = z + ((long long)f * n + j) * K;
+  double* b = B + (long long)f * n_L * n + (long long)j * n_L;
+  for (int l = threadIdx.x; l < n_L; l += blockDim.x) {
+    double acc = 0.0;
+    for (int k = 0; k < K; ++k) acc += G[l + ((long long)k * n + j) * n_L] * zz[k];
+    b[l] += scale * acc;
+  }
+}
+cudaError_t body_accum(const double* G, int n_L, int n, int K, const double* z, int n_freq,
+                       double scale, double* B, cudaStream_t st) {
+  if (n <= 0 || n_freq <= 0) return cudaSuccess;
+  { count_launch(); k_body_accum<<<dim3(n, n_freq), 128, 0, st>>>(G, n_L, n, K, z, scale, B); }
+  return cudaGetLastError();
+}
+
+// Lambda = V diag(w / (1 - w)) V^T (n x n, column-major): the RPA body
+// (1 - B)^{-1} B from the eigen-decomposition B = V diag(w) V^T
+__global__ void k_lambda_from_eig(const double* __restrict__ V, const double* __restrict__ w,
+                                  int n, double* L) {
+  const int j = blockIdx.x;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double acc = 0.0;
+    for (int k = 0; k < n; ++k)
+      acc += V[i + (long long)k * n] * (w[k] / (1.0 - w[k])) * V[j + (long long)k * n];
+    L[i + (long long)j * n] = acc;
+  }
+}
+cudaError_t lambda_from_eig(const double* V, const double* w, int n, double* L, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  { count_launch(); k_lambda_from_eig<<<n, 128, 0, st>>>(V, w, n, L); }
   return cudaGetLastError();
 }
 

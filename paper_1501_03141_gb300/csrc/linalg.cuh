@@ -17,9 +17,11 @@ cudaError_t gemm(bool transA, int m, int n, int k, double alpha, const R* A, lon
                  const int* bmap = nullptr, const int* cmap = nullptr);
 
 // Symmetric eigendecomposition of the n x n matrix M (lda), FP64:
-// one-sided (Hestenes) Jacobi on M - sigma I (sigma = Gershgorin bound, so
-// the shifted matrix is negative definite), Rayleigh quotients with the
-// original M, ascending sort.  W [n] eigenvalues, V [n x n] (ldv) vectors.
+// one-sided (Hestenes) Jacobi on M - sigma I (sigma = twice the Gershgorin
+// bound, so the shifted matrix is negative definite and well conditioned);
+// the eigenvectors are the normalised columns of the converged (M - sigma I) V,
+// the eigenvalues their Rayleigh quotients with the original M, sorted
+// ascending.  W [n] eigenvalues, V [n x n] (ldv) vectors.
 // Work needs 2 n*n + 4 n doubles of device scratch.
 struct EighWork {
   double* a;      // n*n
@@ -49,6 +51,30 @@ cudaError_t philox_normal(double* X, long long ld, int rows, int cols, unsigned 
 // X[d][j] *= sqrt(4 pi)/|G| on the 2 n_half PDEP components of n columns
 cudaError_t scale_sqrt_coulomb(double* X, long long ld, int n_half, int n, const double* g2,
                                cudaStream_t st);
+// Lanczos chains (Sec. II D), Q_k blocks [n][ld], alpha/beta [n][K]:
+// q_0 = r/||r|| and beta[j][0] = ||r||; one three-term step per call; the
+// tridiagonal eigen-decompositions (K <= 64; d ascending, U[j][m][k]); the
+// omega-independent weights of Eq. MCfinal from G = L^T Q (n_L x (K n)) for
+// the chains j cs + c0, j < n.
+cudaError_t lanczos_start(const double* R, long long ld, int n_pw, int n, int K,
+                          const double* r0norm, double* Q0, double* beta, cudaStream_t st);
+cudaError_t lanczos_step(const double* W, const double* Qk, const double* Qkm1, double* Qk1,
+                         long long ld, int n_pw, int n, int K, int k, double* alpha, double* beta,
+                         cudaStream_t st);
+cudaError_t tridiag_eig(const double* alpha, const double* beta, int n, int K, double* d,
+                        double* U, cudaStream_t st);
+cudaError_t lanczos_weights(const double* G, int n_L, int n, int K, const double* U,
+                            const double* beta, double* weights, int cs, int c0,
+                            cudaStream_t st);
+// Body of chi0bar at imaginary frequencies from Lanczos chains (Eq. finalB):
+// per-chain resolvent vectors z [n_freq][n][K] for occupied energy eps_v,
+// their accumulation B[f] += scale G z, and Lambda = V diag(w/(1-w)) V^T.
+cudaError_t lanczos_z(const double* U, const double* d, const double* beta, int n, int K, int cs,
+                      int c0, double eps_v, const double* nu, int n_freq, double* z,
+                      cudaStream_t st);
+cudaError_t body_accum(const double* G, int n_L, int n, int K, const double* z, int n_freq,
+                       double scale, double* B, cudaStream_t st);
+cudaError_t lambda_from_eig(const double* V, const double* w, int n, double* L, cudaStream_t st);
 // W = L^{-T} for the Cholesky factor of the m x m Gram matrix G (m <= 128);
 // *fail = 1 (device) when a pivot is at or below rel_thr * max_i G_ii.
 cudaError_t cholesky_winv(const double* G, int m, double rel_thr, double* W, int* fail,

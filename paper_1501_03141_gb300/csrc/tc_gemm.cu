@@ -12,6 +12,7 @@
 // product would perturb the CG operator at the 1e-4 level).  Operand tiles
 // are staged in shared memory with cp.async; fragment layouts follow the
 // m16n8k8 .row.col TF32 shape of the PTX ISA.
+#include <algorithm>
 #include <cstdint>
 
 #include "linalg.cuh"
@@ -58,7 +59,8 @@ __device__ __forceinline__ void cp_wait() {
 }
 
 // ---------------------------------------------------------------------------
-// coefficients: S (M x N, lds) = diag(sigma) P^T X(:, bmap), K = rows of P, X
+// coefficients: S (M x N, lds) += diag(sigma) P^T X(:, bmap) over the K range
+// [blockIdx.z kchunk, +kchunk) (split K, FP32 atomics; S zeroed beforehand).
 // CTA tile 32 x 64, 4 warps each 32 x 16, K tile 32.
 // ---------------------------------------------------------------------------
 constexpr int C_BM = 32, C_BN = 64, C_BK = 32, C_PAD = 36;
@@ -66,12 +68,15 @@ constexpr int C_BM = 32, C_BN = 64, C_BK = 32, C_PAD = 36;
 __global__ void __launch_bounds__(128)
     k_tc_coeffs(int M, int N, int K, const float* __restrict__ P, long long ldp,
                 const float* __restrict__ X, long long ldx, const int* __restrict__ bmap,
-                const float* __restrict__ sigma, float* __restrict__ S, long long lds) {
+                const float* __restrict__ sigma, float* __restrict__ S, long long lds,
+                int kchunk) {
   __shared__ __align__(16) float As[2][C_BM][C_PAD];
   __shared__ __align__(16) float Bs[2][C_BN][C_PAD];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, t = lane & 3;
   const int row0 = blockIdx.x * C_BM, col0 = blockIdx.y * C_BN;
+  const int kbeg = blockIdx.z * kchunk;
+  const int kend = min(K, kbeg + kchunk);
 
   auto load = [&](int stage, int k0) {
     // A: 32 rows x 8 chunks of 4 floats
@@ -82,8 +87,8 @@ __global__ void __launch_bounds__(128)
       const int gr = row0 + r, gk = k0 + kc;
       int bytes = 0;
       const float* src = P;
-      if (gr < M && gk < K) {
-        bytes = 4 * min(4, K - gk);
+      if (gr < M && gk < kend) {
+        bytes = 4 * min(4, kend - gk);
         src = P + (long long)gr * ldp + gk;
       }
       cp16(&As[stage][r][kc], src, bytes);
@@ -96,8 +101,8 @@ __global__ void __launch_bounds__(128)
       const int gj = col0 + j, gk = k0 + kc;
       int bytes = 0;
       const float* src = X;
-      if (gj < N && gk < K) {
-        bytes = 4 * min(4, K - gk);
+      if (gj < N && gk < kend) {
+        bytes = 4 * min(4, kend - gk);
         src = X + (long long)(bmap ? bmap[gj] : gj) * ldx + gk;
       }
       cp16(&Bs[stage][j][kc], src, bytes);
@@ -112,11 +117,11 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
       for (int e = 0; e < 4; ++e) acc[a][b][e] = 0.f;
 
-  const int nk = (K + C_BK - 1) / C_BK;
-  load(0, 0);
+  const int nk = kend > kbeg ? (kend - kbeg + C_BK - 1) / C_BK : 0;
+  if (nk > 0) load(0, kbeg);
   cp_commit();
   for (int kt = 0; kt < nk; ++kt) {
-    if (kt + 1 < nk) load((kt + 1) & 1, (kt + 1) * C_BK);
+    if (kt + 1 < nk) load((kt + 1) & 1, kbeg + (kt + 1) * C_BK);
     cp_commit();
     cp_wait<1>();
     __syncthreads();
@@ -170,7 +175,7 @@ __global__ void __launch_bounds__(128)
       for (int e = 0; e < 4; ++e) {
         const int r = row0 + mi * 16 + g + (e >= 2 ? 8 : 0);
         const int j = col0 + warp * 16 + ni * 8 + 2 * t + (e & 1);
-        if (r < M && j < N) S[r + (long long)j * lds] = sigma[r] * acc[mi][ni][e];
+        if (r < M && j < N && nk > 0) atomicAdd(S + r + (long long)j * lds, sigma[r] * acc[mi][ni][e]);
       }
 }
 
@@ -222,13 +227,19 @@ __global__ void __launch_bounds__(128)
     }
   };
 
+  // acc starts from Y: its loads overlap the K loop instead of stalling the
+  // epilogue
   float acc[2][4][4];
 #pragma unroll
-  for (int a = 0; a < 2; ++a)
+  for (int mi = 0; mi < 2; ++mi)
 #pragma unroll
-    for (int b = 0; b < 4; ++b)
+    for (int ni = 0; ni < 4; ++ni)
 #pragma unroll
-      for (int e = 0; e < 4; ++e) acc[a][b][e] = 0.f;
+      for (int e = 0; e < 4; ++e) {
+        const int r = row0 + wm * 32 + mi * 16 + g + (e >= 2 ? 8 : 0);
+        const int j = col0 + wn * 32 + ni * 8 + 2 * t + (e & 1);
+        acc[mi][ni][e] = (r < M && j < N) ? Y[r + (long long)(cmap ? cmap[j] : j) * ldy] : 0.f;
+      }
 
   const int nk = (K + U_BK - 1) / U_BK;
   load(0, 0);
@@ -284,10 +295,7 @@ __global__ void __launch_bounds__(128)
       for (int e = 0; e < 4; ++e) {
         const int r = row0 + wm * 32 + mi * 16 + g + (e >= 2 ? 8 : 0);
         const int j = col0 + wn * 32 + ni * 8 + 2 * t + (e & 1);
-        if (r < M && j < N) {
-          float* y = Y + r + (long long)(cmap ? cmap[j] : j) * ldy;
-          *y += acc[mi][ni][e];
-        }
+        if (r < M && j < N) Y[r + (long long)(cmap ? cmap[j] : j) * ldy] = acc[mi][ni][e];
       }
 }
 
@@ -299,10 +307,22 @@ cudaError_t tc_proj_coeffs(int M, int N, int K, const float* P, long long ldp, c
   if (M <= 0 || N <= 0) return cudaSuccess;
   dim3 grid((M + C_BM - 1) / C_BM, (N + C_BN - 1) / C_BN);
   if (grid.y > 65535) return cudaErrorInvalidValue;
+  // split K so that about four CTAs per SM stream X
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long tiles = (long long)grid.x * grid.y;
+  int split = (int)std::max<long long>(1, (4LL * std::max(sms, 1) + tiles - 1) / tiles);
+  split = std::min(split, std::max(1, K / (8 * C_BK)));
+  int kchunk = (K + split - 1) / split;
+  kchunk = ((kchunk + C_BK - 1) / C_BK) * C_BK;
+  grid.z = (unsigned)((K + kchunk - 1) / kchunk);
+  cudaError_t e = cudaMemsetAsync(S, 0, sizeof(float) * (size_t)lds * N, st);
+  if (e != cudaSuccess) return e;
   ProfScope ps(PC_GEMM_TF32, st, 2.0 * M * N * (double)K,
                ((double)M * K + (double)K * N + (double)M * N) * sizeof(float));
   count_launch();
-  k_tc_coeffs<<<grid, 128, 0, st>>>(M, N, K, P, ldp, X, ldx, bmap, sigma, S, lds);
+  k_tc_coeffs<<<grid, 128, 0, st>>>(M, N, K, P, ldp, X, ldx, bmap, sigma, S, lds, kchunk);
   return cudaGetLastError();
 }
 

@@ -1,4 +1,6 @@
 // Plane-wave sphere <-> grid transforms (see transforms.cuh for the scheme).
+#include <atomic>
+
 #include "fft.cuh"
 #include "transforms.cuh"
 #include "profile.cuh"
@@ -463,11 +465,11 @@ static cudaError_t slab_impl(const SphereDev<R>& s, const SlabArgs<R>& a, cudaSt
   if (nt > SlabThreads<R, N2, N3>::v) return cudaErrorInvalidConfiguration;
   const size_t smem = slab_smem_bytes(s.n_col, s.R3, N2, sizeof(R));
   auto kern = k_slab<R, N2, N3>;
-  static bool attr_set = false;  // per instantiation; the limit is raised once
-  if (!attr_set) {
+  static std::atomic<bool> attr_set{false};  // per instantiation; raised once
+  if (!attr_set.load()) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    attr_set.store(true);
   }
   const int gx = a.n_items;
   if (gx == 0) return cudaSuccess;
