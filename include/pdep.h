@@ -163,6 +163,22 @@ int pdep_get_occupied(pdep_ctx* ctx, int sys, double* psi, double* eps, void* st
 int chi0_apply(pdep_ctx* ctx, int sys, const double* phi, int n_pert, double* chi0_phi,
                double* dn_r, void* stream);
 
+/* chibar applied to n PDEP vectors with the Hartree-only self-consistent
+ * response (Sec. II C, Eqs. LF and LFHartree; no exchange-correlation
+ * kernel): the perturbation of Eq. stern becomes dV_tot = v^{1/2} phi +
+ * v dn[dV_tot].  Writing dV_tot = v^{1/2} y gives (1 - chi0bar) y = phi,
+ * which is solved by conjugate gradients (1 - chi0bar is SPD: chi0bar is
+ * negative semi-definite), each iteration applying chi0bar to the n
+ * directions as one batch of Sternheimer solves; then
+ *     out = chibar phi = y - phi = (1 - chi0bar)^{-1} chi0bar phi
+ * (Eq. linearalgebrachichi0).  phi, out [n][n_pdep_dim].  Stops when every
+ * ||phi - (1 - chi0bar) y|| <= tol ||phi|| or after max_iter iterations
+ * (*iterations, may be NULL, receives the count); PDEP_ERR_NOT_CONVERGED
+ * then, with out written.  The accuracy is bounded by that of the chi0bar
+ * applications (the Sternheimer tolerance cg_tol). */
+int pdep_chibar_apply(pdep_ctx* ctx, int sys, const double* phi, int n, double* out, double tol,
+                      int max_iter, int* iterations, void* stream);
+
 /* Sternheimer solves (Eq. stern) for n_pert perturbing potentials dv_r
  * [n_pert][n_r] (Ha) against every occupied state: dpsi [n_pert][n_occ][n_pw]
  * receives P_c dpsi_v; iters and resid [n_pert*n_occ] (may be NULL) receive

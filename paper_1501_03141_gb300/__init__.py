@@ -231,3 +231,15 @@ class Context:
                                             int(nu.shape[0]), int(n_steps), _abi.ptr(B),
                                             _abi.ptr(L), _stream(self.stream)), "pdep_chi0_imag")
         return B, L
+
+    def chibar_apply(self, phi, tol=1e-9, max_iter=200, sys: int = 0, out=None):
+        """chibar phi with the Hartree-only self-consistent response, by CG on
+        (1 - chi0bar) y = phi (Sec. II C); returns (chibar phi, CG iterations)."""
+        if out is None:
+            out = np.empty_like(phi) if isinstance(phi, np.ndarray) else phi.new_empty(phi.shape)
+        it = ctypes.c_int(0)
+        _abi.check(self._lib.pdep_chibar_apply(self._h, sys, _abi.ptr(phi), int(phi.shape[0]),
+                                               _abi.ptr(out), float(tol), int(max_iter),
+                                               ctypes.byref(it), _stream(self.stream)),
+                   "pdep_chibar_apply")
+        return out, it.value

@@ -37,6 +37,7 @@ EXPORTS = (
     "chi0_apply", "sternheimer_solve", "pdep_solve", "pdep_apply_hamiltonian", "pdep_to_grid",
     "pdep_profile", "pdep_destroy", "pdep_status_string", "pdep_last_error",
     "pdep_apply_hamiltonian_noalloc", "pdep_screening_apply", "pdep_lanczos", "pdep_chi0_imag",
+    "pdep_chibar_apply",
 )
 
 PDEP_PROFILE_CLASSES = 11
@@ -135,6 +136,7 @@ def load(path: str = LIB_PATH):
     lib.pdep_screening_apply.argtypes = [vp, ip, ip, vp, vp, ip, vp, ip, vp, vp]
     lib.pdep_lanczos.argtypes = [vp, ip, vp, ip, ip, vp, ip, vp, vp, vp, vp, vp]
     lib.pdep_chi0_imag.argtypes = [vp, ip, vp, ip, vp, ip, ip, vp, vp, vp]
+    lib.pdep_chibar_apply.argtypes = [vp, ip, vp, ip, vp, dp, ip, ctypes.POINTER(ip), vp]
     lib.pdep_apply_hamiltonian_noalloc.argtypes = [vp, ip, vp, ip, vp, vp]
     lib.pdep_apply_hamiltonian_noalloc.restype = ip
     lib.pdep_profile.argtypes = [ip, ctypes.POINTER(pdep_profile_t)]
@@ -147,7 +149,8 @@ def load(path: str = LIB_PATH):
     lib.pdep_last_error.restype = ctypes.c_char_p
     for name in ("pdep_setup", "pdep_get_sizes", "pdep_get_occupied", "chi0_apply",
                  "sternheimer_solve", "pdep_solve", "pdep_apply_hamiltonian", "pdep_to_grid",
-                 "pdep_screening_apply", "pdep_lanczos", "pdep_chi0_imag"):
+                 "pdep_screening_apply", "pdep_lanczos", "pdep_chi0_imag",
+                 "pdep_chibar_apply"):
         getattr(lib, name).restype = ip
     del dp
     _lib = lib

@@ -1711,6 +1711,98 @@ int pdep_lanczos(pdep_ctx* c, int sys, const double* R, int n, int n_steps, cons
   return PDEP_OK;
 }
 
+// chibar phi with the Hartree-only self-consistent perturbation (Sec. II C,
+// Eqs. LF and LFHartree): dV_tot = v^{1/2} phi + v dn[dV_tot].  With
+// dV_tot = v^{1/2} y this is (1 - chi0bar) y = phi, an SPD system solved by
+// CG whose every operator application is a chi0bar application (a batch of
+// Sternheimer solves); then chibar phi = v^{1/2} dn[dV_tot] = y - phi, the
+// (1 - chi0bar)^{-1} chi0bar phi of Eq. linearalgebrachichi0.
+int pdep_chibar_apply(pdep_ctx* c, int sys, const double* phi, int n, double* out, double tol,
+                      int max_iter, int* iterations, void* stream) {
+  RET(check_sys(c, sys));
+  if (n < 0 || max_iter < 1 || !(tol > 0) || (n > 0 && (!phi || !out)))
+    return fail(PDEP_ERR_INVALID_ARG, "bad pdep_chibar_apply arguments");
+  if (iterations) *iterations = 0;
+  if (n == 0) return PDEP_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  SysData& s = c->sys[sys];
+  reset_stats(c);
+  const int dim = s.n_pw - 1;
+  double *y, *r, *p, *q, *d_al, *d_be, *dots;
+  RET(ws(c, "hx_y", (size_t)n * s.ld, &y));
+  RET(ws(c, "hx_r", (size_t)n * s.ld, &r));
+  RET(ws(c, "hx_p", (size_t)n * s.ld, &p));
+  RET(ws(c, "hx_q", (size_t)n * s.ld, &q));
+  RET(ws(c, "hx_al", (size_t)n, &d_al));
+  RET(ws(c, "hx_be", (size_t)n, &d_be));
+  RET(ws(c, "hx_dots", (size_t)n, &dots));
+  // y = 0, r = p = phi
+  CK(cudaMemsetAsync(y, 0, sizeof(double) * (size_t)n * s.ld, st));
+  CK(cudaMemsetAsync(r, 0, sizeof(double) * (size_t)n * s.ld, st));
+  CK(cudaMemcpy2DAsync(r, s.ld * sizeof(double), phi, dim * sizeof(double), dim * sizeof(double),
+                       n, kind_to_dev(phi), st));
+  CK(cudaMemcpyAsync(p, r, sizeof(double) * (size_t)n * s.ld, cudaMemcpyDeviceToDevice, st));
+  std::vector<double> rr(n), r0(n), al(n), be(n), pq(n);
+  CK(pair_dots(r, r, s.ld, s.n_pw, n, dots, st));
+  CK(cudaMemcpyAsync(rr.data(), dots, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+  RET(sync(st));
+  std::vector<char> active(n);
+  int n_act = 0;
+  for (int j = 0; j < n; ++j) {
+    r0[j] = std::sqrt(rr[j]);
+    active[j] = rr[j] > 0.0;
+    n_act += active[j];
+  }
+  int it = 0;
+  for (; it < max_iter && n_act > 0; ++it) {
+    // q = (1 - chi0bar) p
+    int rc = chi0_internal(c, s, p, n, q, nullptr, st);
+    if (rc != PDEP_OK && rc != PDEP_ERR_NOT_CONVERGED) return rc;
+    CK(one_minus(q, p, s.ld, s.n_pw, n, st));
+    CK(pair_dots(p, q, s.ld, s.n_pw, n, dots, st));
+    CK(cudaMemcpyAsync(pq.data(), dots, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    RET(sync(st));
+    for (int j = 0; j < n; ++j) {
+      if (active[j] && !(pq[j] > 0.0)) return fail(PDEP_ERR_NONFINITE, "1 - chi0bar not positive");
+      al[j] = active[j] ? rr[j] / pq[j] : 0.0;
+    }
+    CK(cudaMemcpyAsync(d_al, al.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    CK(block_cg_xr(y, r, p, q, s.ld, s.n_pw, n, d_al, st));
+    CK(pair_dots(r, r, s.ld, s.n_pw, n, dots, st));
+    std::vector<double> rn(n);
+    CK(cudaMemcpyAsync(rn.data(), dots, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    RET(sync(st));
+    n_act = 0;
+    for (int j = 0; j < n; ++j) {
+      if (!active[j]) {
+        be[j] = 0.0;
+        continue;
+      }
+      if (!std::isfinite(rn[j])) return fail(PDEP_ERR_NONFINITE, "non-finite residual");
+      be[j] = rn[j] / rr[j];
+      rr[j] = rn[j];
+      if (std::sqrt(rn[j]) <= tol * r0[j]) {
+        active[j] = 0;
+        be[j] = 0.0;
+      }
+      n_act += active[j];
+    }
+    CK(cudaMemcpyAsync(d_be, be.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    CK(block_cg_p(p, r, s.ld, s.n_pw, n, d_be, st));
+  }
+  if (iterations) *iterations = it;
+  // chibar phi = y - phi: r = phi again, then out = y - r
+  CK(cudaMemsetAsync(r, 0, sizeof(double) * (size_t)n * s.ld, st));
+  CK(cudaMemcpy2DAsync(r, s.ld * sizeof(double), phi, dim * sizeof(double), dim * sizeof(double),
+                       n, kind_to_dev(phi), st));
+  CK(one_minus(r, y, s.ld, s.n_pw, n, st));
+  CK(cudaMemcpy2DAsync(out, dim * sizeof(double), r, s.ld * sizeof(double), dim * sizeof(double),
+                       n, kind_from_dev(out), st));
+  RET(sync(st));
+  if (n_act > 0) return fail(PDEP_ERR_NOT_CONVERGED, "self-consistent response: CG cap reached");
+  return PDEP_OK;
+}
+
 int sternheimer_solve(pdep_ctx* c, int sys, const double* dv_r, int n_pert, double* dpsi,
                       int* iters, double* resid, void* stream) {
   RET(check_sys(c, sys));

@@ -78,13 +78,17 @@ __device__ __forceinline__ double2 block_sum2_r(R a, R b) {
 // ---------------------------------------------------------------------------
 // GEMM (SIMT, register-tiled 64x64x16)
 // ---------------------------------------------------------------------------
-template <typename R, bool TA>
+// C tile of (16 TM) x 64 per CTA of 256 threads (16 x 16, each thread TM x 4
+// outputs), K tiles of 16 staged in shared memory.  TM = 5 gives 80-row tiles
+// for the 80-state projection coefficients (n_occ + n_deflate on the 48^3
+// workload), which 64-row tiles would cover with 37% padding.
+template <typename R, bool TA, int TM>
 __global__ void __launch_bounds__(256) k_gemm(int m, int n, int k, R alpha, const R* __restrict__ A,
                                               long long lda, const R* __restrict__ B, long long ldb,
                                               R beta, R* __restrict__ C, long long ldc, int kchunk,
                                               int atomic, const int* __restrict__ bmap,
                                               const int* __restrict__ cmap) {
-  constexpr int BM = 64, BN = 64, BK = 16;
+  constexpr int BM = 16 * TM, BN = 64, BK = 16;
   __shared__ R As[BK][BM + 1];
   __shared__ R Bs[BK][BN + 1];
   const int tid = threadIdx.x;
@@ -92,28 +96,25 @@ __global__ void __launch_bounds__(256) k_gemm(int m, int n, int k, R alpha, cons
   const int row0 = blockIdx.x * BM, col0 = blockIdx.y * BN;
   const int kbeg = blockIdx.z * kchunk;
   const int kend = min(k, kbeg + kchunk);
-  R acc[4][4];
+  R acc[TM][4];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < TM; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = R(0);
 
   for (int kb = kbeg; kb < kend; kb += BK) {
-    if (TA) {
-      const int i = tid >> 2, kk0 = (tid & 3) * 4;
-      const int gi = row0 + i;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int gk = kb + kk0 + q;
-        As[kk0 + q][i] = (gi < m && gk < kend) ? A[gk + (long long)gi * lda] : R(0);
-      }
-    } else {
-      const int kk = tid >> 4, i0 = (tid & 15) * 4;
-      const int gk = kb + kk;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int gi = row0 + i0 + q;
-        As[kk][i0 + q] = (gi < m && gk < kend) ? A[gi + (long long)gk * lda] : R(0);
+    for (int q = 0; q < TM; ++q) {
+      const int e = tid + 256 * q;
+      if (TA) {
+        // A is k x m: consecutive threads read consecutive k of one row
+        const int i = e >> 4, kk = e & 15;
+        const int gi = row0 + i, gk = kb + kk;
+        As[kk][i] = (gi < m && gk < kend) ? A[gk + (long long)gi * lda] : R(0);
+      } else {
+        const int i = e % BM, kk = e / BM;
+        const int gi = row0 + i, gk = kb + kk;
+        As[kk][i] = (gi < m && gk < kend) ? A[gi + (long long)gk * lda] : R(0);
       }
     }
     {
@@ -129,20 +130,20 @@ __global__ void __launch_bounds__(256) k_gemm(int m, int n, int k, R alpha, cons
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      R av[4], bv[4];
+      R av[TM], bv[4];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) av[a] = As[kk][tx + 16 * a];
+      for (int a = 0; a < TM; ++a) av[a] = As[kk][tx + 16 * a];
 #pragma unroll
       for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][ty + 16 * b];
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+      for (int a = 0; a < TM; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
+  for (int a = 0; a < TM; ++a) {
     const int gi = row0 + tx + 16 * a;
     if (gi >= m) continue;
 #pragma unroll
@@ -177,7 +178,10 @@ cudaError_t gemm(bool transA, int m, int n, int k, double alpha, const R* A, lon
                  const R* B, long long ldb, double beta, R* C, long long ldc, cudaStream_t st,
                  const int* bmap, const int* cmap) {
   if (m <= 0 || n <= 0) return cudaSuccess;
-  const int tm = (m + 63) / 64, tn = (n + 63) / 64;
+  // 80-row tiles when they pad m less than 64-row tiles do
+  const bool t80 = ((m + 79) / 80) * 80 < ((m + 63) / 64) * 64;
+  const int bm = t80 ? 80 : 64;
+  const int tm = (m + bm - 1) / bm, tn = (n + 63) / 64;
   int splits = 1;
   const long long tiles = (long long)tm * tn;
   if (tiles < 2LL * num_sms() && k > 256) {
@@ -203,12 +207,22 @@ cudaError_t gemm(bool transA, int m, int n, int k, double alpha, const R* A, lon
   ProfScope ps(sizeof(R) == 8 ? PC_GEMM_F64 : PC_GEMM_F32, st, 2.0 * m * n * (double)k,
                ((double)m * k + (double)k * n + (beta != 0.0 ? 2.0 : 1.0) * m * n) * sizeof(R));
   count_launch();
-  if (transA)
-    k_gemm<R, true><<<grid, 256, 0, st>>>(m, n, k, (R)alpha, A, lda, B, ldb, (R)beta, C, ldc,
-                                          kchunk, atomic, bmap, cmap);
-  else
-    k_gemm<R, false><<<grid, 256, 0, st>>>(m, n, k, (R)alpha, A, lda, B, ldb, (R)beta, C, ldc,
-                                           kchunk, atomic, bmap, cmap);
+  const R al = (R)alpha, be = (R)beta;
+  if (transA) {
+    if (t80)
+      k_gemm<R, true, 5><<<grid, 256, 0, st>>>(m, n, k, al, A, lda, B, ldb, be, C, ldc, kchunk,
+                                               atomic, bmap, cmap);
+    else
+      k_gemm<R, true, 4><<<grid, 256, 0, st>>>(m, n, k, al, A, lda, B, ldb, be, C, ldc, kchunk,
+                                               atomic, bmap, cmap);
+  } else {
+    if (t80)
+      k_gemm<R, false, 5><<<grid, 256, 0, st>>>(m, n, k, al, A, lda, B, ldb, be, C, ldc, kchunk,
+                                                atomic, bmap, cmap);
+    else
+      k_gemm<R, false, 4><<<grid, 256, 0, st>>>(m, n, k, al, A, lda, B, ldb, be, C, ldc, kchunk,
+                                                atomic, bmap, cmap);
+  }
   return cudaGetLastError();
 }
 
@@ -792,8 +806,12 @@ __global__ void k_lanczos_step(const double* __restrict__ W, const double* __res
     ww += w * w;
   }
   const double2 t = block_sum2(aw, ww);
-  const double a = t.x, hn = sqrt(t.y);
-  const double bk = k > 0 ? beta[(long long)j * K + k] : 0.0;
+  // a chain that stopped (q_k = 0: beta_0 = 0, or beta_k = 0 for k >= 1) stays
+  // stopped: W then holds only the rounding that the packed transforms leak
+  // from the other vector of the pair, which must not restart it
+  const double bk = beta[(long long)j * K + k];
+  const bool dead = bk == 0.0;
+  const double a = dead ? 0.0 : t.x, hn = sqrt(t.y);
   if (threadIdx.x == 0) alpha[(long long)j * K + k] = a;
   if (k + 1 >= K) return;
   double rr = 0.0;
@@ -804,7 +822,7 @@ __global__ void k_lanczos_step(const double* __restrict__ W, const double* __res
     rr += r * r;
   }
   const double b = sqrt(block_sum2(rr, 0.0).x);
-  const bool stop = !(b > 1e-12 * hn);
+  const bool stop = dead || !(b > 1e-12 * hn);
   const double f = stop ? 0.0 : 1.0 / b;
   for (int i = threadIdx.x; i < n_pw; i += blockDim.x) Qk1[o + i] *= f;
   if (threadIdx.x == 0) beta[(long long)j * K + k + 1] = stop ? 0.0 : b;
@@ -1040,6 +1058,87 @@ __global__ void k_lambda_from_eig(const double* __restrict__ V, const double* __
 cudaError_t lambda_from_eig(const double* V, const double* w, int n, double* L, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   { count_launch(); k_lambda_from_eig<<<n, 128, 0, st>>>(V, w, n, L); }
+  return cudaGetLastError();
+}
+
+// out[j] = X_j . Y_j (one block per column)
+__global__ void k_pair_dots(const double* __restrict__ X, const double* __restrict__ Y,
+                            long long ld, int rows, double* out) {
+  const int j = blockIdx.x;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < rows; i += blockDim.x)
+    s += X[(long long)j * ld + i] * Y[(long long)j * ld + i];
+  const double2 t = block_sum2(s, 0.0);
+  if (threadIdx.x == 0) out[j] = t.x;
+}
+cudaError_t pair_dots(const double* X, const double* Y, long long ld, int rows, int n, double* out,
+                      cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  { count_launch(); k_pair_dots<<<n, 256, 0, st>>>(X, Y, ld, rows, out); }
+  return cudaGetLastError();
+}
+
+// One CG update per column j: x += a_j p, r -= a_j q (a = coef[j])
+__global__ void k_cg_xr(double* x, double* r, const double* __restrict__ p,
+                        const double* __restrict__ q, long long ld, int rows,
+                        const double* __restrict__ coef) {
+  const int j = blockIdx.y;
+  const double a = coef[j];
+  if (a == 0.0) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += gridDim.x * blockDim.x) {
+    const long long o = (long long)j * ld + i;
+    x[o] += a * p[o];
+    r[o] -= a * q[o];
+  }
+}
+// p = r + b_j p
+__global__ void k_cg_p(double* p, const double* __restrict__ r, long long ld, int rows,
+                       const double* __restrict__ coef) {
+  const int j = blockIdx.y;
+  const double b = coef[j];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += gridDim.x * blockDim.x) {
+    const long long o = (long long)j * ld + i;
+    p[o] = r[o] + b * p[o];
+  }
+}
+// q = p - q (column blocks)
+__global__ void k_one_minus(double* q, const double* __restrict__ p, long long ld, int rows) {
+  const int j = blockIdx.y;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += gridDim.x * blockDim.x) {
+    const long long o = (long long)j * ld + i;
+    q[o] = p[o] - q[o];
+  }
+}
+cudaError_t one_minus(double* q, const double* p, long long ld, int rows, int n, cudaStream_t st) {
+  const int bx = std::min((rows + 255) / 256, 64);
+  for (int j0 = 0; j0 < n; j0 += 65535) {
+    const int nj = std::min(65535, n - j0);
+    const long long o = (long long)j0 * ld;
+    count_launch();
+    k_one_minus<<<dim3(bx, nj), 256, 0, st>>>(q + o, p + o, ld, rows);
+  }
+  return cudaGetLastError();
+}
+cudaError_t block_cg_xr(double* x, double* r, const double* p, const double* q, long long ld,
+                        int rows, int n, const double* alpha, cudaStream_t st) {
+  const int bx = std::min((rows + 255) / 256, 64);
+  for (int j0 = 0; j0 < n; j0 += 65535) {
+    const int nj = std::min(65535, n - j0);
+    const long long o = (long long)j0 * ld;
+    count_launch();
+    k_cg_xr<<<dim3(bx, nj), 256, 0, st>>>(x + o, r + o, p + o, q + o, ld, rows, alpha + j0);
+  }
+  return cudaGetLastError();
+}
+cudaError_t block_cg_p(double* p, const double* r, long long ld, int rows, int n,
+                       const double* beta, cudaStream_t st) {
+  const int bx = std::min((rows + 255) / 256, 64);
+  for (int j0 = 0; j0 < n; j0 += 65535) {
+    const int nj = std::min(65535, n - j0);
+    const long long o = (long long)j0 * ld;
+    count_launch();
+    k_cg_p<<<dim3(bx, nj), 256, 0, st>>>(p + o, r + o, ld, rows, beta + j0);
+  }
   return cudaGetLastError();
 }
 

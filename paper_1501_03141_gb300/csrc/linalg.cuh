@@ -75,6 +75,16 @@ cudaError_t lanczos_z(const double* U, const double* d, const double* beta, int 
 cudaError_t body_accum(const double* G, int n_L, int n, int K, const double* z, int n_freq,
                        double scale, double* B, cudaStream_t st);
 cudaError_t lambda_from_eig(const double* V, const double* w, int n, double* L, cudaStream_t st);
+// Column-wise dots X_j . Y_j; q = p - q; and the updates of a block of
+// independent CG problems with per-column alpha and beta (device arrays):
+// x += alpha p, r -= alpha q, then p = r + beta p.
+cudaError_t pair_dots(const double* X, const double* Y, long long ld, int rows, int n, double* out,
+                      cudaStream_t st);
+cudaError_t one_minus(double* q, const double* p, long long ld, int rows, int n, cudaStream_t st);
+cudaError_t block_cg_xr(double* x, double* r, const double* p, const double* q, long long ld,
+                        int rows, int n, const double* alpha, cudaStream_t st);
+cudaError_t block_cg_p(double* p, const double* r, long long ld, int rows, int n,
+                       const double* beta, cudaStream_t st);
 // W = L^{-T} for the Cholesky factor of the m x m Gram matrix G (m <= 128);
 // *fail = 1 (device) when a pivot is at or below rel_thr * max_i G_ii.
 cudaError_t cholesky_winv(const double* G, int m, double rel_thr, double* W, int* fail,
