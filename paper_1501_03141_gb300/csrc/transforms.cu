@@ -227,12 +227,24 @@ struct SlabMinBlocks {
   static constexpr int t = SlabThreads<R, N2, N3>::v;
   static constexpr int v = sizeof(R) != 4 ? 1 : t <= 128 ? 384 / t : t <= 256 ? 3 : 1;
 };
-// Row stride of the (n3, i2) shared-memory plane: FP32 rows are padded by 8
-// complex so that the four n3 rows a warp touches fall on two bank halves.
+// Row stride of the (n3, i2) shared-memory plane (FP32 rows padded by 8
+// complex) and, in FP32, a column swizzle: element (row, col) sits at
+// row * TS + (col ^ (row & 7)).  The swizzle stays inside each aligned block
+// of 8 columns (N2 is a multiple of 8) and spreads the eight y-line slots a
+// warp touches, whose four lanes' positions are 12 complex apart, over all
+// banks (a third of the shared-memory wavefronts of the LSU-bound FP32 slab);
+// the four n3 rows of a z-line access keep their distinct halves.  FP64 slabs
+// are FP64-pipe bound and keep the plain layout: the swizzle's index
+// arithmetic costs them a resident block per SM.
 template <typename R, int N2>
 struct T2Stride {
   static constexpr int v = sizeof(R) == 4 ? N2 + 8 : N2;
 };
+template <typename R>
+__device__ __forceinline__ int t2_at(int row, int col, int ts) {
+  if constexpr (sizeof(R) == 4) return row * ts + (col ^ (row & 7));
+  return row * ts + col;
+}
 
 template <typename R, int N2>
 __device__ __forceinline__ void y_inverse(const SphereDev<R>& s, const cpx<R>* S1, cpx<R>* T2) {
@@ -259,7 +271,7 @@ __device__ __forceinline__ void y_inverse(const SphereDev<R>& s, const cpx<R>* S
     fft_a2b<R, N2, TL, +1>(v, t, s.tw2);
     if (act) {
 #pragma unroll
-      for (int i = 0; i < M; ++i) T2[sl * TS + pos_b<N2, TL>(t, i)] = v[i];
+      for (int i = 0; i < M; ++i) T2[t2_at<R>(sl, pos_b<N2, TL>(t, i), TS)] = v[i];
     }
   }
 }
@@ -280,7 +292,7 @@ __device__ __forceinline__ void y_forward(const SphereDev<R>& s, const cpx<R>* T
     const int2 info = act ? s.slot[sl] : make_int2(-1, 0);
     cpx<R> v[M];
 #pragma unroll
-    for (int i = 0; i < M; ++i) v[i] = act ? T2[sl * TS + pos_b<N2, TL>(t, i)] : zero<R>();
+    for (int i = 0; i < M; ++i) v[i] = act ? T2[t2_at<R>(sl, pos_b<N2, TL>(t, i), TS)] : zero<R>();
     fft_b2a<R, N2, TL, -1>(v, t, s.tw2);
     if (act) {
 #pragma unroll
@@ -339,7 +351,7 @@ __global__ void __launch_bounds__(SlabThreads<R, N2, N3>::v, (SlabMinBlocks<R, N
 #pragma unroll
       for (int i = 0; i < M3; ++i) {
         const int n3 = freq_of(pos_a<N3, TL3>(t3, i), N3);
-        v[i] = (act && iabs(n3) <= R3) ? T2[(n3 + R3) * TS + i2] : zero<R>();
+        v[i] = (act && iabs(n3) <= R3) ? T2[t2_at<R>(n3 + R3, i2, TS)] : zero<R>();
       }
       fft_a2b<R, N3, TL3, +1>(v, t3, s.tw3);
       if (a.mode == SLAB_TO_GRID) {
@@ -399,7 +411,7 @@ __global__ void __launch_bounds__(SlabThreads<R, N2, N3>::v, (SlabMinBlocks<R, N
 #pragma unroll
       for (int i = 0; i < M3; ++i) {
         const int n3 = freq_of(pos_a<N3, TL3>(t3, i), N3);
-        if (iabs(n3) <= R3) T2[(n3 + R3) * TS + i2] = v[i];
+        if (iabs(n3) <= R3) T2[t2_at<R>(n3 + R3, i2, TS)] = v[i];
       }
     }
   }
