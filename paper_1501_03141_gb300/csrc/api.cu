@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 #include "linalg.cuh"
 #include "transforms.cuh"
@@ -18,6 +20,15 @@
 namespace pdep {
 
 static thread_local std::string g_last_error;
+
+// NVTX range for the span of a scope (no cost unless a profiler is attached):
+// pdep_solve, davidson_iteration, chi0bar_apply, refinement_round, setup, ...
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 void set_last_error(const char* file, int line, const char* msg) {
   char buf[512];
@@ -628,6 +639,7 @@ int davidson(pdep_ctx* c, SysData& s, int nwant, int nconv, int nb_max, const do
   out->iterations = 0;
   out->converged = 0;
   for (int it = 0; it < max_iter; ++it) {
+    NvtxRange nv("davidson_iteration");
     RET(op(B + (size_t)lo * ld, AB + (size_t)lo * ld, hi - lo));
     out->iterations = it + 1;
     // Rayleigh-Ritz in span(B)
@@ -793,6 +805,7 @@ int chfsi(pdep_ctx* c, SysData& s, int ns, int nconv, double tol, int max_iter, 
 }
 
 int setup_states(pdep_ctx* c, SysData& s, cudaStream_t st) {
+  NvtxRange nv("setup_states");
   const int nocc = s.n_occ;
   s.n_defl = std::max(0, std::min(c->opt.n_deflate, s.n_pw - nocc - 2));
   s.n_ext = nocc + s.n_defl;
@@ -1026,6 +1039,7 @@ int solve_rhs(pdep_ctx* c, SysData& s, const double* b, const double* xd, double
       RET(sync(st));
     }
     for (int round = 0; round < c->opt.max_refine; ++round) {
+      NvtxRange nv("refinement_round");
       CK(unconverged_list(rel, tol, n, list, c->d_counter + 1, st));
       int n_un = 0;
       RET(read_int(c, c->d_counter + 1, &n_un, st));
@@ -1136,6 +1150,7 @@ int perturbation_grids(pdep_ctx* c, SysData& s, const double* phi, int m, double
 // chi0bar phi for m PDEP vectors (internal layout [m][ld], G=0 slot zero)
 int chi0_internal(pdep_ctx* c, SysData& s, const double* phi, int m, double* out, double* dn_out,
                   cudaStream_t st) {
+  NvtxRange nv("chi0bar_apply");
   const int nocc = s.n_occ;
   // perturbation chunk: keep roughly 10 vectors of n_rhs*ld doubles bounded
   size_t per = (size_t)nocc * s.ld * sizeof(double) * 9 + b1_count(s, (nocc + 1) / 2) * 16 +
@@ -1205,6 +1220,7 @@ void reset_stats(pdep_ctx* c) {
 
 int solve_one(pdep_ctx* c, int si, const double* phi0, double* eigvals, double* eigvecs,
               pdep_stats* stats, cudaStream_t st) {
+  NvtxRange nv("pdep_solve");
   SysData& s = c->sys[si];
   const int np = s.n_pdep;
   const int dim = s.n_pw - 1;
@@ -1542,6 +1558,7 @@ int pdep_screening_apply(pdep_ctx* c, int sys, int kind, const double* eigvals,
 // Lambda = (1 - B)^{-1} B (Eq. Bfinal without head and wings).
 int pdep_chi0_imag(pdep_ctx* c, int sys, const double* phi, int n_pdep, const double* nu,
                    int n_freq, int n_steps, double* B, double* Lambda, void* stream) {
+  NvtxRange nv("chi0_imag");
   RET(check_sys(c, sys));
   SysData& s = c->sys[sys];
   const int dim = s.n_pw - 1;
@@ -1650,6 +1667,7 @@ int pdep_chi0_imag(pdep_ctx* c, int sys, const double* phi, int n_pdep, const do
 int pdep_lanczos(pdep_ctx* c, int sys, const double* R, int n, int n_steps, const double* L,
                  int n_L, double* poles, double* weights, double* alpha, double* beta,
                  void* stream) {
+  NvtxRange nv("lanczos");
   RET(check_sys(c, sys));
   if (n < 0 || n_steps < 1 || n_steps > 64 || n_L < 0 ||
       (n > 0 && (!R || !poles || (n_L > 0 && (!L || !weights)))))
@@ -1719,6 +1737,7 @@ int pdep_lanczos(pdep_ctx* c, int sys, const double* R, int n, int n_steps, cons
 // (1 - chi0bar)^{-1} chi0bar phi of Eq. linearalgebrachichi0.
 int pdep_chibar_apply(pdep_ctx* c, int sys, const double* phi, int n, double* out, double tol,
                       int max_iter, int* iterations, void* stream) {
+  NvtxRange nv("chibar_apply");
   RET(check_sys(c, sys));
   if (n < 0 || max_iter < 1 || !(tol > 0) || (n > 0 && (!phi || !out)))
     return fail(PDEP_ERR_INVALID_ARG, "bad pdep_chibar_apply arguments");

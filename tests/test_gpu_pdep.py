@@ -101,3 +101,25 @@ def test_ritz_interlacing_and_monotone(tiny_ref):
         assert np.all(th >= lam - tol), th - lam
     assert np.all(thetas[1] <= thetas[0] + tol)
     assert np.all(thetas[2] <= thetas[1] + tol)
+
+
+def test_checkpoint_resume(tiny_ref, tmp_path):
+    """A run cut after two Davidson iterations is saved to disk; resuming from
+    the saved vectors converges to the same eigenpairs in fewer iterations
+    than a cold start."""
+    need_gpu()
+    lib_ready()
+    import paper_1501_03141_gb300 as pg
+    s, b, ks = oracle_for("tiny")
+    lam, _ = tiny_ref
+    with pg.Context(s, dav_tol=0.0, dav_max_iter=2) as ctx:
+        _, evec, _ = ctx.pdep_solve(allow_unconverged=True)
+    ck = tmp_path / "pdep_vectors.npy"
+    np.save(ck, evec.reshape(s.n_pdep, b.n_pdep_dim))
+    with pg.Context(s) as ctx:
+        ev_cold, _, st_cold = ctx.pdep_solve()
+        ev_warm, _, st_warm = ctx.pdep_solve(phi0=np.load(ck))
+    assert st_cold["converged"] == 1 and st_warm["converged"] == 1
+    assert (np.abs(ev_warm - lam) / np.abs(lam)).max() < 1e-8
+    assert (np.abs(ev_warm - ev_cold) / np.abs(lam)).max() < 1e-8
+    assert st_warm["dav_iterations"] < st_cold["dav_iterations"]
