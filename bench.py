@@ -10,7 +10,8 @@ response, projection), Rayleigh-Ritz, orthonormalisation.  The setup
 
   value    Sternheimer solves/s of the mixed-precision path (FP32 CG, FP64
            refinement), inputs resident in HBM, CUDA events on the stream
-           the library runs on, W warm-up steps then K timed steps.
+           the library runs on, W warm-up steps then K timed steps
+           (step_ms: median and p10-p90 of the per-step times).
   fp64     the same step with the plain FP64 path.
   e2e      the mixed step through the public API with pinned host buffers
            (start block in, eigenvalues and eigenvectors out).
@@ -78,6 +79,22 @@ def reduce_scalar(x: float, op: str, device=None) -> float:
     t = torch.tensor([float(x)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def step_spread(ms):
+    """Median, 10th and 90th percentile (linear interpolation) of per-step times."""
+    xs = sorted(float(x) for x in ms)
+    if not xs:
+        return None
+
+    def pct(q):
+        pos = q * (len(xs) - 1)
+        lo = int(pos)
+        hi = min(lo + 1, len(xs) - 1)
+        return xs[lo] + (xs[hi] - xs[lo]) * (pos - lo)
+
+    return {"median": round(pct(0.5), 2), "p10": round(pct(0.1), 2),
+            "p90": round(pct(0.9), 2), "n": len(xs)}
 
 
 # ---------------------------------------------------------------------------
@@ -292,11 +309,14 @@ def run_ours(args):
     nvtx = getattr(torch.cuda, "nvtx", None)
     if nvtx is not None:
         nvtx.range_push("timed")   # profilers can restrict themselves to this range
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps - 1)]
     e0.record(stream)
     solves = 0
-    for _ in range(args.steps):
+    for i in range(args.steps):
         _, _, stats = ctx.pdep_solve(eigvals=ev, eigvecs=evec)
         solves += stats["sternheimer_solves"]
+        if i < args.steps - 1:
+            marks[i].record(stream)
     e1.record(stream)
     torch.cuda.synchronize(dev)
     if nvtx is not None:
@@ -305,6 +325,8 @@ def run_ours(args):
     clk = clocks.stop()
     barrier()
     t_local = e0.elapsed_time(e1) / 1e3
+    bounds = [e0] + marks + [e1]
+    step_ms = step_spread([a.elapsed_time(b) for a, b in zip(bounds[:-1], bounds[1:])])
     t = reduce_scalar(t_local, "max", dev if world > 1 else None)
     total_solves = reduce_scalar(solves, "sum", dev if world > 1 else None)
     value = total_solves / t
@@ -367,7 +389,8 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": round(value, 2), "unit": "solves/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": round(1e3 * t / args.steps, 1), "higher_is_better": True,
+            "ms_per_step": round(1e3 * t / args.steps, 1), "step_ms": step_ms,
+            "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "precision": "mixed: FP32 FFT/H*psi/P_v in CG, "
@@ -499,7 +522,7 @@ def run_small(args):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=1)

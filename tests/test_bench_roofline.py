@@ -64,3 +64,13 @@ def test_traffic_needs_matching_sources(tmp_path, monkeypatch):
     good["classes"]["slab_f64"]["sources_hash"] = "0" * 16
     f.write_text(json.dumps(good))
     assert bench.traffic_for("slab_f64", 100.0) is None
+
+
+def test_step_spread():
+    import bench
+    assert bench.step_spread([]) is None
+    one = bench.step_spread([5.0])
+    assert one == {"median": 5.0, "p10": 5.0, "p90": 5.0, "n": 1}
+    sp = bench.step_spread([3.0, 1.0, 2.0, 5.0, 4.0])
+    assert sp["median"] == 3.0 and sp["n"] == 5
+    assert sp["p10"] == pytest.approx(1.4) and sp["p90"] == pytest.approx(4.6)
