@@ -75,7 +75,9 @@ typedef enum {
   PDEP_ERR_NOT_CONVERGED = 5, /* a solve reached its iteration cap */
   PDEP_ERR_NONFINITE = 6,     /* NaN/Inf met in the data or a CG scalar */
   PDEP_ERR_TIMEOUT = 7,       /* reserved: no device loop waits on another agent */
-  PDEP_ERR_UNSUPPORTED = 8    /* option combination not implemented */
+  PDEP_ERR_UNSUPPORTED = 8,   /* option combination not implemented */
+  PDEP_ERR_BOUNDS = 9         /* bounds-checked builds: a kernel met an index outside
+                                 the sphere tables and skipped the access */
 } pdep_status;
 
 typedef enum {
@@ -318,6 +320,20 @@ typedef struct {
   pdep_kernel_class cls[PDEP_PROFILE_CLASSES];
 } pdep_profile_t;
 int pdep_profile(int enable, pdep_profile_t* out);
+
+/* Device status word.  Kernels OR condition bits into a per-context word
+ * (non-finite CG scalar, CG breakdown, and in bounds-checked builds an index
+ * outside the sphere tables).  The Sternheimer solves and pdep_setup read it
+ * after their last launch; pdep_sync_status synchronises 'stream', returns
+ * the condition of the word (PDEP_OK, PDEP_ERR_NONFINITE or PDEP_ERR_BOUNDS)
+ * for every call enqueued so far, and clears it.  PDEP_ERR_INVALID_ARG for a
+ * NULL context. */
+int pdep_sync_status(pdep_ctx* ctx, void* stream);
+
+/* 1 if this library was compiled with -DPDEP_BOUNDS_CHECK (every index read
+ * from the host-built sphere tables is tested before use in the transform
+ * kernels), else 0. */
+int pdep_bounds_checked(void);
 
 void pdep_destroy(pdep_ctx* ctx);
 const char* pdep_status_string(int status);

@@ -125,6 +125,12 @@ class Context:
                                                _stream(self.stream)), "pdep_get_occupied")
         return psi, eps
 
+    def sync_status(self):
+        """Wait for the context's stream; raise PdepError if a kernel flagged a
+        condition (non-finite value, index out of range in a bounds-checked
+        build) since the last check, and clear the device status word."""
+        _abi.check(self._lib.pdep_sync_status(self._h, _stream(self.stream)), "pdep_sync_status")
+
     def apply_hamiltonian(self, x, sys: int = 0, precision: int = PDEP_FP64, out=None):
         """H x for sphere vectors x [n, n_pw]."""
         if out is None:

@@ -12,7 +12,9 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libpdep.so")
+#: PDEP_BOUNDS_CHECK=1 in the environment selects the bounds-checked build
+BOUNDS_CHECK = os.environ.get("PDEP_BOUNDS_CHECK", "0") not in ("", "0")
+LIB_PATH = os.path.join(HERE, "libpdep_check.so" if BOUNDS_CHECK else "libpdep.so")
 
 PDEP_OK = 0
 PDEP_ERR_INVALID_ARG = 1
@@ -23,6 +25,7 @@ PDEP_ERR_NOT_CONVERGED = 5
 PDEP_ERR_NONFINITE = 6
 PDEP_ERR_TIMEOUT = 7
 PDEP_ERR_UNSUPPORTED = 8
+PDEP_ERR_BOUNDS = 9
 
 PDEP_FP64 = 0
 PDEP_MIXED = 1
@@ -37,7 +40,7 @@ EXPORTS = (
     "chi0_apply", "sternheimer_solve", "pdep_solve", "pdep_apply_hamiltonian", "pdep_to_grid",
     "pdep_profile", "pdep_destroy", "pdep_status_string", "pdep_last_error",
     "pdep_apply_hamiltonian_noalloc", "pdep_screening_apply", "pdep_lanczos", "pdep_chi0_imag",
-    "pdep_chibar_apply",
+    "pdep_chibar_apply", "pdep_sync_status", "pdep_bounds_checked",
 )
 
 PDEP_PROFILE_CLASSES = 11
@@ -118,7 +121,8 @@ def load(path: str = LIB_PATH):
         return _lib
     if not os.path.exists(path):
         raise RuntimeError(
-            f"{path} is missing: build it with paper_1501_03141_gb300.build.build() "
+            f"{path} is missing: build it with paper_1501_03141_gb300.build.build("
+            f"bounds_check={BOUNDS_CHECK}) "
             "(nvcc, sm_103a); there is no CPU fallback")
     lib = ctypes.CDLL(path)
     vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
@@ -147,10 +151,12 @@ def load(path: str = LIB_PATH):
     lib.pdep_status_string.restype = ctypes.c_char_p
     lib.pdep_last_error.argtypes = []
     lib.pdep_last_error.restype = ctypes.c_char_p
+    lib.pdep_sync_status.argtypes = [vp, vp]
+    lib.pdep_bounds_checked.argtypes = []
     for name in ("pdep_setup", "pdep_get_sizes", "pdep_get_occupied", "chi0_apply",
                  "sternheimer_solve", "pdep_solve", "pdep_apply_hamiltonian", "pdep_to_grid",
                  "pdep_screening_apply", "pdep_lanczos", "pdep_chi0_imag",
-                 "pdep_chibar_apply"):
+                 "pdep_chibar_apply", "pdep_sync_status", "pdep_bounds_checked"):
         getattr(lib, name).restype = ip
     del dp
     _lib = lib

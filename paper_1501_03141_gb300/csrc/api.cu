@@ -220,6 +220,7 @@ int check_status(pdep_ctx* c, cudaStream_t st) {
   memcpy(&h, c->h_pin, sizeof(unsigned));
   if (h & DEV_NONFINITE) return fail(PDEP_ERR_NONFINITE, "non-finite value met on the device");
   if (h & DEV_BREAKDOWN) return fail(PDEP_ERR_NONFINITE, "CG breakdown (p.Ap <= 0)");
+  if (h & DEV_BOUNDS) return fail(PDEP_ERR_BOUNDS, "sphere-table index out of range");
   return PDEP_OK;
 }
 
@@ -361,6 +362,9 @@ int upload_tables(pdep_ctx* c, SysData& s) {
     d.tw1 = tw[0];
     d.tw2 = tw[1];
     d.tw3 = tw[2];
+#ifdef PDEP_BOUNDS_CHECK
+    d.status = c->d_status;
+#endif
   };
   fill(s.sd, s.d_tw64);
   fill(s.sf, s.d_tw32);
@@ -1350,11 +1354,29 @@ const char* pdep_status_string(int s) {
     case PDEP_ERR_NONFINITE: return "non-finite value";
     case PDEP_ERR_TIMEOUT: return "timeout";
     case PDEP_ERR_UNSUPPORTED: return "unsupported";
+    case PDEP_ERR_BOUNDS: return "index out of range (bounds-checked build)";
   }
   return "unknown status";
 }
 
 const char* pdep_last_error(void) { return g_last_error.c_str(); }
+
+int pdep_sync_status(pdep_ctx* c, void* stream) {
+  if (!c) return fail(PDEP_ERR_INVALID_ARG, "null context");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int r = check_status(c, st);
+  CK(cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), st));
+  CK(cudaStreamSynchronize(st));
+  return r;
+}
+
+int pdep_bounds_checked(void) {
+#ifdef PDEP_BOUNDS_CHECK
+  return 1;
+#else
+  return 0;
+#endif
+}
 
 void pdep_destroy(pdep_ctx* c) {
   if (!c) return;
@@ -1438,6 +1460,7 @@ int pdep_setup(const pdep_system_desc* sys, int n_sys, const pdep_options* opt, 
     }
     r = setup_states(c, s, st);
     if (r != PDEP_OK) return bail(r);
+    if ((r = check_status(c, st)) != PDEP_OK) return bail(r);
   }
   *out = c;
   return PDEP_OK;

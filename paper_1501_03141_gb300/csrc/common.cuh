@@ -57,6 +57,21 @@ enum : unsigned {
   DEV_BREAKDOWN = 8u,
 };
 
+// Builds compiled with -DPDEP_BOUNDS_CHECK test every index that a kernel
+// reads from the host-built sphere tables before using it: an index outside
+// [0, n) sets DEV_BOUNDS in the status word and the access is skipped (the
+// result is then wrong, and the call that reads the status returns
+// PDEP_ERR_BOUNDS).  Normal builds compile the test to `true`.
+__device__ __forceinline__ bool in_range(unsigned* status, long long i, long long n) {
+#ifdef PDEP_BOUNDS_CHECK
+  if (i >= 0 && i < n) return true;
+  if (status) atomicOr(status, (unsigned)DEV_BOUNDS);
+  return false;
+#else
+  return true;
+#endif
+}
+
 }  // namespace pdep
 
 #define PDEP_CUDA_CHECK(call)                                                  \

@@ -68,10 +68,11 @@ __global__ void __launch_bounds__(128) k_cols_fwd(SphereDev<R> s, const R* __res
   const int t = threadIdx.x & (TPL - 1);
   const long long g = (long long)blockIdx.x * (blockDim.x / TPL) + threadIdx.x / TPL;
   const long long total = (long long)n_items * s.n_ucol;
-  const bool active = g < total;
-  const int item = active ? (int)(g / s.n_ucol) : 0;
-  const int uc = active ? (int)(g - (long long)item * s.n_ucol) : 0;
+  const bool live = g < total;
+  const int item = live ? (int)(g / s.n_ucol) : 0;
+  const int uc = live ? (int)(g - (long long)item * s.n_ucol) : 0;
   const UCol c = s.ucol[uc];
+  const bool active = live && ucol_in_range(s, c);
   const bool self = (c.col == c.mcol);
   const int ia = map.vec(item, 0), ib = map.vec(item, 1);
   const R* xa = (active && ia >= 0) ? x + (long long)ia * ldx : nullptr;
@@ -151,10 +152,11 @@ __global__ void __launch_bounds__(128) k_cols_bwd(SphereDev<R> s, const cpx<R>* 
   const int t = threadIdx.x & (TPL - 1);
   const long long g = (long long)blockIdx.x * (blockDim.x / TPL) + threadIdx.x / TPL;
   const long long total = (long long)n_items * s.n_ucol;
-  const bool active = g < total;
-  const int item = active ? (int)(g / s.n_ucol) : 0;
-  const int uc = active ? (int)(g - (long long)item * s.n_ucol) : 0;
+  const bool live = g < total;
+  const int item = live ? (int)(g / s.n_ucol) : 0;
+  const int uc = live ? (int)(g - (long long)item * s.n_ucol) : 0;
   const UCol c = s.ucol[uc];
+  const bool active = live && ucol_in_range(s, c);
   const bool self = (c.col == c.mcol);
 
   const cpx<R>* base = b1 + (long long)item * N1 * s.n_col;
@@ -260,8 +262,9 @@ __device__ __forceinline__ void y_inverse(const SphereDev<R>& s, const cpx<R>* S
   for (int base = 0; base < nslot; base += per) {
     if (base + wslot0 >= nslot) break;
     const int sl = base + threadIdx.x / TL;
-    const bool act = sl < nslot;
-    const int2 info = act ? s.slot[sl] : make_int2(-1, 0);
+    const bool live = sl < nslot;
+    const int2 info = live ? s.slot[sl] : make_int2(-1, 0);
+    const bool act = live && slot_in_range(s, info);
     cpx<R> v[M];
 #pragma unroll
     for (int i = 0; i < M; ++i) {
@@ -288,8 +291,9 @@ __device__ __forceinline__ void y_forward(const SphereDev<R>& s, const cpx<R>* T
   for (int base = 0; base < nslot; base += per) {
     if (base + wslot0 >= nslot) break;
     const int sl = base + threadIdx.x / TL;
-    const bool act = sl < nslot;
-    const int2 info = act ? s.slot[sl] : make_int2(-1, 0);
+    const bool live = sl < nslot;
+    const int2 info = live ? s.slot[sl] : make_int2(-1, 0);
+    const bool act = live && slot_in_range(s, info);
     cpx<R> v[M];
 #pragma unroll
     for (int i = 0; i < M; ++i) v[i] = act ? T2[t2_at<R>(sl, pos_b<N2, TL>(t, i), TS)] : zero<R>();

@@ -34,7 +34,39 @@ struct SphereDev {
   const cpx<R>* tw1;        // exp(+2 pi i j/N1), j < N1
   const cpx<R>* tw2;
   const cpx<R>* tw3;
+#ifdef PDEP_BOUNDS_CHECK
+  unsigned* status = nullptr;  // device status word the bounds tests report to
+#endif
 };
+
+// Bounds-checked builds: the sphere members and the columns of x-line c lie
+// inside the tables (members h0 .. h0 + 2 R1 of a mirrored pair, h0 ..
+// h0 + R1 - 1 of the self-mirrored (0, 0) line).  Always true otherwise.
+template <typename R>
+__device__ __forceinline__ bool ucol_in_range(const SphereDev<R>& s, const UCol& c) {
+#ifdef PDEP_BOUNDS_CHECK
+  const int members = c.col == c.mcol ? c.R1 : 2 * c.R1 + 1;
+  bool ok = in_range(s.status, c.col, s.n_col) && in_range(s.status, c.mcol, s.n_col) &&
+            in_range(s.status, c.R1, s.N1 / 2 + 1);
+  if (members > 0)
+    ok = ok && in_range(s.status, c.h0, s.n_half) && in_range(s.status, c.h0 + members - 1, s.n_half);
+  return ok;
+#else
+  return true;
+#endif
+}
+
+// Bounds-checked builds: the columns of y-line slot (R2, first) lie inside
+// the column list.  Always true otherwise.
+template <typename R>
+__device__ __forceinline__ bool slot_in_range(const SphereDev<R>& s, int2 info) {
+#ifdef PDEP_BOUNDS_CHECK
+  return in_range(s.status, info.y, s.n_col) && in_range(s.status, info.y + 2 * info.x, s.n_col) &&
+         in_range(s.status, info.x, s.N2 / 2 + 1);
+#else
+  return true;
+#endif
+}
 
 // Which real vectors an FFT item packs: vectors are grouped; item w of a
 // group takes members 2w and 2w+1 (the second may be absent).

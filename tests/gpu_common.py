@@ -14,8 +14,8 @@ def need_gpu():
 
 @functools.lru_cache(maxsize=None)
 def lib_ready():
-    from paper_1501_03141_gb300 import build
-    build.build()
+    from paper_1501_03141_gb300 import _abi, build
+    build.build(bounds_check=_abi.BOUNDS_CHECK)
     return True
 
 
