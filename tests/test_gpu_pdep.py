@@ -123,3 +123,30 @@ def test_checkpoint_resume(tiny_ref, tmp_path):
     assert (np.abs(ev_warm - lam) / np.abs(lam)).max() < 1e-8
     assert (np.abs(ev_warm - ev_cold) / np.abs(lam)).max() < 1e-8
     assert st_warm["dav_iterations"] < st_cold["dav_iterations"]
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-8), (1, 1e-6)])
+def test_free_electron_golden(precision, tol):
+    """V = 0 on the 24^3 grid, 7 occupied states: the GPU's PDEP eigenvalues
+    against the stored closed-form values (tests/golden), through the first
+    two complete multiplets (6 + 8); the occupied shell and the Sternheimer
+    operators are degenerate."""
+    need_gpu()
+    lib_ready()
+    import os
+    import sys
+    import synthetic
+    import paper_1501_03141_gb300 as pg
+    sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
+    import make_golden
+    stored = make_golden.read(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                           make_golden.NAME))
+    s = synthetic.System(name="free24", grid=make_golden.GRID, cell=make_golden.CELL,
+                         v_r=np.zeros(make_golden.GRID), n_occ=make_golden.N_OCC, n_pdep=14,
+                         seed=0)
+    with pg.Context(s, precision=precision) as ctx:
+        assert ctx.sizes()["n_pw"] == 799
+        ev, _, st = ctx.pdep_solve()
+    assert st["converged"] == 1
+    err = np.abs(ev - stored[:14]) / np.abs(stored[:14])
+    assert err.max() < tol, err
