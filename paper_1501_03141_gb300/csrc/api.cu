@@ -129,6 +129,8 @@ struct pdep_ctx {
   int proj_tune_calls = 0;
   double cg_tune_ms[2][CG_NUM_VARIANTS] = {};
   int cg_tune_next[2] = {0, 0};
+  // executable graphs of the Jacobi sweeps, released in pdep_destroy
+  EighGraphCache eig_graphs;
 };
 
 namespace {
@@ -519,6 +521,7 @@ int eigh_ws(pdep_ctx* c, int n, EighWork* wk) {
   RET(ws(c, "eig_t", (size_t)n * n + n, &wk->tmp));
   RET(ws(c, "eig_w", (size_t)n, &wk->w));
   RET(ws(c, "eig_f", (size_t)4, &wk->flag));
+  wk->graphs = &c->eig_graphs;
   return PDEP_OK;
 }
 
@@ -1384,6 +1387,7 @@ void pdep_destroy(pdep_ctx* c) {
   cudaGetDevice(&cur);
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
+  c->eig_graphs.release();
   for (auto& kv : c->bufs)
     if (kv.second.p) cudaFree(kv.second.p);
   for (void* p : c->owned) cudaFree(p);

@@ -7,13 +7,13 @@
 namespace pdep {
 
 static int num_sms() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
+  // queried once (thread-safe static initialisation); 152 on GB300
+  static const int n = [] {
+    int dev = 0, sms = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 132;
-  }
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 152;
+  }();
   return n;
 }
 
@@ -428,30 +428,24 @@ cudaError_t eigh(int n, const double* M, long long ldm, double* W, double* V, lo
   // One sweep = nn - 1 dependent rounds; they are replayed from a CUDA graph
   // captured once per (size, buffers) to avoid nn - 1 stream launches.
   cudaGraphExec_t sweep = nullptr;
-  if (nn - 1 > 8) {
-    struct Key {
-      int n;
-      const void *a, *v, *c;
-      cudaGraphExec_t exec;
-    };
-    static std::vector<Key> cache;
-    for (const Key& k : cache)
-      if (k.n == n && k.a == wk.a && k.v == wk.v && k.c == counter) sweep = k.exec;
+  if (nn - 1 > 8 && wk.graphs) {
+    for (const EighGraphCache::Entry& k : wk.graphs->entries)
+      if (k.n == n && k.a == wk.a && k.counter == counter) sweep = k.exec;
     if (!sweep) {
       cudaStream_t cap;
       cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
       if (e != cudaSuccess) return e;
-      cudaGraph_t g;
+      cudaGraph_t g = nullptr;
       e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-      if (e != cudaSuccess) return e;
-      for (int r = 0; r < nn - 1; ++r) round_k<<<jb, tpb, 0, cap>>>(wk.a, n, nn, r, counter);
-      e = cudaStreamEndCapture(cap, &g);
-      if (e != cudaSuccess) return e;
-      e = cudaGraphInstantiate(&sweep, g, 0);
-      cudaGraphDestroy(g);
+      if (e == cudaSuccess) {
+        for (int r = 0; r < nn - 1; ++r) round_k<<<jb, tpb, 0, cap>>>(wk.a, n, nn, r, counter);
+        e = cudaStreamEndCapture(cap, &g);
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&sweep, g, 0);
+      if (g) cudaGraphDestroy(g);
       cudaStreamDestroy(cap);
       if (e != cudaSuccess) return e;
-      cache.push_back(Key{n, wk.a, wk.v, counter, sweep});
+      wk.graphs->entries.push_back(EighGraphCache::Entry{n, wk.a, counter, sweep});
     }
   }
   unsigned hcount = 1;

@@ -4,6 +4,8 @@
 // the column-major ld x n matrix whose columns are the vectors.
 #pragma once
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace pdep {
@@ -23,12 +25,31 @@ cudaError_t gemm(bool transA, int m, int n, int k, double alpha, const R* A, lon
 // the eigenvalues their Rayleigh quotients with the original M, sorted
 // ascending.  W [n] eigenvalues, V [n x n] (ldv) vectors.
 // Work needs 2 n*n + 4 n doubles of device scratch.
+// Executable graphs of one Jacobi sweep (its nn - 1 dependent rounds), keyed
+// by the matrix size and the device buffers the rounds were captured with.
+// Owned by the caller (one per context, so calls on different contexts never
+// share it); release() destroys the graphs.
+struct EighGraphCache {
+  struct Entry {
+    int n;
+    const void* a;
+    const void* counter;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Entry> entries;
+  void release() {
+    for (Entry& e : entries) cudaGraphExecDestroy(e.exec);
+    entries.clear();
+  }
+};
+
 struct EighWork {
   double* a;      // n*n
   double* v;      // n*n
   double* tmp;    // n*n
   double* w;      // n (unsorted)
   int* flag;      // 1 int + 1 unsigned (rotation counter)
+  EighGraphCache* graphs = nullptr;  // sweeps replayed from graphs (null: plain launches)
 };
 cudaError_t eigh(int n, const double* M, long long ldm, double* W, double* V, long long ldv,
                  EighWork wk, cudaStream_t st, int max_sweeps = 40);
