@@ -21,7 +21,7 @@ def _declared():
 @pytest.fixture(scope="module")
 def lib():
     from paper_1501_03141_gb300 import _abi, build
-    build.build()
+    build.build(bounds_check=_abi.BOUNDS_CHECK)
     return _abi.load()
 
 
@@ -50,3 +50,22 @@ def test_host_only_calls(lib):
     # a null descriptor is rejected before any device work
     assert lib.pdep_setup(None, 0, None, None, ctypes.byref(h)) == _abi.PDEP_ERR_INVALID_ARG
     assert not h.value
+
+
+def test_null_context_and_bounds_flag(lib):
+    from paper_1501_03141_gb300 import _abi
+    assert lib.pdep_sync_status(None, None) == _abi.PDEP_ERR_INVALID_ARG
+    assert lib.pdep_bounds_checked() == (1 if _abi.BOUNDS_CHECK else 0)
+    assert "bounds" in lib.pdep_status_string(_abi.PDEP_ERR_BOUNDS).decode()
+
+
+def test_bounds_checked_variant_builds_and_exports():
+    """build(bounds_check=True) makes libpdep_check.so, compiled with the index
+    tests, exporting the same symbols (loaded side by side, host calls only)."""
+    from paper_1501_03141_gb300 import build
+    path = build.build(bounds_check=True)
+    assert os.path.basename(path) == "libpdep_check.so"
+    chk = ctypes.CDLL(path)
+    assert chk.pdep_bounds_checked() == 1
+    for name in _declared():
+        assert hasattr(chk, name), name
