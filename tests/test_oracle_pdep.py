@@ -5,7 +5,8 @@
 * chi0bar is symmetric and negative semi-definite (Eq. AdlerWiser at
   omega = 0: every term is -|p|^2 / (eps_c - eps_v));
 * chi0bar applied through Sternheimer solves equals the dense matrix;
-* invariance under V -> V + const;
+* invariance under V -> V + const and under rotations inside degenerate
+  shells;
 * planted mistakes in the oracle (a wrong Coulomb root, a dropped factor)
   are caught by these pins.
 """
@@ -63,6 +64,33 @@ def test_constant_shift_invariance():
     l1, _ = pdep_reference(chi0bar_dense(b, ks_states(b, v, 4)), 8)
     l2, _ = pdep_reference(chi0bar_dense(b, ks_states(b, v - 1.3, 4)), 8)
     np.testing.assert_allclose(l2, l1, rtol=1e-11)
+
+
+def test_degenerate_shell_rotation_invariance():
+    """chi0bar depends on the occupied and empty spaces, not on the basis chosen
+    inside a degenerate shell: random rotations of the six degenerate
+    |k| = 2 pi/L free-electron states (occupied) and of the twelve of the next
+    shell (empty) leave it unchanged, while the same rotation mixing occupied
+    and empty states does not."""
+    from oracle.hamiltonian import KSStates
+    b = Basis((12, 12, 12), (6.0, 6.0, 6.0))
+    ks = ks_states(b, np.zeros(b.grid), 7)
+    assert np.ptp(ks.eps[1:7]) < 1e-12 and np.ptp(ks.eps[7:19]) < 1e-12
+    ref = chi0bar_dense(b, ks)
+    rng = np.random.default_rng(5)
+    C = ks.C.copy()
+    for lo, hi in ((1, 7), (7, 19)):
+        q, _ = np.linalg.qr(rng.standard_normal((hi - lo, hi - lo)))
+        C[:, lo:hi] = C[:, lo:hi] @ q
+    rot = chi0bar_dense(b, KSStates(eps=ks.eps, C=C, n_occ=7))
+    scale = np.abs(ref).max()
+    assert np.abs(rot - ref).max() < 1e-13 * scale
+    # mixing an occupied state with an empty one changes the response
+    C2 = ks.C.copy()
+    c, s_ = np.cos(0.3), np.sin(0.3)
+    C2[:, [6, 7]] = C2[:, [6, 7]] @ np.array([[c, -s_], [s_, c]])
+    mixed = chi0bar_dense(b, KSStates(eps=ks.eps, C=C2, n_occ=7))
+    assert np.abs(mixed - ref).max() > 1e-3 * scale
 
 
 def test_tiny_reference_shape(tiny_chib, tiny_system):
