@@ -44,6 +44,13 @@ def pair_coefficients(basis: Basis, u_occ, u_emp_block):
     return c[:, :-1].reshape(nocc, nb, basis.n_pdep_dim)
 
 
+def resolvent_weight(den, nu: float):
+    """Weight of one (v, c) pair in the Adler-Wiser sum at omega = i nu (Sec.
+    II B, Eq. AdlerWiser): with den = eps_v - eps_c, each of its two
+    denominators contributes Re 1/(den +- i nu) = den / (den^2 + nu^2)."""
+    return den / (den * den + nu * nu)
+
+
 def chi0bar_dense(basis: Basis, ks: KSStates, block: int = 64, nu: float = 0.0) -> np.ndarray:
     """Dense chi0bar(i nu) on the PDEP sphere, shape (2 n_half, 2 n_half)."""
     nocc = ks.n_occ
@@ -56,7 +63,7 @@ def chi0bar_dense(basis: Basis, ks: KSStates, block: int = 64, nu: float = 0.0) 
         u_emp = basis.coeffs_to_grid(ks.C[:, c0:c1].T)
         p = pair_coefficients(basis, u_occ, u_emp)               # (nocc, nb, dim)
         den = ev[:, None] - ks.eps[c0:c1][None, :]              # eps_v - eps_c
-        pw = p * (den / (den * den + nu * nu))[:, :, None]
+        pw = p * resolvent_weight(den, nu)[:, :, None]
         chi0 += 4.0 * np.einsum("vcg,vch->gh", pw, p, optimize=True)
     vh = basis.sqrt_coulomb()
     chib = vh[:, None] * chi0 * vh[None, :]

@@ -7,7 +7,8 @@
   (chi0bar(i nu2) - chi0bar(i nu1) is NSD for nu2 < nu1);
 * B(0) in the PDEP basis is diag(lambda); Lambda = (1 - B)^{-1} B has the
   eigenvalues b/(1 - b) of B and shares its eigenvectors;
-* the free-electron Lambda(i nu) is diag(lambda/(1 - lambda)) of the closed form.
+* the free-electron Lambda(i nu) is diag(lambda/(1 - lambda)) of the closed form;
+* a planted sign mistake in the imaginary-frequency denominator is caught.
 """
 import numpy as np
 import pytest
@@ -60,3 +61,14 @@ def test_body_at_zero_and_lambda(tiny_oracle, tiny_chib, tiny_system):
     L = screening.lambda_body(B)
     mu, V = np.linalg.eigh(0.5 * (B + B.T))
     np.testing.assert_allclose(V.T @ L @ V, np.diag(mu / (1 - mu)), atol=1e-12)
+
+
+def test_planted_denominator_sign_is_caught(monkeypatch, free19):
+    """den/(den^2 - nu^2) in place of den/(den^2 + nu^2) fails the closed form."""
+    from oracle import pdep
+    b, ks = free19
+    nu = 1.0
+    lam = free_electron_chi0bar(b, 19, nu=nu)
+    monkeypatch.setattr(pdep, "resolvent_weight", lambda den, nu: den / (den * den - nu * nu))
+    chib = pdep.chi0bar_dense(b, ks, nu=nu)
+    assert np.abs(chib - np.diag(lam)).max() > 1e-2 * np.abs(lam).max()
