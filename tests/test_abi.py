@@ -69,3 +69,12 @@ def test_bounds_checked_variant_builds_and_exports():
     assert chk.pdep_bounds_checked() == 1
     for name in _declared():
         assert hasattr(chk, name), name
+
+
+def test_python_options_by_name(lib):
+    import paper_1501_03141_gb300 as pg
+    o = pg.default_options(cg_tol=1e-9, dav_max_iter=7, precision=pg.PDEP_MIXED)
+    assert o.cg_tol == 1e-9 and o.dav_max_iter == 7 and o.precision == pg.PDEP_MIXED
+    assert o.n_deflate == 16 and o.proj_variant == -1 and o.inner_tol == 1e-5
+    with pytest.raises(KeyError):
+        pg.default_options(cg_toll=1e-9)
