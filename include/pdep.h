@@ -42,16 +42,26 @@
  *     each pointer and stages host data through its own device workspace.
  *     The caller owns every argument buffer; the library owns the context and
  *     its workspace and frees them in pdep_destroy.
- *   - 'stream' is a cudaStream_t (NULL = legacy default stream).  Calls
- *     enqueue work on it and return once their results are complete in the
- *     output buffers (the Sternheimer and Davidson loops read convergence
- *     flags from the device between steps).
+ *   - 'stream' is a cudaStream_t (NULL = legacy default stream).
+ *     chi0_apply and sternheimer_solve only enqueue work on it when every
+ *     array argument is a device buffer: the Sternheimer CG loops and the
+ *     mixed-precision refinement rounds are driven on the device, and
+ *     nothing is read back; results are valid once the stream has been
+ *     synchronised.  With a host buffer among the arguments the call copies
+ *     through its workspace and synchronises before returning.  pdep_solve
+ *     reads the Ritz values and residual norms back once per Davidson
+ *     iteration (convergence test, correction choice) and synchronises at
+ *     its end; the other calls synchronise before returning.
  *   - Every function returns a pdep_status.  pdep_last_error() gives a
  *     human-readable message for the most recent failure in this thread.
- *     Device-detected conditions (a non-finite CG scalar, a solve that hit
- *     its iteration cap) are returned as PDEP_ERR_NONFINITE /
- *     PDEP_ERR_NOT_CONVERGED by the call that detected them; outputs are
- *     still written.
+ *     Argument and launch errors are returned by the call.  Device-detected
+ *     conditions (a non-finite CG scalar, a solve that ended above cg_tol,
+ *     a spent clock budget) are OR-ed into a per-context device status word;
+ *     a synchronising call (one with host outputs, pdep_solve,
+ *     pdep_get_stats, pdep_sync_status) returns them as PDEP_ERR_NONFINITE,
+ *     PDEP_ERR_TIMEOUT or PDEP_ERR_NOT_CONVERGED and clears the word, so the
+ *     condition may stem from any call enqueued since the last such read.
+ *     Outputs are written in every one of these cases.
  *   - One GPU (the device current when pdep_setup is called).  Calls on one
  *     context must not run concurrently.
  */
@@ -74,18 +84,25 @@ typedef enum {
   PDEP_ERR_NO_GAP = 4,        /* eps_{n_occ+1} - eps_{n_occ} < gap_min */
   PDEP_ERR_NOT_CONVERGED = 5, /* a solve reached its iteration cap */
   PDEP_ERR_NONFINITE = 6,     /* NaN/Inf met in the data or a CG scalar */
-  PDEP_ERR_TIMEOUT = 7,       /* reserved: no device loop waits on another agent */
+  PDEP_ERR_TIMEOUT = 7,       /* a CG loop spent its clock_budget_cycles */
   PDEP_ERR_UNSUPPORTED = 8,   /* option combination not implemented */
   PDEP_ERR_BOUNDS = 9         /* bounds-checked builds: a kernel met an index outside
                                  the sphere tables and skipped the access */
 } pdep_status;
 
 typedef enum {
-  PDEP_FP64 = 0,  /* every step in FP64 */
-  PDEP_MIXED = 1  /* FP32 FFTs, H*psi and projections inside the Sternheimer
-                     CG, FP64 residual refinement, FP64 density response,
-                     orthogonalisation and Rayleigh-Ritz */
+  PDEP_FP64 = 0,       /* every step in FP64 */
+  PDEP_MIXED_TF32 = 1, /* FP32 FFTs, H*psi and vector updates inside the
+                          Sternheimer CG, its projection term on the tensor
+                          cores (TF32 operands split in three for FP32
+                          accuracy, FP32 accumulation); FP64 residual
+                          refinement, density response, orthogonalisation and
+                          Rayleigh-Ritz */
+  PDEP_MIXED_BF16 = 2  /* as PDEP_MIXED_TF32 with the projection term from BF16
+                          operands (each FP32 value split in three BF16 parts,
+                          FP32 accumulation) */
 } pdep_precision;
+#define PDEP_MIXED PDEP_MIXED_TF32 /* the default mixed mode */
 
 /* One system. v_r: [N1*N2*N3] local potential (Ha), host or device. */
 typedef struct {
@@ -121,7 +138,25 @@ typedef struct {
   int proj_variant;          /* kernel of the FP32 (mixed-mode CG) projection term
                                 sum_w sigma_w |w><w| x: -1 = autotuned (default; the
                                 first large calls time both), 0 = FP32 CUDA-core GEMMs,
-                                1 = tensor-core 3xTF32 GEMMs (FP32 accuracy). */
+                                1 = tensor-core GEMMs of the precision mode. */
+  long long clock_budget_cycles; /* device time budget of every CG loop, in SM clock
+                                cycles at the device's rated clock (0 = none).  A loop
+                                whose budget runs out with unconverged RHS stops after
+                                its current step and sets PDEP_ERR_TIMEOUT in the device
+                                status word (outputs are still written). */
+  int autotune;              /* 1 (default): the first large CG loops of a context time
+                                the CG-step launch shapes and the projection kernels and
+                                keep the fastest; 0: fixed defaults */
+  int use_graph;             /* 1 (default): each Sternheimer CG loop runs as one CUDA
+                                graph with a device-driven while node (no host round trip
+                                per step) once the autotuner has fixed the launch shapes;
+                                0: a host loop that reads the loop state after every step */
+  int df_refine;             /* mixed modes: 1 (default) = the refinement's A delta (and the
+                                density response accumulated with it) through transforms in
+                                double-float arithmetic (pairs of FP32 numbers, about 48
+                                significant bits; the FP32 pipe runs 64x the FP64 rate),
+                                vectors, residuals and projections in FP64; 0 = FP64
+                                transforms */
 } pdep_options;
 
 typedef struct {
@@ -136,6 +171,10 @@ typedef struct {
   double seconds;               /* wall time of the call */
   int cg_variant;               /* CG-step launch shape the autotuner chose (-1: untuned) */
   int proj_variant;             /* FP32 projection kernel in use (-1: untuned, 0, 1) */
+  int chi0_chunks;              /* perturbation chunks of the last chi0bar application */
+  long long kernel_launches;    /* library kernels the call ran, those inside CUDA graphs
+                                   included (graph steps counted on the device) */
+  long long graph_launches;     /* CG-loop graphs launched */
 } pdep_stats;
 
 /* Fill *opt with the defaults (FP64, cg_tol 1e-10, dav_tol 1e-8, ...). */
@@ -266,8 +305,11 @@ int pdep_lanczos(pdep_ctx* ctx, int sys, const double* R, int n, int n_steps, co
 
 /* y = H x for n sphere vectors x [n][n_pw] -> y [n][n_pw], H = -nabla^2/2 + V
  * (the local-potential Hamiltonian of the setup), evaluated with the pruned
- * sphere <-> grid transforms; precision PDEP_FP64 or PDEP_MIXED (FP32
- * transforms).  This is the H*psi kernel the Sternheimer CG applies. */
+ * sphere <-> grid transforms; precision PDEP_FP64, PDEP_MIXED (FP32
+ * transforms) or PDEP_APPLY_DF64 (double-float transforms on FP64 vectors,
+ * those of the mixed modes' refinement).  This is the H*psi kernel the
+ * Sternheimer CG applies. */
+#define PDEP_APPLY_DF64 3
 int pdep_apply_hamiltonian(pdep_ctx* ctx, int sys, const double* x, int n, double* y,
                            int precision, void* stream);
 
@@ -307,7 +349,7 @@ int pdep_to_grid(pdep_ctx* ctx, int sys, const double* x, int n, double* u, void
  * waits for the recorded events and fills *out (may be NULL).  flops and
  * bytes are the algorithmic counts of the launches (complex line FFT:
  * 5 L log2 L flops; bytes: every input read and output written once). */
-#define PDEP_PROFILE_CLASSES 11
+#define PDEP_PROFILE_CLASSES 15
 typedef struct {
   char name[24];
   long long launches;
@@ -322,13 +364,22 @@ typedef struct {
 int pdep_profile(int enable, pdep_profile_t* out);
 
 /* Device status word.  Kernels OR condition bits into a per-context word
- * (non-finite CG scalar, CG breakdown, and in bounds-checked builds an index
- * outside the sphere tables).  The Sternheimer solves and pdep_setup read it
- * after their last launch; pdep_sync_status synchronises 'stream', returns
- * the condition of the word (PDEP_OK, PDEP_ERR_NONFINITE or PDEP_ERR_BOUNDS)
- * for every call enqueued so far, and clears it.  PDEP_ERR_INVALID_ARG for a
- * NULL context. */
+ * (non-finite CG scalar, CG breakdown, a solve that ended above cg_tol, a
+ * spent clock budget, and in bounds-checked builds an index outside the
+ * sphere tables).  pdep_sync_status synchronises 'stream', returns the
+ * condition of the word (PDEP_OK, PDEP_ERR_NONFINITE, PDEP_ERR_BOUNDS,
+ * PDEP_ERR_TIMEOUT or PDEP_ERR_NOT_CONVERGED, in that priority) for every
+ * call enqueued since the last synchronising read, and clears it.
+ * PDEP_ERR_INVALID_ARG for a NULL context. */
 int pdep_sync_status(pdep_ctx* ctx, void* stream);
+
+/* Statistics of the last chi0_apply, sternheimer_solve, pdep_solve or
+ * pdep_chibar_apply on this context (*stats, host): synchronises 'stream',
+ * reads the device-side counters (CG iterations, residuals, refinement
+ * rounds, kernel launches) and returns the device status word's condition
+ * (then cleared) as pdep_sync_status does.  dav_* fields are those of the
+ * last pdep_solve. */
+int pdep_get_stats(pdep_ctx* ctx, pdep_stats* stats, void* stream);
 
 /* 1 if this library was compiled with -DPDEP_BOUNDS_CHECK (every index read
  * from the host-built sphere tables is tested before use in the transform

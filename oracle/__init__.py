@@ -27,6 +27,10 @@ real orbitals:
 * ``lanczos``     Lanczos chains of the deflated Hamiltonian P_c H P_c and the
                   omega-independent poles and weights of M_c(omega) (Sec. II D,
                   Eqs. MCdef, MCfinal), and the exact sum over empty states.
+* ``iterative``   the same Kohn-Sham states, Sternheimer solutions and chi0bar
+                  phi without dense matrices (Lanczos eigensolver and
+                  preconditioned block CG on the grid-applied H), for systems
+                  whose dense H does not fit (the 64x64x192 interface).
 
 Pins (tests/test_oracle_*.py): free-electron closed form, finite-difference
 density and second-order band-energy response, brute-force matrix elements,
@@ -34,4 +38,4 @@ Sternheimer = sum over states, symmetry, negative semi-definiteness,
 charge neutrality, invariance under V -> V + const.  The paper prints no
 worked numerical example for this path, so no pin uses printed values.
 """
-from . import basis, hamiltonian, response, pdep, screening, lanczos  # noqa: F401
+from . import basis, hamiltonian, response, pdep, screening, lanczos, iterative  # noqa: F401

@@ -13,7 +13,8 @@ import ctypes
 import numpy as np
 
 from . import _abi
-from ._abi import PDEP_FP64, PDEP_MIXED, PdepError  # noqa: F401
+from ._abi import PDEP_FP64, PDEP_MIXED, PDEP_MIXED_BF16, PDEP_MIXED_TF32, PdepError  # noqa: F401
+from ._abi import PDEP_APPLY_DF64  # noqa: F401
 from ._abi import PDEP_SCREEN_CHIBAR, PDEP_SCREEN_EPSINV, PDEP_SCREEN_WP  # noqa: F401
 
 SCREEN_KINDS = {"chibar": PDEP_SCREEN_CHIBAR, "epsinv": PDEP_SCREEN_EPSINV, "wp": PDEP_SCREEN_WP}
@@ -149,19 +150,37 @@ class Context:
                                           _stream(self.stream)), "pdep_to_grid")
         return out
 
+    def stats(self):
+        """Statistics of the last hot-path call (pdep_get_stats; synchronises the
+        stream and raises PdepError on a pending device condition other than
+        'not converged')."""
+        st = _abi.pdep_stats()
+        r = self._lib.pdep_get_stats(self._h, ctypes.byref(st), _stream(self.stream))
+        _abi.check(r, "pdep_get_stats", (_abi.PDEP_OK, _abi.PDEP_ERR_NOT_CONVERGED))
+        return {k: getattr(st, k) for k, _ in _abi.pdep_stats._fields_}
+
+    def _finish(self, status, where, allow, bufs, sync):
+        """With device buffers only the library call just enqueued the work:
+        unless sync is False, wait and read the device status word here."""
+        _abi.check(status, where, allow)
+        if sync and all(b is None or not isinstance(b, np.ndarray) and b.is_cuda for b in bufs):
+            _abi.check(self._lib.pdep_sync_status(self._h, _stream(self.stream)), where, allow)
+
     # -- hot path ------------------------------------------------------------
-    def chi0_apply(self, phi, sys: int = 0, out=None, dn=None, allow_unconverged=False):
-        """chi0bar phi for phi [n_pert, n_pdep_dim]; returns out (and dn if given)."""
+    def chi0_apply(self, phi, sys: int = 0, out=None, dn=None, allow_unconverged=False, sync=True):
+        """chi0bar phi for phi [n_pert, n_pdep_dim]; returns out (and dn if given).
+        With CUDA tensors and sync=False the call only enqueues on the stream."""
         n_pert = int(phi.shape[0])
         if out is None:
             out = np.empty_like(phi) if isinstance(phi, np.ndarray) else phi.new_empty(phi.shape)
         allow = (_abi.PDEP_OK, _abi.PDEP_ERR_NOT_CONVERGED) if allow_unconverged else (_abi.PDEP_OK,)
-        _abi.check(self._lib.chi0_apply(self._h, sys, _abi.ptr(phi), n_pert, _abi.ptr(out),
-                                        _abi.ptr(dn), _stream(self.stream)), "chi0_apply", allow)
+        r = self._lib.chi0_apply(self._h, sys, _abi.ptr(phi), n_pert, _abi.ptr(out), _abi.ptr(dn),
+                                 _stream(self.stream))
+        self._finish(r, "chi0_apply", allow, (phi, out, dn), sync)
         return out
 
     def sternheimer_solve(self, dv, sys: int = 0, dpsi=None, iters=None, resid=None,
-                          allow_unconverged=False):
+                          allow_unconverged=False, sync=True):
         """P_c dpsi for dv [n_pert, n_r]; returns (dpsi [n_pert, n_occ, n_pw], iters, resid)."""
         n_pert = int(dv.shape[0])
         sz = self.sizes(sys)
@@ -173,9 +192,9 @@ class Context:
         if resid is None:
             resid = np.empty(n_pert * s.n_occ)
         allow = (_abi.PDEP_OK, _abi.PDEP_ERR_NOT_CONVERGED) if allow_unconverged else (_abi.PDEP_OK,)
-        _abi.check(self._lib.sternheimer_solve(self._h, sys, _abi.ptr(dv), n_pert, _abi.ptr(dpsi),
-                                               _abi.ptr(iters), _abi.ptr(resid),
-                                               _stream(self.stream)), "sternheimer_solve", allow)
+        r = self._lib.sternheimer_solve(self._h, sys, _abi.ptr(dv), n_pert, _abi.ptr(dpsi),
+                                        _abi.ptr(iters), _abi.ptr(resid), _stream(self.stream))
+        self._finish(r, "sternheimer_solve", allow, (dv, dpsi, iters, resid), sync)
         return dpsi, iters, resid
 
     def pdep_solve(self, sys: int = 0, phi0=None, eigvals=None, eigvecs=None,

@@ -28,7 +28,10 @@ PDEP_ERR_UNSUPPORTED = 8
 PDEP_ERR_BOUNDS = 9
 
 PDEP_FP64 = 0
-PDEP_MIXED = 1
+PDEP_MIXED_TF32 = 1
+PDEP_MIXED_BF16 = 2
+PDEP_MIXED = PDEP_MIXED_TF32
+PDEP_APPLY_DF64 = 3   # pdep_apply_hamiltonian: double-float transforms
 
 PDEP_SCREEN_CHIBAR = 0
 PDEP_SCREEN_EPSINV = 1
@@ -40,10 +43,10 @@ EXPORTS = (
     "chi0_apply", "sternheimer_solve", "pdep_solve", "pdep_apply_hamiltonian", "pdep_to_grid",
     "pdep_profile", "pdep_destroy", "pdep_status_string", "pdep_last_error",
     "pdep_apply_hamiltonian_noalloc", "pdep_screening_apply", "pdep_lanczos", "pdep_chi0_imag",
-    "pdep_chibar_apply", "pdep_sync_status", "pdep_bounds_checked",
+    "pdep_chibar_apply", "pdep_sync_status", "pdep_bounds_checked", "pdep_get_stats",
 )
 
-PDEP_PROFILE_CLASSES = 11
+PDEP_PROFILE_CLASSES = 15
 
 
 class pdep_system_desc(ctypes.Structure):
@@ -75,6 +78,10 @@ class pdep_options(ctypes.Structure):
         ("workspace_limit_bytes", ctypes.c_size_t),
         ("n_deflate", ctypes.c_int),
         ("proj_variant", ctypes.c_int),
+        ("clock_budget_cycles", ctypes.c_longlong),
+        ("autotune", ctypes.c_int),
+        ("use_graph", ctypes.c_int),
+        ("df_refine", ctypes.c_int),
     ]
 
 
@@ -91,6 +98,9 @@ class pdep_stats(ctypes.Structure):
         ("seconds", ctypes.c_double),
         ("cg_variant", ctypes.c_int),
         ("proj_variant", ctypes.c_int),
+        ("chi0_chunks", ctypes.c_int),
+        ("kernel_launches", ctypes.c_longlong),
+        ("graph_launches", ctypes.c_longlong),
     ]
 
 
@@ -152,11 +162,12 @@ def load(path: str = LIB_PATH):
     lib.pdep_last_error.argtypes = []
     lib.pdep_last_error.restype = ctypes.c_char_p
     lib.pdep_sync_status.argtypes = [vp, vp]
+    lib.pdep_get_stats.argtypes = [vp, ctypes.POINTER(pdep_stats), vp]
     lib.pdep_bounds_checked.argtypes = []
     for name in ("pdep_setup", "pdep_get_sizes", "pdep_get_occupied", "chi0_apply",
                  "sternheimer_solve", "pdep_solve", "pdep_apply_hamiltonian", "pdep_to_grid",
                  "pdep_screening_apply", "pdep_lanczos", "pdep_chi0_imag",
-                 "pdep_chibar_apply", "pdep_sync_status", "pdep_bounds_checked"):
+                 "pdep_chibar_apply", "pdep_sync_status", "pdep_bounds_checked", "pdep_get_stats"):
         getattr(lib, name).restype = ip
     del dp
     _lib = lib

@@ -15,6 +15,7 @@
 
 #include "common.cuh"
 #include "linalg.cuh"
+#include "profile.cuh"
 #include "transforms.cuh"
 
 namespace pdep {
@@ -78,8 +79,11 @@ struct SysData {
   double* d_g2 = nullptr;
   cpx<double>* d_tw64[3] = {nullptr, nullptr, nullptr};
   cpx<float>* d_tw32[3] = {nullptr, nullptr, nullptr};
+  cpx<df>* d_twdf[3] = {nullptr, nullptr, nullptr};
   double* d_v = nullptr;
   float* d_vf = nullptr;
+  df* d_vdf = nullptr;       // V(r) in double-float (refinement transforms)
+  df* d_kindf = nullptr;
   double* d_psi = nullptr;   // [n_occ][ld]
   float* d_psif = nullptr;
   double* d_u = nullptr;     // [n_occ][n_r]  u_v(r) = Omega^{1/2} psi_v(r)
@@ -94,6 +98,7 @@ struct SysData {
   double vmax = 0;           // max_r V(r)
   SphereDev<double> sd{};
   SphereDev<float> sf{};
+  SphereDev<df> sdf{};
 };
 
 }  // namespace pdep
@@ -105,6 +110,16 @@ struct DevBuf {
   size_t cap = 0;
 };
 
+// One captured Sternheimer CG loop (prologue + while node over the steps),
+// valid for the buffers and settings it was captured with.
+struct CgGraph {
+  int prec, sys, n, max_iter, cg_variant, proj_variant;
+  double tol;
+  const void *b, *x, *sc, *mask;
+  unsigned long long ws_gen, budget_ns;
+  cudaGraphExec_t exec;
+};
+
 struct pdep_ctx {
   int device = 0;
   pdep_options opt{};
@@ -114,11 +129,25 @@ struct pdep_ctx {
   std::vector<void*> owned;
   unsigned* d_status = nullptr;
   int* d_counter = nullptr;
+  // device-side loop state and statistics of the Sternheimer solves
+  CgLoopState* d_loop = nullptr;
+  DevStats* d_dstats = nullptr;
+  int* d_refine = nullptr;        // [0]: unconverged count of the current refinement round
+  cudaStream_t cap_stream = nullptr;  // private stream the CG graphs are captured on
+  unsigned long long ws_gen = 0;  // bumped whenever a workspace buffer is reallocated
+  unsigned long long budget_ns = 0;   // clock_budget_cycles in ns of %globaltimer
+  std::vector<CgGraph> cg_graphs;     // executable CG-loop graphs, released in pdep_destroy
+  int body_launches[2] = {0, 0};      // kernels per CG step in the graphs (FP32, FP64)
+  long long graph_launches = 0;       // CG graphs launched
+  long long eager_steps[2] = {0, 0};  // CG steps launched from the host loop (FP32, FP64)
+  long long st_launch0 = 0;           // launch counter at the last statistics reset
+  pdep_stats last_dav{};              // statistics of the last pdep_solve
   cudaEvent_t ev[2] = {nullptr, nullptr};
   int* h_pin = nullptr;  // pinned host scratch (ints)
   // statistics of the current call
   long long st_solves = 0, st_cg_iters = 0;
   int st_cg_max = 0, st_refine_max = 0;
+  int st_chunks = 0;  // perturbation chunks of the last chi0bar application
   double st_max_res = 0;
   // autotuned launch shape of the CG step, per precision (-1: not tuned yet)
   int cg_variant[2] = {-1, -1};
@@ -170,6 +199,7 @@ int ws(pdep_ctx* c, const char* name, size_t count, T** out) {
     }
     b.cap = newcap;
     c->ws_bytes += newcap;
+    ++c->ws_gen;  // graphs captured with the old buffer are stale now
   }
   *out = (T*)b.p;
   return PDEP_OK;
@@ -208,21 +238,20 @@ int sync(cudaStream_t st) {
   return PDEP_OK;
 }
 
-int read_int(pdep_ctx* c, const int* d, int* h, cudaStream_t st) {
-  CK(cudaMemcpyAsync(c->h_pin, d, sizeof(int), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  *h = *c->h_pin;
-  return PDEP_OK;
-}
-
+// Synchronises st, reads the device status word and clears it: the
+// conditions of every call enqueued since the last read.
 int check_status(pdep_ctx* c, cudaStream_t st) {
   unsigned h = 0;
   CK(cudaMemcpyAsync(c->h_pin, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), st));
   CK(cudaStreamSynchronize(st));
   memcpy(&h, c->h_pin, sizeof(unsigned));
   if (h & DEV_NONFINITE) return fail(PDEP_ERR_NONFINITE, "non-finite value met on the device");
   if (h & DEV_BREAKDOWN) return fail(PDEP_ERR_NONFINITE, "CG breakdown (p.Ap <= 0)");
   if (h & DEV_BOUNDS) return fail(PDEP_ERR_BOUNDS, "sphere-table index out of range");
+  if (h & DEV_TIMEOUT) return fail(PDEP_ERR_TIMEOUT, "a CG loop spent its clock budget");
+  if (h & DEV_NOT_CONVERGED)
+    return fail(PDEP_ERR_NOT_CONVERGED, "a Sternheimer solve ended above cg_tol");
   return PDEP_OK;
 }
 
@@ -329,25 +358,32 @@ int upload_tables(pdep_ctx* c, SysData& s) {
       k64[k] = 0.5 * s.g2[k];
       k32[k] = (float)k64[k];
     }
+    std::vector<df> kdf(k64.begin(), k64.end());
     RET(persistent(c, &s.d_kin64, k64.size()));
     RET(persistent(c, &s.d_kin32, k32.size()));
+    RET(persistent(c, &s.d_kindf, kdf.size()));
     CK(cudaMemcpy(s.d_kin64, k64.data(), sizeof(double) * k64.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(s.d_kin32, k32.data(), sizeof(float) * k32.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(s.d_kindf, kdf.data(), sizeof(df) * kdf.size(), cudaMemcpyHostToDevice));
   }
   const double two_pi = 6.283185307179586476925286766559;
   for (int a = 0; a < 3; ++a) {
     const int N = s.N[a];
     std::vector<cpx<double>> td(N);
     std::vector<cpx<float>> tf(N);
+    std::vector<cpx<df>> tdf(N);
     for (int j = 0; j < N; ++j) {
       double ang = two_pi * j / N;
       td[j] = mk(cos(ang), sin(ang));
       tf[j] = mk((float)cos(ang), (float)sin(ang));
+      tdf[j] = mk(df(cos(ang)), df(sin(ang)));
     }
     RET(persistent(c, &s.d_tw64[a], N));
     RET(persistent(c, &s.d_tw32[a], N));
+    RET(persistent(c, &s.d_twdf[a], N));
     CK(cudaMemcpy(s.d_tw64[a], td.data(), sizeof(cpx<double>) * N, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(s.d_tw32[a], tf.data(), sizeof(cpx<float>) * N, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(s.d_twdf[a], tdf.data(), sizeof(cpx<df>) * N, cudaMemcpyHostToDevice));
   }
   auto fill = [&](auto& d, auto tw) {
     d.N1 = s.N[0];
@@ -370,16 +406,20 @@ int upload_tables(pdep_ctx* c, SysData& s) {
   };
   fill(s.sd, s.d_tw64);
   fill(s.sf, s.d_tw32);
+  fill(s.sdf, s.d_twdf);
   s.sd.kin = s.d_kin64;
   s.sf.kin = s.d_kin32;
+  s.sdf.kin = s.d_kindf;
   return PDEP_OK;
 }
 
 // precision selectors
 inline const SphereDev<double>& sph(const SysData& s, double*) { return s.sd; }
 inline const SphereDev<float>& sph(const SysData& s, float*) { return s.sf; }
+inline const SphereDev<df>& sph(const SysData& s, df*) { return s.sdf; }
 inline const double* vgrid(const SysData& s, double*) { return s.d_v; }
 inline const float* vgrid(const SysData& s, float*) { return s.d_vf; }
+inline const df* vgrid(const SysData& s, df*) { return s.d_vdf; }
 inline const double* psi_of(const SysData& s, double*) { return s.d_psi; }
 inline const float* psi_of(const SysData& s, float*) { return s.d_psif; }
 inline const double* kprec_of(const SysData& s, double*) { return s.d_kprec64; }
@@ -400,26 +440,33 @@ size_t b1_count(const SysData& s, int n_items) {
 // dn (FP64 only, may be null): the transform also accumulates the density
 // response dn_j(r) += (4/Omega) u_v(r) x_i(r) of every vector i = j n_occ + v
 // it transforms (Eq. deltani); dn must hold the (i / n_occ) perturbations.
-template <typename R>
+// d_count (with d_list): device length of the list; n_list is then the
+// largest length, which sizes the launches (kernels read the count).
+// C is the arithmetic type of the transforms (float, double, or df: double-
+// float on FP32 vectors... on FP64 vectors); the vectors and the projection
+// term use its storage type R (FP64 for df).
+template <typename C, typename R = typename Io<C>::T>
 int apply_h(pdep_ctx* c, SysData& s, const R* X, R* Y, int n, const int* d_list, int n_list,
-            bool with_shift, bool with_pv, cudaStream_t st, double* dn = nullptr) {
+            bool with_shift, bool with_pv, cudaStream_t st, double* dn = nullptr,
+            const int* d_count = nullptr) {
   ItemMap map{n, (n + 1) / 2};
   int n_items = (n + 1) / 2;
   if (d_list) {
     map.list = d_list;
     map.n_list = n_list;
+    map.n_dev = d_count;
     n_items = (n_list + 1) / 2;
   }
   if (n_items > 0) {
-    cpx<R>* b1;
-    RET(ws(c, sizeof(R) == 8 ? "b1_64" : "b1_32", b1_count(s, n_items), &b1));
-    const SphereDev<R>& sd = sph(s, (R*)nullptr);
-    CK(launch_cols_fwd<R>(sd, X, s.ld, map, n_items, COEF_ONE, b1, st));
-    SlabArgs<R> a{};
+    cpx<C>* b1;   // double-float shares the FP64 scratch (16 bytes per complex)
+    RET(ws(c, sizeof(C) == 8 ? "b1_64" : "b1_32", b1_count(s, n_items), &b1));
+    const SphereDev<C>& sd = sph(s, (C*)nullptr);
+    CK(launch_cols_fwd<C>(sd, X, s.ld, map, n_items, COEF_ONE, b1, st));
+    SlabArgs<C> a{};
     a.mode = SLAB_HPSI;
     a.b1 = b1;
     a.n_items = n_items;
-    a.v = vgrid(s, (R*)nullptr);
+    a.v = vgrid(s, (C*)nullptr);
     a.map = map;
     if (dn) {
       a.dn = dn;
@@ -428,19 +475,19 @@ int apply_h(pdep_ctx* c, SysData& s, const R* X, R* Y, int n, const int* d_list,
       a.dn_stride = s.n_r;
       a.dn_scale = 4.0 / s.omega;
     }
-    CK(launch_slab<R>(sd, a, st));
-    Epilogue<R> ep{};
+    CK(launch_slab<C>(sd, a, st));
+    Epilogue<C> ep{};
     ep.y = Y;
     ep.ldy = s.ld;
     ep.x_in = X;
     ep.ldx = s.ld;
     ep.shift = with_shift ? negeps_of(s, (R*)nullptr) : nullptr;
     ep.shift_period = with_shift ? s.n_occ : 1;
-    ep.scale = (R)(1.0 / s.n_r);
-    ep.kin = R(1);
+    ep.scale = C(1.0 / s.n_r);
+    ep.kin = C(1);
     ep.beta = R(0);
     ep.coef = COEF_ONE;
-    CK(launch_cols_bwd<R>(sd, b1, map, n_items, ep, st));
+    CK(launch_cols_bwd<C>(sd, b1, map, n_items, ep, st));
   }
   if (with_pv) {
     // only the listed columns when a list is given
@@ -450,7 +497,7 @@ int apply_h(pdep_ctx* c, SysData& s, const R* X, R* Y, int n, const int* d_list,
       // While untuned, calls with many columns alternate the two and keep
       // their time per column; afterwards the faster one is used.
       int pv = c->opt.proj_variant >= 0 ? c->opt.proj_variant : c->proj_variant;
-      const bool tuning = pv < 0 && m >= 256;
+      const bool tuning = c->opt.autotune && pv < 0 && m >= 256;
       if (pv < 0) pv = tuning ? c->proj_tune_next : 1;
       if (tuning) CK(cudaEventRecord(c->ev[0], st));
       if (pv == 1) {
@@ -458,16 +505,17 @@ int apply_h(pdep_ctx* c, SysData& s, const R* X, R* Y, int n, const int* d_list,
         float* S;
         RET(ws(c, "pv_32", (size_t)lds * std::max(m, 1), &S));
         CK(tc_proj_coeffs(s.n_ext, m, s.n_pw, s.d_psif, s.ld, X, s.ld, d_list, s.d_sigma32, S, lds,
-                          st));
-        CK(tc_proj_update(s.n_pw, m, s.n_ext, s.d_psif, s.ld, S, lds, Y, s.ld, d_list, st));
+                          st, d_count));
+        CK(tc_proj_update(s.n_pw, m, s.n_ext, s.d_psif, s.ld, S, lds, Y, s.ld, d_list, st,
+                          d_count));
       } else {
         float* S;
         RET(ws(c, "pv_32", (size_t)s.n_ext * std::max(m, 1), &S));
         CK(gemm<float>(true, s.n_ext, m, s.n_pw, 1.0, s.d_psif, s.ld, X, s.ld, 0.0, S, s.n_ext,
-                       st, d_list, nullptr));
+                       st, d_list, nullptr, d_count));
         CK(scale_rows<float>(S, s.n_ext, s.n_ext, m, s.d_sigma32, st));
         CK(gemm<float>(false, s.n_pw, m, s.n_ext, 1.0, s.d_psif, s.ld, S, s.n_ext, 1.0, Y, s.ld,
-                       st, nullptr, d_list));
+                       st, nullptr, d_list, d_count));
       }
       if (tuning) {
         CK(cudaEventRecord(c->ev[1], st));
@@ -488,10 +536,10 @@ int apply_h(pdep_ctx* c, SysData& s, const R* X, R* Y, int n, const int* d_list,
     RET(ws(c, sizeof(R) == 8 ? "pv_64" : "pv_32", (size_t)s.n_ext * std::max(m, 1), &S));
     const R* P = psi_of(s, (R*)nullptr);
     CK(gemm<R>(true, s.n_ext, m, s.n_pw, 1.0, P, s.ld, X, s.ld, 0.0, S, s.n_ext, st, d_list,
-               nullptr));
+               nullptr, d_count));
     CK(scale_rows<R>(S, s.n_ext, s.n_ext, m, sigma_of(s, (R*)nullptr), st));
     CK(gemm<R>(false, s.n_pw, m, s.n_ext, 1.0, P, s.ld, S, s.n_ext, 1.0, Y, s.ld, st, nullptr,
-               d_list));
+               d_list, d_count));
   }
   return PDEP_OK;
 }
@@ -907,18 +955,137 @@ int setup_states(pdep_ctx* c, SysData& s, cudaStream_t st) {
 // on that subspace: H commutes with the projector, so x has no component
 // along any w; the deflated states' share is added exactly, see split_rhs)
 // ---------------------------------------------------------------------------
+// The CG step's launch shape and the FP32 projection kernel are fixed once
+// the autotuner has timed them (or autotuning is off); only then is the loop
+// captured in a graph.
+bool tuned(const pdep_ctx* c, int pi) {
+  if (!c->opt.autotune) return true;
+  const bool pv_ok = pi == 1 || c->opt.proj_variant >= 0 || c->proj_variant >= 0;
+  return c->cg_variant[pi] >= 0 && pv_ok;
+}
+int cg_variant_of(const pdep_ctx* c, int pi) {
+  return c->cg_variant[pi] >= 0 ? c->cg_variant[pi] : (int)CG_STREAM256;
+}
+
+// Workspace the step of a CG loop over n RHS needs (allocated before a
+// capture, so that nothing is allocated while capturing).
 template <typename R>
-int cg_loop(pdep_ctx* c, SysData& s, const R* b, R* x, int n, double tol, int max_iter,
-            CgScal* sc, cudaStream_t st, bool* hit_cap) {
-  R *r, *p, *ap;
-  int* list;
+int cg_workspace(pdep_ctx* c, SysData& s, int n, R** r, R** p, R** ap, int** list) {
   const char* tag = sizeof(R) == 8 ? "64" : "32";
   std::string nr = std::string("cg_r") + tag, np = std::string("cg_p") + tag,
               na = std::string("cg_ap") + tag;
-  RET(ws(c, nr.c_str(), (size_t)n * s.ld, &r));
-  RET(ws(c, np.c_str(), (size_t)n * s.ld, &p));
-  RET(ws(c, na.c_str(), (size_t)n * s.ld, &ap));
-  RET(ws(c, "cg_list", (size_t)n, &list));
+  RET(ws(c, nr.c_str(), (size_t)n * s.ld, r));
+  RET(ws(c, np.c_str(), (size_t)n * s.ld, p));
+  RET(ws(c, na.c_str(), (size_t)n * s.ld, ap));
+  RET(ws(c, "cg_list", (size_t)n, list));
+  cpx<R>* b1;
+  RET(ws(c, sizeof(R) == 8 ? "b1_64" : "b1_32", b1_count(s, (n + 1) / 2), &b1));
+  const int pv = c->opt.proj_variant >= 0 ? c->opt.proj_variant : c->proj_variant;
+  R* S;
+  if (sizeof(R) == 4 && pv != 0) {
+    RET(ws(c, "pv_32", (size_t)((s.n_ext + 3) & ~3) * std::max(n, 1), &S));
+  } else {
+    RET(ws(c, sizeof(R) == 8 ? "pv_64" : "pv_32", (size_t)s.n_ext * std::max(n, 1), &S));
+  }
+  return PDEP_OK;
+}
+
+// Captures one CG loop over n RHS into an executable graph:
+//   prologue: active = 0, cg_start (r = b, p = K b, active count), loop_begin
+//   while (go): active list, A p on the listed RHS, PCG step, loop_next
+// Launches inside are sized for n; the kernels read the list length from
+// the device loop state.  All workspace is allocated beforehand (cg_workspace).
+template <typename R>
+int capture_cg_graph(pdep_ctx* c, SysData& s, CgArgs<R> a, const R* b, int n, int max_iter,
+                     int* list, cudaGraphExec_t* out) {
+  const int pi = sizeof(R) == 8 ? 1 : 0;
+  cudaStream_t cs = c->cap_stream;
+  const unsigned long long gen = c->ws_gen;
+  cudaGraph_t g = nullptr, pro = nullptr, body = nullptr;
+  cudaGraphConditionalHandle h = 0;
+  int status = PDEP_OK, launches = 0;
+  auto abort_capture = [&]() {
+    cudaGraph_t junk = nullptr;
+    cudaStreamEndCapture(cs, &junk);
+    if (junk && junk != body) cudaGraphDestroy(junk);
+    cudaGetLastError();
+  };
+  auto chk = [&](cudaError_t e) {
+    if (e != cudaSuccess && status == PDEP_OK) {
+      set_last_error(__FILE__, __LINE__, cudaGetErrorString(e));
+      status = PDEP_ERR_CUDA;
+    }
+    return e == cudaSuccess;
+  };
+  if (!chk(cudaGraphCreate(&g, 0))) return status;
+  if (chk(cudaGraphConditionalHandleCreate(&h, g, 0, 0)) &&
+      chk(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed))) {
+    capture_begin();
+    bool ok = chk(cudaMemsetAsync(&c->d_loop->active, 0, sizeof(int), cs)) &&
+              chk(cg_start<R>(a, b, s.ld, cs)) && chk(loop_begin(c->d_loop, max_iter, h, 1, cs));
+    capture_end();
+    if (ok) {
+      chk(cudaStreamEndCapture(cs, &pro));
+    } else {
+      abort_capture();
+    }
+  }
+  cudaGraphNode_t pn = nullptr, wn = nullptr;
+  cudaGraphNodeParams cp{};
+  if (status == PDEP_OK && chk(cudaGraphAddChildGraphNode(&pn, g, nullptr, 0, pro))) {
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    if (chk(cudaGraphAddNode(&wn, g, &pn, nullptr, 1, &cp))) body = cp.conditional.phGraph_out[0];
+  }
+  if (status == PDEP_OK &&
+      chk(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed))) {
+    capture_begin();
+    bool ok = chk(active_list_reset(a.sc, n, list, &c->d_loop->listed, &c->d_loop->active, cs));
+    if (ok) {
+      const int r = apply_h<R>(c, s, a.p, (R*)a.ap, n, list, n, true, true, cs, nullptr,
+                               &c->d_loop->listed);
+      if (r != PDEP_OK) {
+        status = r;
+        ok = false;
+      }
+    }
+    a.list_count = &c->d_loop->listed;
+    ok = ok && chk(cg_step<R>(a, list, n, cs)) &&
+         chk(loop_next(c->d_loop, max_iter, c->budget_ns, c->d_status, pi, h, 1, cs));
+    launches = capture_end();
+    if (ok) {
+      cudaGraph_t got = body;
+      chk(cudaStreamEndCapture(cs, &got));
+    } else {
+      abort_capture();
+    }
+  }
+  if (status == PDEP_OK && c->ws_gen != gen)
+    status = fail(PDEP_ERR_CUDA, "workspace moved while capturing a CG graph");
+  if (status == PDEP_OK) chk(cudaGraphInstantiate(out, g, 0));
+  if (pro) cudaGraphDestroy(pro);
+  cudaGraphDestroy(g);
+  if (status == PDEP_OK) c->body_launches[pi] = launches;
+  return status;
+}
+
+// Sternheimer PCG on (H - eps_v + sum_w sigma_w |w><w|) x = b for n RHS
+// (b, x: [n][ld]), each to ||r|| <= tol ||b|| or max_iter steps.  mask
+// (optional, device): RHS i takes part only if mask[i] != 0.  The loop runs on
+// the device: a CUDA graph with a while node whose body is one CG step and a
+// control kernel (no host round trip per step).  While the autotuner is
+// still timing launch shapes (or use_graph is 0) the same steps are launched
+// from a host loop that reads the control flag after each step.
+template <typename R>
+int cg_loop(pdep_ctx* c, SysData& s, const R* b, R* x, int n, double tol, int max_iter,
+            CgScal* sc, const double* mask, cudaStream_t st) {
+  const int si = (int)(&s - c->sys.data());
+  R *r, *p, *ap;
+  int* list;
+  RET(cg_workspace<R>(c, s, n, &r, &p, &ap, &list));
+  const int pi = sizeof(R) == 8 ? 1 : 0;
   CgArgs<R> a{};
   a.x = x;
   a.r = r;
@@ -933,74 +1100,112 @@ int cg_loop(pdep_ctx* c, SysData& s, const R* b, R* x, int n, double tol, int ma
   a.sc = sc;
   a.tol = tol;
   a.status = c->d_status;
-  a.n_active = c->d_counter;
-  const int pi = sizeof(R) == 8 ? 1 : 0;
-  CK(cudaMemsetAsync(c->d_counter, 0, sizeof(int), st));
-  CK(cg_start<R>(a, b, s.ld, st));
-  *hit_cap = false;
-  for (int it = 0;; ++it) {
-    int n_act = 0;
-    RET(read_int(c, c->d_counter, &n_act, st));
-    if (n_act == 0) break;
-    if (it >= max_iter) {
-      *hit_cap = true;
+  a.n_active = &c->d_loop->active;
+  a.mask = mask;
+  // loops under 256 RHS are never timed by the autotuner: they run the
+  // current (or default) shapes and are captured right away
+  const bool graph = c->opt.use_graph && (tuned(c, pi) || n < 256);
+  if (!graph) {
+    // eager: host loop, one 8-byte read of the loop state per step
+    CK(cudaMemsetAsync(&c->d_loop->active, 0, sizeof(int), st));
+    CK(cg_start<R>(a, b, s.ld, st));
+    CK(loop_begin(c->d_loop, max_iter, 0, 0, st));
+    for (;;) {
+      // active, listed, iter, go: one 16-byte read per step
+      CK(cudaMemcpyAsync(c->h_pin, &c->d_loop->active, 4 * sizeof(int), cudaMemcpyDeviceToHost,
+                         st));
+      CK(cudaStreamSynchronize(st));
+      int h[4];
+      memcpy(h, c->h_pin, sizeof(h));
+      if (!h[3]) break;
+      const int n_act = h[0];
+      CK(active_list_reset(sc, n, list, &c->d_loop->listed, &c->d_loop->active, st));
+      RET(apply_h<R>(c, s, p, ap, n, list, n_act, true, true, st));
+      // Autotuner: while untuned, each large step tries the next launch shape
+      // (all shapes compute the same update) and its time per RHS is kept;
+      // afterwards the fastest shape is used.
+      const bool tuning = c->opt.autotune && c->cg_variant[pi] < 0 && n_act >= 256;
+      a.variant = tuning ? c->cg_tune_next[pi] : cg_variant_of(c, pi);
+      a.list_count = nullptr;
+      if (tuning) CK(cudaEventRecord(c->ev[0], st));
+      CK(cg_step<R>(a, list, n_act, st));
+      if (tuning) {
+        CK(cudaEventRecord(c->ev[1], st));
+        CK(cudaEventSynchronize(c->ev[1]));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+        c->cg_tune_ms[pi][a.variant] = ms / n_act;
+        if (++c->cg_tune_next[pi] == CG_NUM_VARIANTS) {
+          int best = 0;
+          for (int v = 1; v < CG_NUM_VARIANTS; ++v)
+            if (c->cg_tune_ms[pi][v] < c->cg_tune_ms[pi][best]) best = v;
+          c->cg_variant[pi] = best;
+        }
+      }
+      CK(loop_next(c->d_loop, max_iter, c->budget_ns, c->d_status, pi, 0, 0, st));
+      ++c->eager_steps[pi];
+    }
+    return PDEP_OK;
+  }
+  a.variant = cg_variant_of(c, pi);
+  int pv = c->opt.proj_variant >= 0 ? c->opt.proj_variant : c->proj_variant;
+  if (pv < 0) pv = 1;  // what apply_h uses while the projection kernel is untimed
+  CgGraph* g = nullptr;
+  for (CgGraph& e : c->cg_graphs)
+    if (e.prec == pi && e.sys == si && e.n == n && e.max_iter == max_iter && e.tol == tol &&
+        e.b == b && e.x == x && e.sc == sc && e.mask == mask && e.ws_gen == c->ws_gen &&
+        e.cg_variant == a.variant && e.proj_variant == pv && e.budget_ns == c->budget_ns) {
+      g = &e;
       break;
     }
-    CK(active_list(sc, n, list, c->d_counter + 1, st));
-    RET(apply_h<R>(c, s, p, ap, n, list, n_act, true, true, st));
-    CK(cudaMemsetAsync(c->d_counter, 0, sizeof(int), st));
-    // Autotuner: while untuned, each large step tries the next launch shape
-    // (all shapes compute the same update) and its time per RHS is kept;
-    // afterwards the fastest shape is used.
-    const bool tuning = c->cg_variant[pi] < 0 && n_act >= 256;
-    a.variant = tuning ? c->cg_tune_next[pi]
-                       : (c->cg_variant[pi] >= 0 ? c->cg_variant[pi] : (int)CG_STREAM256);
-    if (tuning) CK(cudaEventRecord(c->ev[0], st));
-    CK(cg_step<R>(a, list, n_act, st));
-    if (tuning) {
-      CK(cudaEventRecord(c->ev[1], st));
-      CK(cudaEventSynchronize(c->ev[1]));
-      float ms = 0.f;
-      CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
-      c->cg_tune_ms[pi][a.variant] = ms / n_act;
-      if (++c->cg_tune_next[pi] == CG_NUM_VARIANTS) {
-        int best = 0;
-        for (int v = 1; v < CG_NUM_VARIANTS; ++v)
-          if (c->cg_tune_ms[pi][v] < c->cg_tune_ms[pi][best]) best = v;
-        c->cg_variant[pi] = best;
-      }
+  if (!g) {
+    CgGraph e{};
+    e.prec = pi;
+    e.sys = si;
+    e.n = n;
+    e.max_iter = max_iter;
+    e.tol = tol;
+    e.b = b;
+    e.x = x;
+    e.sc = sc;
+    e.mask = mask;
+    e.ws_gen = c->ws_gen;
+    e.cg_variant = a.variant;
+    e.proj_variant = pv;
+    e.budget_ns = c->budget_ns;
+    RET(capture_cg_graph<R>(c, s, a, b, n, max_iter, list, &e.exec));
+    if (c->cg_graphs.size() >= 16) {
+      cudaGraphExecDestroy(c->cg_graphs.front().exec);
+      c->cg_graphs.erase(c->cg_graphs.begin());
     }
+    c->cg_graphs.push_back(e);
+    g = &c->cg_graphs.back();
   }
+  {
+    ProfScope ps(sizeof(R) == 8 ? PC_CG_GRAPH_F64 : PC_CG_GRAPH_F32, st, 0.0, 0.0);
+    CK(cudaGraphLaunch(g->exec, st));
+  }
+  ++c->graph_launches;
   return PDEP_OK;
 }
 
-int collect_cg_stats(pdep_ctx* c, const CgScal* sc, int n, int* iters_out, cudaStream_t st,
-                     std::vector<int>* its) {
-  std::vector<CgScal> h(n);
-  CK(cudaMemcpyAsync(h.data(), sc, sizeof(CgScal) * n, cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  its->resize(n);
-  for (int i = 0; i < n; ++i) {
-    (*its)[i] = h[i].iters;
-    c->st_cg_iters += h[i].iters;
-    c->st_cg_max = std::max(c->st_cg_max, h[i].iters);
-  }
-  (void)iters_out;
-  return PDEP_OK;
-}
-
-// Solve for n right-hand sides b (FP64, [n][ld]); x out (FP64).  h_iters and
-// h_res (host, may be null) get per-RHS iteration counts and FP64 residuals.
+// d_refine[0] holds the refinement round's unconverged count: the FP64 A delta
+// and the residual update run on that many listed RHS (launches sized for n).
+// Solve for n right-hand sides b (FP64, [n][ld]); x out (FP64).  Nothing is
+// read back to the host: per-RHS iteration counts accumulate in its_total
+// (device, may be null), the FP64 relative residuals are left in 'rel'
+// (device, [n]), and the statistics and the not-converged condition go to the
+// device statistics and status word.
 int solve_rhs(pdep_ctx* c, SysData& s, const double* b, const double* xd, double* x, int n,
-              double* dn, int* h_iters, double* h_res, cudaStream_t st) {
+              double* dn, int* its_total, double** rel_out, cudaStream_t st) {
   const double tol = c->opt.cg_tol;
   double *rel, *r64, *ad;
   RET(ws(c, "sv_rel", (size_t)n, &rel));
   RET(ws(c, "sv_r64", (size_t)n * s.ld, &r64));
   RET(ws(c, "sv_ap64", (size_t)n * s.ld, &ad));
-  std::vector<int> its_total(n, 0);
-  bool capped = false;
-  int rounds = 0;
+  if (rel_out) *rel_out = rel;
+  if (its_total) CK(cudaMemsetAsync(its_total, 0, sizeof(int) * (size_t)n, st));
+  CK(cudaMemsetAsync(&c->d_dstats->rounds_cur, 0, sizeof(int), st));
   // r64 = b: the FP64 residual, updated as r -= A delta for every update
   // delta of x (and checked against b's norm)
   CK(cudaMemcpyAsync(r64, b, sizeof(double) * (size_t)n * s.ld, cudaMemcpyDeviceToDevice, st));
@@ -1010,11 +1215,9 @@ int solve_rhs(pdep_ctx* c, SysData& s, const double* b, const double* xd, double
     RET(ws(c, "cg_sc64", (size_t)n, &sc));
     // stop the recursion a little below tol so that the FP64 residual
     // recomputed from x (which drifts slightly from the recursion) meets it
-    RET(cg_loop<double>(c, s, b, x, n, 0.9 * tol, c->opt.cg_max_iter, sc, st, &capped));
-    std::vector<int> its;
-    RET(collect_cg_stats(c, sc, n, nullptr, st, &its));
-    for (int i = 0; i < n; ++i) its_total[i] = its[i];
-    rounds = 1;
+    RET(cg_loop<double>(c, s, b, x, n, 0.9 * tol, c->opt.cg_max_iter, sc, nullptr, st));
+    CK(cg_collect(sc, n, its_total, c->d_dstats, st));
+    CK(cudaMemsetAsync(&c->d_dstats->rounds_cur, 0, sizeof(int), st));
     // x += xd (the deflated states' exact share); then the FP64 residual
     // b - A x of the CG part, with the density response of the whole x
     // accumulated by the same transform
@@ -1027,8 +1230,12 @@ int solve_rhs(pdep_ctx* c, SysData& s, const double* b, const double* xd, double
     }
     RET(apply_h<double>(c, s, hx, ad, n, nullptr, 0, true, true, st, dn));
     CK(residual_update(r64, ad, b, s.ld, s.n_pw, n, rel, nullptr, xd, s.d_sigma64, s.n_occ, st));
+    int one = 1;
+    CK(cudaMemcpyAsync(&c->d_dstats->rounds_cur, &one, sizeof(int), cudaMemcpyHostToDevice, st));
   } else {
-    // mixed: FP32 inner CG on the scaled residual, FP64 residual refinement
+    // mixed: FP32 inner CG on the scaled residual, FP64 residual refinement.
+    // Every round is enqueued; a round whose list is empty costs only its
+    // launches (each kernel exits on the zero count).
     float *r32, *d32;
     double *rn, *dl;
     CgScal* sc;
@@ -1040,55 +1247,33 @@ int solve_rhs(pdep_ctx* c, SysData& s, const double* b, const double* xd, double
     RET(ws(c, "mx_list", (size_t)n, &list));
     RET(ws(c, "sv_dl", (size_t)n * s.ld, &dl));
     CK(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)n * s.ld, st));
-    {
-      std::vector<double> ones(n, 1.0);
-      CK(cudaMemcpyAsync(rel, ones.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
-      RET(sync(st));
-    }
+    CK(fill_value(rel, n, 1.0, st));
+    int* n_un = c->d_refine;
     for (int round = 0; round < c->opt.max_refine; ++round) {
       NvtxRange nv("refinement_round");
-      CK(unconverged_list(rel, tol, n, list, c->d_counter + 1, st));
-      int n_un = 0;
-      RET(read_int(c, c->d_counter + 1, &n_un, st));
-      if (n_un == 0) break;
-      rounds = round + 1;
+      CK(unconverged_list(rel, tol, n, list, n_un, st, &c->d_dstats->rounds_cur));
       CK(refine_prepare(r64, s.ld, s.n_pw, n, rel, tol, r32, s.ld, rn, st));
-      bool cap = false;
-      RET(cg_loop<float>(c, s, r32, d32, n, c->opt.inner_tol, c->opt.inner_max_iter, sc, st, &cap));
-      std::vector<int> its;
-      RET(collect_cg_stats(c, sc, n, nullptr, st, &its));
-      for (int i = 0; i < n; ++i) its_total[i] += its[i];
+      RET(cg_loop<float>(c, s, r32, d32, n, c->opt.inner_tol, c->opt.inner_max_iter, sc, rn, st));
+      CK(cg_collect(sc, n, its_total, c->d_dstats, st));
       // delta = rn d32 (+ xd in the first round, when every RHS is listed);
       // x += delta; r -= A delta in FP64, and the density response of delta
       // is accumulated by the same transform (dn is linear in x)
       const double* xr = round == 0 ? xd : nullptr;
       CK(refine_delta(x, dl, s.ld, d32, s.ld, s.n_pw, n, rn, xr, st));
-      RET(apply_h<double>(c, s, dl, ad, n, list, n_un, true, true, st, dn));
-      CK(residual_update(r64, ad, b, s.ld, s.n_pw, n_un, rel, list, xr, s.d_sigma64, s.n_occ, st));
-    }
-    {
-      CK(unconverged_list(rel, tol, n, list, c->d_counter + 1, st));
-      int n_un = 0;
-      RET(read_int(c, c->d_counter + 1, &n_un, st));
-      capped = n_un > 0;
+      if (c->opt.df_refine)
+        RET(apply_h<df>(c, s, dl, ad, n, list, n, true, true, st, dn, n_un));
+      else
+        RET(apply_h<double>(c, s, dl, ad, n, list, n, true, true, st, dn, n_un));
+      CK(residual_update(r64, ad, b, s.ld, s.n_pw, n, rel, list, xr, s.d_sigma64, s.n_occ, st,
+                         n_un));
     }
   }
-  c->st_refine_max = std::max(c->st_refine_max, rounds);
   // rel holds the FP64 residual of every RHS from its last update.  No final
-  // P_c projection is needed: the shifted
-  // operator lifts occupied state w to eps_{n_ext} - eps_v > 0, so the
-  // occupied component of x is at most ||b - A x|| / (eps_{n_ext} - eps_v).
-  std::vector<double> hr(n);
-  CK(cudaMemcpyAsync(hr.data(), rel, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
-  RET(sync(st));
-  for (int i = 0; i < n; ++i) {
-    c->st_max_res = std::max(c->st_max_res, hr[i]);
-    if (h_res) h_res[i] = hr[i];
-    if (h_iters) h_iters[i] = its_total[i];
-  }
+  // P_c projection is needed: the shifted operator lifts occupied state w to
+  // eps_{n_ext} - eps_v > 0, so the occupied component of x is at most
+  // ||b - A x|| / (eps_{n_ext} - eps_v).
+  CK(solve_finish(rel, n, tol, c->d_dstats, c->d_status, st));
   c->st_solves += n;
-  RET(check_status(c, st));
-  if (capped) return fail(PDEP_ERR_NOT_CONVERGED, "Sternheimer CG reached its iteration cap");
   return PDEP_OK;
 }
 
@@ -1165,7 +1350,11 @@ int chi0_internal(pdep_ctx* c, SysData& s, const double* phi, int m, double* out
   size_t budget = (size_t)24 << 30;
   if (c->opt.workspace_limit_bytes) budget = c->opt.workspace_limit_bytes / 2;
   int mc_max = (int)std::max<size_t>(1, budget / per);
+  // every chunk is solved and written; a solve left above cg_tol only marks
+  // the device status word
+  c->st_chunks = 0;
   for (int j0 = 0; j0 < m; j0 += mc_max) {
+    ++c->st_chunks;
     const int mc = std::min(mc_max, m - j0);
     double *dv, *bvec, *xvec, *dn;
     RET(ws(c, "c0_dv", (size_t)mc * s.n_r, &dv));
@@ -1182,8 +1371,7 @@ int chi0_internal(pdep_ctx* c, SysData& s, const double* phi, int m, double* out
     RET(build_rhs(c, s, dv, mc, bvec, xd, st));
     // the density response dn (Eq. deltani) is accumulated inside the
     // solver's FP64 transforms of the solution updates
-    int r = solve_rhs(c, s, bvec, xd, xvec, mc * nocc, dn, nullptr, nullptr, st);
-    if (r != PDEP_OK && r != PDEP_ERR_NOT_CONVERGED) return r;
+    RET(solve_rhs(c, s, bvec, xd, xvec, mc * nocc, dn, nullptr, nullptr, st));
     // (chi0bar phi_j)(G) = sqrt(4pi)/|G| * Omega^{1/2}/N_r * FFT[dn_j](G)
     {
       ItemMap map{mc, (mc + 1) / 2};
@@ -1206,7 +1394,6 @@ int chi0_internal(pdep_ctx* c, SysData& s, const double* phi, int m, double* out
       ep.coef = COEF_SQRT_COULOMB;
       CK(launch_cols_bwd<double>(s.sd, b1, map, n_items, ep, st));
     }
-    if (r == PDEP_ERR_NOT_CONVERGED) return r;
   }
   return PDEP_OK;
 }
@@ -1217,12 +1404,43 @@ int check_sys(const pdep_ctx* c, int sys) {
   return PDEP_OK;
 }
 
-void reset_stats(pdep_ctx* c) {
+int reset_stats(pdep_ctx* c, cudaStream_t st) {
   c->st_solves = 0;
-  c->st_cg_iters = 0;
-  c->st_cg_max = 0;
-  c->st_refine_max = 0;
-  c->st_max_res = 0;
+  c->st_chunks = 0;
+  c->graph_launches = 0;
+  c->eager_steps[0] = c->eager_steps[1] = 0;
+  c->st_launch0 = launch_count();
+  CK(cudaMemsetAsync(c->d_dstats, 0, sizeof(DevStats), st));
+  CK(cudaMemsetAsync(c->d_loop->steps, 0, sizeof(c->d_loop->steps), st));
+  return PDEP_OK;
+}
+
+// Synchronises st and fills the solve statistics (device counters included).
+int read_stats(pdep_ctx* c, pdep_stats* out, cudaStream_t st) {
+  DevStats d;
+  unsigned long long steps[2];
+  CK(cudaMemcpyAsync(&d, c->d_dstats, sizeof(DevStats), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(steps, c->d_loop->steps, sizeof(steps), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  out->sternheimer_solves = c->st_solves;
+  out->cg_iterations = (long long)d.cg_iters;
+  out->cg_iterations_max = d.cg_max;
+  out->refine_rounds_max = d.refine_max;
+  double mr;
+  memcpy(&mr, &d.max_res_bits, sizeof(double));
+  out->max_cg_residual = mr;
+  out->cg_variant = c->cg_variant[c->opt.precision == PDEP_FP64 ? 1 : 0];
+  out->proj_variant = c->opt.proj_variant >= 0 ? c->opt.proj_variant : c->proj_variant;
+  out->chi0_chunks = c->st_chunks;
+  // launches outside graphs are counted on the host; a graph contributes its
+  // prologue (2 kernels) per launch and its body per step, the steps counted
+  // on the device (loop_next counts eager steps too: those are subtracted)
+  long long in_graphs = 2 * c->graph_launches;
+  for (int pi = 0; pi < 2; ++pi)
+    in_graphs += ((long long)steps[pi] - c->eager_steps[pi]) * c->body_launches[pi];
+  out->kernel_launches = (launch_count() - c->st_launch0) + in_graphs;
+  out->graph_launches = c->graph_launches;
+  return PDEP_OK;
 }
 
 int solve_one(pdep_ctx* c, int si, const double* phi0, double* eigvals, double* eigvecs,
@@ -1242,14 +1460,8 @@ int solve_one(pdep_ctx* c, int si, const double* phi0, double* eigvals, double* 
   } else {
     CK(philox_normal(start, s.ld, dim, np, c->opt.seed, 0ULL, st));
   }
-  int app_status = PDEP_OK;
   OpFn op = [&](const double* in, double* outv, int m) -> int {
-    int r = chi0_internal(c, s, in, m, outv, nullptr, st);
-    if (r == PDEP_ERR_NOT_CONVERGED) {
-      app_status = r;
-      return (int)PDEP_OK;
-    }
-    return r;
+    return chi0_internal(c, s, in, m, outv, nullptr, st);
   };
   std::vector<double> th(np);
   DavidsonOut dout;
@@ -1268,7 +1480,7 @@ int solve_one(pdep_ctx* c, int si, const double* phi0, double* eigvals, double* 
     stats->max_dav_residual = std::max(stats->max_dav_residual, dout.max_res);
   }
   if (!fixed && !dout.converged) return fail(PDEP_ERR_NOT_CONVERGED, "Davidson did not converge");
-  return app_status;
+  return PDEP_OK;
 }
 
 }  // namespace
@@ -1344,6 +1556,10 @@ void pdep_default_options(pdep_options* o) {
   o->workspace_limit_bytes = 0;
   o->n_deflate = 16;
   o->proj_variant = -1;
+  o->clock_budget_cycles = 0;
+  o->autotune = 1;
+  o->use_graph = 1;
+  o->df_refine = 1;
 }
 
 const char* pdep_status_string(int s) {
@@ -1388,6 +1604,12 @@ void pdep_destroy(pdep_ctx* c) {
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
   c->eig_graphs.release();
+  for (CgGraph& g : c->cg_graphs) cudaGraphExecDestroy(g.exec);
+  c->cg_graphs.clear();
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->d_loop) cudaFree(c->d_loop);
+  if (c->d_dstats) cudaFree(c->d_dstats);
+  if (c->d_refine) cudaFree(c->d_refine);
   for (auto& kv : c->bufs)
     if (kv.second.p) cudaFree(kv.second.p);
   for (void* p : c->owned) cudaFree(p);
@@ -1417,11 +1639,31 @@ int pdep_setup(const pdep_system_desc* sys, int n_sys, const pdep_options* opt, 
   };
   if (cudaGetDevice(&c->device) != cudaSuccess) return bail(fail(PDEP_ERR_CUDA, "no CUDA device"));
   if (upload_local_twiddles() != cudaSuccess) return bail(fail(PDEP_ERR_CUDA, "twiddle upload"));
+  if (c->opt.precision != PDEP_FP64 && c->opt.precision != PDEP_MIXED_TF32 &&
+      c->opt.precision != PDEP_MIXED_BF16)
+    return bail(fail(PDEP_ERR_INVALID_ARG, "unknown precision mode"));
+  if (c->opt.clock_budget_cycles < 0) return bail(fail(PDEP_ERR_INVALID_ARG, "negative clock budget"));
   if (cudaMalloc(&c->d_status, sizeof(unsigned)) != cudaSuccess ||
       cudaMalloc(&c->d_counter, 4 * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&c->d_loop, sizeof(CgLoopState)) != cudaSuccess ||
+      cudaMalloc(&c->d_dstats, sizeof(DevStats)) != cudaSuccess ||
+      cudaMalloc(&c->d_refine, 4 * sizeof(int)) != cudaSuccess ||
       cudaMallocHost(&c->h_pin, 16 * sizeof(int)) != cudaSuccess)
     return bail(fail(PDEP_ERR_OOM, "context allocation"));
   cudaMemset(c->d_status, 0, sizeof(unsigned));
+  cudaMemset(c->d_loop, 0, sizeof(CgLoopState));
+  cudaMemset(c->d_dstats, 0, sizeof(DevStats));
+  cudaMemset(c->d_refine, 0, 4 * sizeof(int));
+  if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(fail(PDEP_ERR_CUDA, "capture stream creation"));
+  if (c->opt.clock_budget_cycles > 0) {
+    int khz = 0;
+    if (cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, c->device) != cudaSuccess || khz <= 0)
+      khz = 2070000;
+    // cycles at the rated SM clock -> ns of %globaltimer
+    c->budget_ns = (unsigned long long)((double)c->opt.clock_budget_cycles * 1e6 / khz);
+    if (c->budget_ns == 0) c->budget_ns = 1;
+  }
   if (cudaEventCreate(&c->ev[0]) != cudaSuccess || cudaEventCreate(&c->ev[1]) != cudaSuccess)
     return bail(fail(PDEP_ERR_CUDA, "event creation"));
   c->sys.resize(n_sys);
@@ -1447,9 +1689,11 @@ int pdep_setup(const pdep_system_desc* sys, int n_sys, const pdep_options* opt, 
     if (r != PDEP_OK) return bail(r);
     if ((r = persistent(c, &s.d_v, s.n_r)) != PDEP_OK) return bail(r);
     if ((r = persistent(c, &s.d_vf, s.n_r)) != PDEP_OK) return bail(r);
+    if ((r = persistent(c, &s.d_vdf, s.n_r)) != PDEP_OK) return bail(r);
     if (cudaMemcpyAsync(s.d_v, d.v_r, sizeof(double) * s.n_r, kind_to_dev(d.v_r), st) != cudaSuccess)
       return bail(fail(PDEP_ERR_CUDA, "potential upload"));
-    if (convert<float, double>(s.d_vf, s.n_r, s.d_v, s.n_r, s.n_r, 1, st) != cudaSuccess)
+    if (convert<float, double>(s.d_vf, s.n_r, s.d_v, s.n_r, s.n_r, 1, st) != cudaSuccess ||
+        convert<df, double>(s.d_vdf, s.n_r, s.d_v, s.n_r, s.n_r, 1, st) != cudaSuccess)
       return bail(fail(PDEP_ERR_CUDA, "potential conversion"));
     // the potential must be finite
     std::vector<double> hv(s.n_r);
@@ -1499,11 +1743,13 @@ int chi0_apply(pdep_ctx* c, int sys, const double* phi, int n_pert, double* chi0
   if (n_pert == 0) return PDEP_OK;
   cudaStream_t st = (cudaStream_t)stream;
   SysData& s = c->sys[sys];
-  reset_stats(c);
+  RET(reset_stats(c, st));
   const int dim = s.n_pw - 1;
   double *in, *outv, *dn = nullptr;
   RET(ws(c, "api_in", (size_t)n_pert * s.ld, &in));
   RET(ws(c, "api_out", (size_t)n_pert * s.ld, &outv));
+  const bool host_io = !is_device_ptr(phi) || !is_device_ptr(chi0_phi) ||
+                       (dn_r && !is_device_ptr(dn_r));
   CK(cudaMemsetAsync(in, 0, sizeof(double) * (size_t)n_pert * s.ld, st));
   CK(cudaMemcpy2DAsync(in, s.ld * sizeof(double), phi, dim * sizeof(double), dim * sizeof(double),
                        n_pert, kind_to_dev(phi), st));
@@ -1514,15 +1760,16 @@ int chi0_apply(pdep_ctx* c, int sys, const double* phi, int n_pert, double* chi0
     else
       RET(ws(c, "api_dn", (size_t)n_pert * s.n_r, &dn));
   }
-  int r = chi0_internal(c, s, in, n_pert, outv, dn, st);
-  if (r != PDEP_OK && r != PDEP_ERR_NOT_CONVERGED) return r;
+  RET(chi0_internal(c, s, in, n_pert, outv, dn, st));
   CK(cudaMemcpy2DAsync(chi0_phi, dim * sizeof(double), outv, s.ld * sizeof(double),
                        dim * sizeof(double), n_pert, kind_from_dev(chi0_phi), st));
   if (dn_r && !dn_dev)
     CK(cudaMemcpyAsync(dn_r, dn, sizeof(double) * (size_t)n_pert * s.n_r, cudaMemcpyDeviceToHost,
                        st));
-  RET(sync(st));
-  return r;
+  // device buffers only: enqueued, nothing waited for; conditions stay in the
+  // status word until a synchronising call reads them
+  if (!host_io) return PDEP_OK;
+  return check_status(c, st);
 }
 
 // Screening operators at omega = 0 in the PDEP basis (Eqs. linearalgebrachichi0,
@@ -1772,7 +2019,7 @@ int pdep_chibar_apply(pdep_ctx* c, int sys, const double* phi, int n, double* ou
   if (n == 0) return PDEP_OK;
   cudaStream_t st = (cudaStream_t)stream;
   SysData& s = c->sys[sys];
-  reset_stats(c);
+  RET(reset_stats(c, st));
   const int dim = s.n_pw - 1;
   double *y, *r, *p, *q, *d_al, *d_be, *dots;
   RET(ws(c, "hx_y", (size_t)n * s.ld, &y));
@@ -1844,7 +2091,8 @@ int pdep_chibar_apply(pdep_ctx* c, int sys, const double* phi, int n, double* ou
   CK(one_minus(r, y, s.ld, s.n_pw, n, st));
   CK(cudaMemcpy2DAsync(out, dim * sizeof(double), r, s.ld * sizeof(double), dim * sizeof(double),
                        n, kind_from_dev(out), st));
-  RET(sync(st));
+  const int dev = check_status(c, st);
+  if (dev != PDEP_OK) return dev;
   if (n_act > 0) return fail(PDEP_ERR_NOT_CONVERGED, "self-consistent response: CG cap reached");
   return PDEP_OK;
 }
@@ -1857,26 +2105,27 @@ int sternheimer_solve(pdep_ctx* c, int sys, const double* dv_r, int n_pert, doub
   if (n_pert == 0) return PDEP_OK;
   cudaStream_t st = (cudaStream_t)stream;
   SysData& s = c->sys[sys];
-  reset_stats(c);
+  RET(reset_stats(c, st));
   const int n = n_pert * s.n_occ;
-  double *dv, *bvec, *xvec;
+  const bool host_io = !is_device_ptr(dv_r) || !is_device_ptr(dpsi) ||
+                       (iters && !is_device_ptr(iters)) || (resid && !is_device_ptr(resid));
+  double *dv, *bvec, *xvec, *rel = nullptr;
+  int* its;
   RET(ws(c, "st_dv", (size_t)n_pert * s.n_r, &dv));
   RET(ws(c, "st_b", (size_t)n * s.ld, &bvec));
   RET(ws(c, "st_x", (size_t)n * s.ld, &xvec));
+  RET(ws(c, "st_its", (size_t)n, &its));
   CK(cudaMemcpyAsync(dv, dv_r, sizeof(double) * (size_t)n_pert * s.n_r, kind_to_dev(dv_r), st));
   double* xd = nullptr;
   if (s.n_defl > 0) RET(ws(c, "st_xd", (size_t)n * s.ld, &xd));
   RET(build_rhs(c, s, dv, n_pert, bvec, xd, st));
-  std::vector<int> hi(n);
-  std::vector<double> hr(n);
-  int r = solve_rhs(c, s, bvec, xd, xvec, n, nullptr, hi.data(), hr.data(), st);
-  if (r != PDEP_OK && r != PDEP_ERR_NOT_CONVERGED) return r;
+  RET(solve_rhs(c, s, bvec, xd, xvec, n, nullptr, its, &rel, st));
   CK(cudaMemcpy2DAsync(dpsi, s.n_pw * sizeof(double), xvec, s.ld * sizeof(double),
                        s.n_pw * sizeof(double), n, kind_from_dev(dpsi), st));
-  RET(sync(st));
-  if (iters) RET(copy_from_host(iters, hi.data(), sizeof(int) * n, st));
-  if (resid) RET(copy_from_host(resid, hr.data(), sizeof(double) * n, st));
-  return r;
+  if (iters) CK(cudaMemcpyAsync(iters, its, sizeof(int) * n, kind_from_dev(iters), st));
+  if (resid) CK(cudaMemcpyAsync(resid, rel, sizeof(double) * n, kind_from_dev(resid), st));
+  if (!host_io) return PDEP_OK;
+  return check_status(c, st);
 }
 
 int pdep_apply_hamiltonian(pdep_ctx* c, int sys, const double* x, int n, double* y,
@@ -1894,6 +2143,8 @@ int pdep_apply_hamiltonian(pdep_ctx* c, int sys, const double* x, int n, double*
                        s.n_pw * sizeof(double), n, kind_to_dev(x), st));
   if (precision == PDEP_FP64) {
     RET(apply_h<double>(c, s, in, outv, n, nullptr, 0, false, false, st));
+  } else if (precision == PDEP_APPLY_DF64) {
+    RET(apply_h<df>(c, s, in, outv, n, nullptr, 0, false, false, st));
   } else {
     float *in32, *out32;
     RET(ws(c, "api_in32", (size_t)n * s.ld, &in32));
@@ -1944,11 +2195,11 @@ int pdep_solve(pdep_ctx* c, int sys, const double* phi0, double* eigvals, double
   if (sys != -1) RET(check_sys(c, sys));
   cudaStream_t st = (cudaStream_t)stream;
   auto t0 = std::chrono::steady_clock::now();
-  reset_stats(c);
-  if (stats) {
-    memset(stats, 0, sizeof(*stats));
-    stats->converged = 1;
-  }
+  RET(reset_stats(c, st));
+  pdep_stats local{};
+  if (!stats) stats = &local;
+  memset(stats, 0, sizeof(*stats));
+  stats->converged = 1;
   int result = PDEP_OK;
   const int lo = sys == -1 ? 0 : sys, hi = sys == -1 ? (int)c->sys.size() : sys + 1;
   size_t off_val = 0, off_vec = 0;
@@ -1961,18 +2212,24 @@ int pdep_solve(pdep_ctx* c, int sys, const double* phi0, double* eigvals, double
     off_val += s.n_pdep;
     off_vec += (size_t)s.n_pdep * (s.n_pw - 1);
   }
-  if (stats) {
-    stats->sternheimer_solves = c->st_solves;
-    stats->cg_iterations = c->st_cg_iters;
-    stats->cg_iterations_max = c->st_cg_max;
-    stats->refine_rounds_max = c->st_refine_max;
-    stats->max_cg_residual = c->st_max_res;
-    stats->cg_variant = c->cg_variant[c->opt.precision == PDEP_FP64 ? 1 : 0];
-    stats->proj_variant = c->opt.proj_variant >= 0 ? c->opt.proj_variant : c->proj_variant;
-    stats->seconds =
-        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  }
+  RET(read_stats(c, stats, st));
+  stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  c->last_dav = *stats;
+  const int dev = check_status(c, st);
+  if (dev != PDEP_OK && dev != PDEP_ERR_NOT_CONVERGED) return dev;
+  if (dev == PDEP_ERR_NOT_CONVERGED) result = dev;
   return result;
+}
+
+int pdep_get_stats(pdep_ctx* c, pdep_stats* stats, void* stream) {
+  if (!c || !stats) return fail(PDEP_ERR_INVALID_ARG, "null context or stats");
+  cudaStream_t st = (cudaStream_t)stream;
+  memset(stats, 0, sizeof(*stats));
+  stats->dav_iterations = c->last_dav.dav_iterations;
+  stats->converged = c->last_dav.converged;
+  stats->max_dav_residual = c->last_dav.max_dav_residual;
+  RET(read_stats(c, stats, st));
+  return check_status(c, st);
 }
 
 }  // extern "C"

@@ -55,6 +55,7 @@ enum : unsigned {
   DEV_NOT_CONVERGED = 2u,
   DEV_BOUNDS = 4u,
   DEV_BREAKDOWN = 8u,
+  DEV_TIMEOUT = 16u,
 };
 
 // Builds compiled with -DPDEP_BOUNDS_CHECK test every index that a kernel

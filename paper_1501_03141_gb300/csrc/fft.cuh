@@ -17,7 +17,10 @@
 // unnormalised), S = -1 the forward transform (grid -> sphere).
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
+#include "df64.cuh"
 
 namespace pdep {
 
@@ -33,6 +36,7 @@ constexpr int LOCAL_TW_SIZE = 240;
 // defined here: fft.cuh is included by a single translation unit (no -rdc)
 __constant__ double2 c_local_tw_d[LOCAL_TW_SIZE];
 __constant__ float2 c_local_tw_f[LOCAL_TW_SIZE];
+__constant__ float4 c_local_tw_df[LOCAL_TW_SIZE];  // (re.hi, re.lo, im.hi, im.lo)
 
 template <typename R>
 struct LocalTw;
@@ -48,6 +52,13 @@ struct LocalTw<float> {
   static __device__ __forceinline__ cpx<float> get(int i) {
     float2 v = c_local_tw_f[i];
     return mk(v.x, v.y);
+  }
+};
+template <>
+struct LocalTw<df> {
+  static __device__ __forceinline__ cpx<df> get(int i) {
+    float4 v = c_local_tw_df[i];
+    return mk(df(v.x, v.y), df(v.z, v.w));
   }
 };
 
@@ -168,9 +179,29 @@ __device__ __forceinline__ int bitrev(int t, int bits) {
 template <typename R, int S>
 __device__ __forceinline__ cpx<R> table_w(const cpx<R>* __restrict__ tw, int j) {
   cpx<R> w;
-  w.x = __ldg(&tw[j].x);
-  w.y = __ldg(&tw[j].y);
+  if constexpr (std::is_same<R, df>::value) {
+    // double-float: one 16-byte load of (re.hi, re.lo, im.hi, im.lo)
+    const float4 v = __ldg(reinterpret_cast<const float4*>(tw + j));
+    w = mk(R(v.x, v.y), R(v.z, v.w));
+  } else {
+    w.x = __ldg(&tw[j].x);
+    w.y = __ldg(&tw[j].y);
+  }
   return S > 0 ? w : conj(w);
+}
+
+// p + v (lower lane of a butterfly) or p - v (upper lane): one fused
+// multiply-add per component in FP32 / FP64, a sign flip and one addition in
+// double-float
+template <typename R>
+__device__ __forceinline__ cpx<R> pm(cpx<R> p, cpx<R> v, bool up) {
+  const R sgn = up ? R(-1) : R(1);
+  return mk(p.x + sgn * v.x, p.y + sgn * v.y);
+}
+template <>
+__device__ __forceinline__ cpx<df> pm<df>(cpx<df> p, cpx<df> v, bool up) {
+  const cpx<df> w = up ? mk(-v.x, -v.y) : v;
+  return mk(p.x + w.x, p.y + w.y);
 }
 
 // Distribution A -> B.  t = lane index inside the group (0..TPL-1).
@@ -186,7 +217,6 @@ __device__ __forceinline__ void fft_a2b(cpx<R> (&v)[N / TPL], int t, const cpx<R
       const int L = 2 * half;
       const int j = t & (half - 1);
       const bool up = (t & half) != 0;
-      const R sgn = up ? R(-1) : R(1);
       if (L <= 4) {
         // twiddles of 2- and 4-point butterflies are 1 and S*i: one fused
         // +-1 multiply-add per component, then a swap for j = 1 (upper lanes)
@@ -194,7 +224,7 @@ __device__ __forceinline__ void fft_a2b(cpx<R> (&v)[N / TPL], int t, const cpx<R
 #pragma unroll
         for (int i = 0; i < M; ++i) {
           const cpx<R> p = shfl_xor(v[i], half);
-          const cpx<R> d = mk(p.x + sgn * v[i].x, p.y + sgn * v[i].y);
+          const cpx<R> d = pm(p, v[i], up);
           v[i] = rot ? mul_si<R, S>(d) : d;
         }
       } else {
@@ -202,7 +232,7 @@ __device__ __forceinline__ void fft_a2b(cpx<R> (&v)[N / TPL], int t, const cpx<R
 #pragma unroll
         for (int i = 0; i < M; ++i) {
           cpx<R> p = shfl_xor(v[i], half);
-          const cpx<R> d = mk(p.x + sgn * v[i].x, p.y + sgn * v[i].y);
+          const cpx<R> d = pm(p, v[i], up);
           v[i] = up ? d * W : d;
         }
       }
@@ -220,14 +250,13 @@ __device__ __forceinline__ void fft_b2a(cpx<R> (&v)[N / TPL], int t, const cpx<R
       const int L = 2 * half;
       const int j = t & (half - 1);
       const bool up = (t & half) != 0;
-      const R sgn = up ? R(-1) : R(1);
       if (L <= 4) {
         const bool rot = up && j == 1;
 #pragma unroll
         for (int i = 0; i < M; ++i) {
           const cpx<R> own = rot ? mul_si<R, S>(v[i]) : v[i];
           const cpx<R> p = shfl_xor(own, half);
-          v[i] = mk(p.x + sgn * own.x, p.y + sgn * own.y);
+          v[i] = pm(p, own, up);
         }
       } else {
         const cpx<R> W = table_w<R, S>(tw, j * (N / L));
@@ -235,7 +264,7 @@ __device__ __forceinline__ void fft_b2a(cpx<R> (&v)[N / TPL], int t, const cpx<R
         for (int i = 0; i < M; ++i) {
           const cpx<R> own = up ? v[i] * W : v[i];
           const cpx<R> p = shfl_xor(own, half);
-          v[i] = mk(p.x + sgn * own.x, p.y + sgn * own.y);
+          v[i] = pm(p, own, up);
         }
       }
     }

@@ -87,13 +87,16 @@ __global__ void __launch_bounds__(256) k_gemm(int m, int n, int k, R alpha, cons
                                               long long lda, const R* __restrict__ B, long long ldb,
                                               R beta, R* __restrict__ C, long long ldc, int kchunk,
                                               int atomic, const int* __restrict__ bmap,
-                                              const int* __restrict__ cmap) {
+                                              const int* __restrict__ cmap,
+                                              const int* __restrict__ ndev) {
   constexpr int BM = 16 * TM, BN = 64, BK = 16;
   __shared__ R As[BK][BM + 1];
   __shared__ R Bs[BK][BN + 1];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int row0 = blockIdx.x * BM, col0 = blockIdx.y * BN;
+  if (ndev) n = min(n, *ndev);  // device count of the mapped columns
+  if (col0 >= n) return;
   const int kbeg = blockIdx.z * kchunk;
   const int kend = min(k, kbeg + kchunk);
   R acc[TM][4];
@@ -163,7 +166,9 @@ __global__ void __launch_bounds__(256) k_gemm(int m, int n, int k, R alpha, cons
 }
 
 template <typename R>
-__global__ void k_scale_mat(R* C, long long ldc, int m, int n, R beta, const int* cmap) {
+__global__ void k_scale_mat(R* C, long long ldc, int m, int n, R beta, const int* cmap,
+                            const int* ndev) {
+  if (ndev) n = min(n, *ndev);
   const long long tot = (long long)m * n;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
        e += (long long)gridDim.x * blockDim.x) {
@@ -176,7 +181,7 @@ __global__ void k_scale_mat(R* C, long long ldc, int m, int n, R beta, const int
 template <typename R>
 cudaError_t gemm(bool transA, int m, int n, int k, double alpha, const R* A, long long lda,
                  const R* B, long long ldb, double beta, R* C, long long ldc, cudaStream_t st,
-                 const int* bmap, const int* cmap) {
+                 const int* bmap, const int* cmap, const int* ndev) {
   if (m <= 0 || n <= 0) return cudaSuccess;
   // 80-row tiles when they pad m less than 64-row tiles do
   const bool t80 = ((m + 79) / 80) * 80 < ((m + 63) / 64) * 64;
@@ -199,39 +204,40 @@ cudaError_t gemm(bool transA, int m, int n, int k, double alpha, const R* A, lon
     const long long tot = (long long)m * n;
     const int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
     count_launch();
-    k_scale_mat<R><<<blocks, 256, 0, st>>>(C, ldc, m, n, (R)beta, cmap);
+    k_scale_mat<R><<<blocks, 256, 0, st>>>(C, ldc, m, n, (R)beta, cmap, ndev);
     if (k <= 0) return cudaGetLastError();
     atomic = 1;
   }
   dim3 grid(tm, tn, splits);
   ProfScope ps(sizeof(R) == 8 ? PC_GEMM_F64 : PC_GEMM_F32, st, 2.0 * m * n * (double)k,
-               ((double)m * k + (double)k * n + (beta != 0.0 ? 2.0 : 1.0) * m * n) * sizeof(R));
+               ((double)m * k + (double)k * n + (beta != 0.0 ? 2.0 : 1.0) * m * n) * sizeof(R),
+               ndev, n);
   count_launch();
   const R al = (R)alpha, be = (R)beta;
   if (transA) {
     if (t80)
       k_gemm<R, true, 5><<<grid, 256, 0, st>>>(m, n, k, al, A, lda, B, ldb, be, C, ldc, kchunk,
-                                               atomic, bmap, cmap);
+                                               atomic, bmap, cmap, ndev);
     else
       k_gemm<R, true, 4><<<grid, 256, 0, st>>>(m, n, k, al, A, lda, B, ldb, be, C, ldc, kchunk,
-                                               atomic, bmap, cmap);
+                                               atomic, bmap, cmap, ndev);
   } else {
     if (t80)
       k_gemm<R, false, 5><<<grid, 256, 0, st>>>(m, n, k, al, A, lda, B, ldb, be, C, ldc, kchunk,
-                                                atomic, bmap, cmap);
+                                                atomic, bmap, cmap, ndev);
     else
       k_gemm<R, false, 4><<<grid, 256, 0, st>>>(m, n, k, al, A, lda, B, ldb, be, C, ldc, kchunk,
-                                                atomic, bmap, cmap);
+                                                atomic, bmap, cmap, ndev);
   }
   return cudaGetLastError();
 }
 
 template cudaError_t gemm<double>(bool, int, int, int, double, const double*, long long,
                                   const double*, long long, double, double*, long long,
-                                  cudaStream_t, const int*, const int*);
+                                  cudaStream_t, const int*, const int*, const int*);
 template cudaError_t gemm<float>(bool, int, int, int, double, const float*, long long,
                                  const float*, long long, double, float*, long long, cudaStream_t,
-                                 const int*, const int*);
+                                 const int*, const int*, const int*);
 
 // ---------------------------------------------------------------------------
 // one-sided Jacobi eigensolver
@@ -532,6 +538,8 @@ template cudaError_t convert<double, double>(double*, long long, const double*, 
                                              cudaStream_t);
 template cudaError_t convert<float, double>(float*, long long, const double*, long long, int, int,
                                             cudaStream_t);
+template cudaError_t convert<df, double>(df*, long long, const double*, long long, int, int,
+                                         cudaStream_t);
 template cudaError_t convert<double, float>(double*, long long, const float*, long long, int, int,
                                             cudaStream_t);
 
@@ -1180,6 +1188,14 @@ cudaError_t build_precond(const double* g2, int n_half, int n_pw, const double* 
 template <typename R>
 __global__ void k_cg_start(CgArgs<R> a, const R* __restrict__ b, long long ldb) {
   const int i = blockIdx.x;
+  if (a.mask && a.mask[i] == 0.0) {
+    // not part of this solve (a converged RHS of a refinement round)
+    if (threadIdx.x == 0) {
+      CgScal s{};
+      a.sc[i] = s;
+    }
+    return;
+  }
   const long long o = (long long)i * a.ld;
   const R* K = a.kprec + (long long)(i % a.n_occ) * a.ld;
   R bb = R(0), rz = R(0);
@@ -1228,6 +1244,7 @@ __device__ __forceinline__ void cg_finish(const CgArgs<R>& a, int i, const CgSca
 // per-thread partial sums are promoted to FP64 for the block reductions.
 template <typename R, int E>
 __global__ void __launch_bounds__(512) k_cg_step_reg(CgArgs<R> a, const int* __restrict__ list) {
+  if (a.list_count && (int)blockIdx.x >= *a.list_count) return;
   const int i = list ? list[blockIdx.x] : blockIdx.x;
   __shared__ CgScal s;
   __shared__ R coef[2];  // alpha, then beta
@@ -1303,6 +1320,7 @@ __global__ void __launch_bounds__(512) k_cg_step_reg(CgArgs<R> a, const int* __r
 // fewer registers, so more RHS in flight per SM than the cached variant.
 template <typename R>
 __global__ void __launch_bounds__(512) k_cg_step(CgArgs<R> a, const int* __restrict__ list) {
+  if (a.list_count && (int)blockIdx.x >= *a.list_count) return;
   const int i = list ? list[blockIdx.x] : blockIdx.x;
   __shared__ CgScal s;
   __shared__ R coef[2];
@@ -1363,7 +1381,7 @@ cudaError_t cg_step(const CgArgs<R>& a, const int* list, int n_list, cudaStream_
   if (nb <= 0) return cudaSuccess;
   // x, r, p, Ap read once; x, r, p written once: 7 vector passes per active RHS
   ProfScope ps(sizeof(R) == 8 ? PC_CG_F64 : PC_CG_F32, st, 12.0 * nb * (double)a.n_pw,
-               7.0 * nb * (double)a.n_pw * sizeof(R));
+               7.0 * nb * (double)a.n_pw * sizeof(R), list ? a.list_count : nullptr, nb);
   count_launch();
   int v = a.variant;
   if ((v == CG_REG256 && a.n_pw > 16 * 256) || (v == CG_REG512 && a.n_pw > 16 * 512))
@@ -1404,22 +1422,143 @@ __device__ void compact_block(int n, Pred pred, int* list, int* count) {
     if (pred(i)) list[o++] = i;
   if (threadIdx.x == T - 1) *count = offs[T - 1];
 }
-__global__ void k_active_list(const CgScal* __restrict__ sc, int n, int* list, int* count) {
+__global__ void k_active_list(const CgScal* __restrict__ sc, int n, int* list, int* count,
+                              int* reset) {
   compact_block(n, [&](int i) { return sc[i].active != 0; }, list, count);
+  if (reset && threadIdx.x == 0) *reset = 0;
 }
 __global__ void k_unconv_list(const double* __restrict__ rel, double tol, int n, int* list,
-                              int* count) {
+                              int* count, int* rounds) {
   compact_block(n, [&](int i) { return rel[i] > tol; }, list, count);
+  if (rounds && threadIdx.x == blockDim.x - 1 && *count > 0) *rounds += 1;
 }
 cudaError_t active_list(const CgScal* sc, int n, int* list, int* count, cudaStream_t st) {
   count_launch();
-  k_active_list<<<1, 1024, 0, st>>>(sc, n, list, count);
+  k_active_list<<<1, 1024, 0, st>>>(sc, n, list, count, nullptr);
+  return cudaGetLastError();
+}
+cudaError_t active_list_reset(const CgScal* sc, int n, int* list, int* count, int* reset,
+                              cudaStream_t st) {
+  count_launch();
+  k_active_list<<<1, 1024, 0, st>>>(sc, n, list, count, reset);
   return cudaGetLastError();
 }
 cudaError_t unconverged_list(const double* rel, double tol, int n, int* list, int* count,
-                             cudaStream_t st) {
+                             cudaStream_t st, int* rounds) {
   count_launch();
-  k_unconv_list<<<1, 1024, 0, st>>>(rel, tol, n, list, count);
+  k_unconv_list<<<1, 1024, 0, st>>>(rel, tol, n, list, count, rounds);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// device-side loop control and statistics of the Sternheimer solves
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__global__ void k_loop_begin(CgLoopState* ls, int max_iter, cudaGraphConditionalHandle h,
+                             int has_handle) {
+  ls->iter = 0;
+  ls->t0 = global_ns();
+  const int go = (ls->active > 0 && max_iter > 0) ? 1 : 0;
+  ls->go = go;
+  if (has_handle) cudaGraphSetConditional(h, go);
+}
+__global__ void k_loop_next(CgLoopState* ls, int max_iter, unsigned long long budget_ns,
+                            unsigned* status, int prec, cudaGraphConditionalHandle h,
+                            int has_handle) {
+  const int it = ls->iter + 1;
+  ls->iter = it;
+  ls->steps[prec] += 1;
+  const bool active = ls->active > 0;
+  bool go = active && it < max_iter;
+  if (go && budget_ns > 0 && global_ns() - ls->t0 > budget_ns) {
+    go = false;
+    atomicOr(status, (unsigned)DEV_TIMEOUT);
+  }
+  ls->go = go ? 1 : 0;
+  if (has_handle) cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+cudaError_t loop_begin(CgLoopState* ls, int max_iter, cudaGraphConditionalHandle h, int has_handle,
+                       cudaStream_t st) {
+  count_launch();
+  k_loop_begin<<<1, 1, 0, st>>>(ls, max_iter, h, has_handle);
+  return cudaGetLastError();
+}
+cudaError_t loop_next(CgLoopState* ls, int max_iter, unsigned long long budget_ns,
+                      unsigned* status, int prec, cudaGraphConditionalHandle h, int has_handle,
+                      cudaStream_t st) {
+  count_launch();
+  k_loop_next<<<1, 1, 0, st>>>(ls, max_iter, budget_ns, status, prec, h, has_handle);
+  return cudaGetLastError();
+}
+
+__global__ void k_cg_collect(const CgScal* __restrict__ sc, int n, int* its_total, DevStats* ds) {
+  unsigned long long sum = 0;
+  int mx = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int it = sc[i].iters;
+    if (its_total) its_total[i] += it;
+    sum += (unsigned long long)it;
+    mx = max(mx, it);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (sum) atomicAdd(&ds->cg_iters, sum);
+    if (mx) atomicMax(&ds->cg_max, mx);
+  }
+}
+cudaError_t cg_collect(const CgScal* sc, int n, int* its_total, DevStats* ds, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  count_launch();
+  const int blocks = std::min((n + 255) / 256, 4 * num_sms());
+  k_cg_collect<<<blocks, 256, 0, st>>>(sc, n, its_total, ds);
+  return cudaGetLastError();
+}
+
+__global__ void k_solve_finish(const double* __restrict__ rel, int n, double tol, DevStats* ds,
+                               unsigned* status) {
+  double mx = 0.0;
+  int bad = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double r = rel[i];
+    if (!(r <= tol)) bad = 1;
+    if (r > mx || r != r) mx = (r != r) ? INFINITY : r;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    // non-negative doubles order like their bit patterns
+    atomicMax(&ds->max_res_bits, (unsigned long long)__double_as_longlong(mx));
+    if (bad) atomicOr(status, (unsigned)DEV_NOT_CONVERGED);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicMax(&ds->refine_max, ds->rounds_cur);
+}
+cudaError_t solve_finish(const double* rel, int n, double tol, DevStats* ds, unsigned* status,
+                         cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  count_launch();
+  const int blocks = std::min((n + 255) / 256, 4 * num_sms());
+  k_solve_finish<<<blocks, 256, 0, st>>>(rel, n, tol, ds, status);
+  return cudaGetLastError();
+}
+
+__global__ void k_fill_value(double* x, int n, double v) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = v;
+}
+cudaError_t fill_value(double* x, int n, double v, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  count_launch();
+  k_fill_value<<<std::min((n + 255) / 256, 1024), 256, 0, st>>>(x, n, v);
   return cudaGetLastError();
 }
 
@@ -1501,7 +1640,8 @@ __global__ void k_residual_update(double* r, const double* __restrict__ ad,
                                   const double* __restrict__ b, long long ld, int n_pw,
                                   double* rel, const int* __restrict__ list,
                                   const double* __restrict__ xd, const double* __restrict__ sv,
-                                  int n_occ) {
+                                  int n_occ, const int* __restrict__ ndev) {
+  if (ndev && (int)blockIdx.x >= *ndev) return;
   const int i = list ? list[blockIdx.x] : blockIdx.x;
   const long long o = (long long)i * ld;
   const double s = xd ? sv[i % n_occ] : 0.0;
@@ -1519,11 +1659,11 @@ __global__ void k_residual_update(double* r, const double* __restrict__ ad,
 }
 cudaError_t residual_update(double* r, const double* ad, const double* b, long long ld, int n_pw,
                             int n, double* rel, const int* list, const double* xd,
-                            const double* sv, int n_occ, cudaStream_t st) {
+                            const double* sv, int n_occ, cudaStream_t st, const int* ndev) {
   if (n <= 0) return cudaSuccess;
   {
     count_launch();
-    k_residual_update<<<n, 256, 0, st>>>(r, ad, b, ld, n_pw, rel, list, xd, sv, n_occ);
+    k_residual_update<<<n, 256, 0, st>>>(r, ad, b, ld, n_pw, rel, list, xd, sv, n_occ, ndev);
   }
   return cudaGetLastError();
 }

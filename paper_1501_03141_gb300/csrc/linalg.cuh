@@ -7,16 +7,20 @@
 #include <vector>
 
 #include "common.cuh"
+#include "df64.cuh"
 
 namespace pdep {
 
 // C[m x n] = alpha * op(A)[m x k] * B[k x n] + beta * C, op(A) = A^T if transA.
 // Split over k (atomic accumulation) when the tile count is small.  Optional
 // column maps: column j of B is B[:, bmap[j]] and column j of C is C[:, cmap[j]].
+// ndev (optional): device count of the mapped columns (<= n); the launch is
+// sized for n and columns from *ndev on are left untouched.
 template <typename R>
 cudaError_t gemm(bool transA, int m, int n, int k, double alpha, const R* A, long long lda,
                  const R* B, long long ldb, double beta, R* C, long long ldc, cudaStream_t st,
-                 const int* bmap = nullptr, const int* cmap = nullptr);
+                 const int* bmap = nullptr, const int* cmap = nullptr,
+                 const int* ndev = nullptr);
 
 // Symmetric eigendecomposition of the n x n matrix M (lda), FP64:
 // one-sided (Hestenes) Jacobi on M - sigma I (sigma = twice the Gershgorin
@@ -119,12 +123,13 @@ cudaError_t fill_zero(void* p, size_t bytes, cudaStream_t st);
 // Y(:, cmap) (M x N) += P (M x K) S (K x N, lds)
 // Rows of P, X, Y and S must start on 16-byte boundaries (ldp, ldx, lds
 // multiples of 4 floats; aligned bases).
+// ndev (optional): device count of the mapped columns (<= N).
 cudaError_t tc_proj_coeffs(int M, int N, int K, const float* P, long long ldp, const float* X,
                            long long ldx, const int* bmap, const float* sigma, float* S,
-                           long long lds, cudaStream_t st);
+                           long long lds, cudaStream_t st, const int* ndev = nullptr);
 cudaError_t tc_proj_update(int M, int N, int K, const float* P, long long ldp, const float* S,
                            long long lds, float* Y, long long ldy, const int* cmap,
-                           cudaStream_t st);
+                           cudaStream_t st, const int* ndev = nullptr);
 
 // Per-RHS preconditioned CG kernels (one CTA per RHS vector).
 // State of one RHS: x, r, p (length n_pw, stride ld), scalars in CgScal.
@@ -152,7 +157,49 @@ struct CgArgs {
   unsigned* status;
   int* n_active;        // counter (atomic) of RHS still active after the step
   int variant;          // CgVariant (picked by the autotuner)
+  const int* list_count = nullptr;  // device length of the active list (cg_step sized for
+                                    // the largest; blocks past it exit)
+  const double* mask = nullptr;     // cg_start: RHS i takes part only if mask[i] != 0
 };
+
+// Device state of one Sternheimer CG loop (context-owned device memory).
+// The loop runs on the device: a control kernel after every step decides
+// whether another step follows (CUDA-graph while node, or a flag the host
+// reads in the eager form).
+struct CgLoopState {
+  int active;                     // RHS still active after the last step (cg_step adds)
+  int listed;                     // length of the compacted active list
+  int iter;                       // steps done in this loop
+  int go;                         // 1 while another step is due
+  unsigned long long t0;          // %globaltimer (ns) at the loop start
+  unsigned long long steps[2];    // steps over all loops (FP32, FP64), for launch counts
+};
+// Device statistics of the Sternheimer solves since the last reset.
+struct DevStats {
+  unsigned long long cg_iters;      // CG iterations summed over RHS (all rounds)
+  unsigned long long max_res_bits;  // largest final relative FP64 residual (bits of a double >= 0)
+  int cg_max;                       // largest per-RHS iteration count of one CG loop
+  int refine_max;                   // largest refinement-round count of one solve
+  int rounds_cur;                   // rounds with unconverged RHS in the current solve
+  int pad;
+};
+// Loop control: begin (iter = 0, go = active > 0 && max_iter > 0) and the
+// step after each CG step (iter += 1; go = active > 0 && iter < max_iter &&
+// elapsed <= budget_ns; a spent budget with RHS still active sets
+// DEV_TIMEOUT).  With a graph handle (has_handle) the decision also drives
+// the enclosing while node.  prec selects the launch-count slot (0 FP32, 1 FP64).
+cudaError_t loop_begin(CgLoopState* ls, int max_iter, cudaGraphConditionalHandle h, int has_handle,
+                       cudaStream_t st);
+cudaError_t loop_next(CgLoopState* ls, int max_iter, unsigned long long budget_ns,
+                      unsigned* status, int prec, cudaGraphConditionalHandle h, int has_handle,
+                      cudaStream_t st);
+// After a CG loop: its_total[i] += sc[i].iters (its_total may be null), and
+// the sum / largest count into ds.
+cudaError_t cg_collect(const CgScal* sc, int n, int* its_total, DevStats* ds, cudaStream_t st);
+// End of a solve: ds->max_res = max(ds->max_res, max_i rel[i]); any rel[i] > tol
+// sets DEV_NOT_CONVERGED; ds->refine_max = max(refine_max, rounds_cur).
+cudaError_t solve_finish(const double* rel, int n, double tol, DevStats* ds, unsigned* status,
+                         cudaStream_t st);
 // launch shapes of one CG step: register-cached (the RHS read once) or
 // streaming (three passes, more RHS resident per SM)
 enum CgVariant : int {
@@ -174,9 +221,14 @@ cudaError_t build_precond(const double* g2, int n_half, int n_pw, const double* 
 
 // Ordered list of the RHS with sc[i].active (list[0..count)), one block.
 cudaError_t active_list(const CgScal* sc, int n, int* list, int* count, cudaStream_t st);
-// Ordered list of i with rel[i] > tol.
+// Ordered list of i with rel[i] > tol; a non-empty list adds 1 to *rounds
+// (may be null).
 cudaError_t unconverged_list(const double* rel, double tol, int n, int* list, int* count,
-                             cudaStream_t st);
+                             cudaStream_t st, int* rounds = nullptr);
+// Ordered active list as active_list, also zeroing *reset (the step counter
+// cg_step accumulates into).
+cudaError_t active_list_reset(const CgScal* sc, int n, int* list, int* count, int* reset,
+                              cudaStream_t st);
 
 // Mixed-precision refinement: for i with rel[i] > tol, rn[i] = ||r64_i|| and
 // r32_i = r64_i / rn[i]; otherwise rn[i] = 0 and r32_i = 0.
@@ -190,10 +242,14 @@ cudaError_t refine_accumulate(double* x64, long long ld64, const float* d32, lon
 // dl_i = delta_i; with d32 = null, delta_i = x_i + xd_i and x_i = delta_i.
 cudaError_t refine_delta(double* x, double* dl, long long ld, const float* d32, long long ld32,
                          int n_pw, int n, const double* rn, const double* xd, cudaStream_t st);
-// r_i -= ad_i (+ sv[i % n_occ] xd_i); rel_i = ||r_i|| / ||b_i|| (listed vectors)
+// r_i -= ad_i (+ sv[i % n_occ] xd_i); rel_i = ||r_i|| / ||b_i|| (listed vectors;
+// ndev: device length of the list, <= n)
 cudaError_t residual_update(double* r, const double* ad, const double* b, long long ld, int n_pw,
                             int n, double* rel, const int* list, const double* xd,
-                            const double* sv, int n_occ, cudaStream_t st);
+                            const double* sv, int n_occ, cudaStream_t st,
+                            const int* ndev = nullptr);
+// rel[i] = v for i < n
+cudaError_t fill_value(double* rel, int n, double v, cudaStream_t st);
 // Kinetic energy sum_k |G_k|^2/2 (x_2k^2 + x_2k+1^2) of each column.
 cudaError_t kinetic_energy(const double* X, long long ld, int n_half, int n, const double* g2,
                            double* out, cudaStream_t st);

@@ -1,4 +1,5 @@
 // Kernel profiler of the library (see profile.cuh and pdep_profile in pdep.h).
+#include <algorithm>
 #include <atomic>
 #include <cstring>
 #include <list>
@@ -15,14 +16,20 @@ struct Rec {
   cudaEvent_t a, b;
   double flops, bytes;
   bool closed;  // the end event has been recorded
+  int* slot;    // device copy of the launch's unit count (or null)
+  int units;
 };
 struct Acc {
   long long launches = 0;
   double ms = 0, flops = 0, bytes = 0;
 };
-const char* kNames[PDEP_PROFILE_CLASSES] = {"cols_f64", "cols_f32", "slab_f64", "slab_f32",
-                                            "gemm_f64", "gemm_f32", "cg_f64",   "cg_f32",
-                                            "eigh",     "other",    "gemm_tf32x3"};
+const char* kNames[PDEP_PROFILE_CLASSES] = {"cols_f64", "cols_f32",    "slab_f64",    "slab_f32",
+                                            "gemm_f64", "gemm_f32",    "cg_f64",      "cg_f32",
+                                            "eigh",     "other",       "gemm_tf32x3", "cg_graph_f32",
+                                            "cg_graph_f64", "cols_df64", "slab_df64"};
+thread_local bool t_capturing = false;
+thread_local int t_capture_launches = 0;
+std::atomic<long long> g_launches{0};
 // Shared by every host thread that launches library kernels (the lanes of a
 // chi0bar application): the record list and the event pool are guarded by mu;
 // list nodes keep their addresses, so a scope can close its record later.
@@ -33,6 +40,22 @@ struct Profiler {
   std::list<Rec> pending;
   std::vector<cudaEvent_t> pool;
   Acc acc[PDEP_PROFILE_CLASSES];
+  std::vector<int*> slots;  // free device ints for unit counts (chunks of 4096)
+  std::vector<int*> chunks;
+  int* slot() {
+    if (slots.empty()) {
+      int* p = nullptr;
+      if (cudaMalloc(&p, 4096 * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+      }
+      chunks.push_back(p);
+      for (int i = 0; i < 4096; ++i) slots.push_back(p + i);
+    }
+    int* p = slots.back();
+    slots.pop_back();
+    return p;
+  }
   cudaEvent_t get() {
     if (!pool.empty()) {
       cudaEvent_t e = pool.back();
@@ -53,13 +76,23 @@ struct Profiler {
       Rec& r = *it;
       float ms = 0.f;
       if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+        double f = 1.0;
+        if (r.slot) {
+          int n = 0;
+          if (cudaMemcpy(&n, r.slot, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && r.units > 0)
+            f = std::min(1.0, std::max(0.0, (double)n / r.units));
+          else
+            cudaGetLastError();
+          slots.push_back(r.slot);
+        }
         Acc& a = acc[r.cls];
         a.launches += 1;
         a.ms += ms;
-        a.flops += r.flops;
-        a.bytes += r.bytes;
+        a.flops += f * r.flops;
+        a.bytes += f * r.bytes;
       } else {
         cudaGetLastError();
+        if (r.slot) slots.push_back(r.slot);
       }
       pool.push_back(r.a);
       pool.push_back(r.b);
@@ -74,14 +107,40 @@ Profiler& prof() {
 }  // namespace
 
 void count_launch() {
+  if (t_capturing) {
+    ++t_capture_launches;
+    return;
+  }
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   Profiler& p = prof();
   if (p.on) p.launches.fetch_add(1, std::memory_order_relaxed);
 }
 
-ProfScope::ProfScope(int c, cudaStream_t s, double f, double b)
+void capture_begin() {
+  t_capturing = true;
+  t_capture_launches = 0;
+}
+
+int capture_end() {
+  t_capturing = false;
+  return t_capture_launches;
+}
+
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+// records nothing while the stream is being captured (events cannot time a
+// kernel inside a graph, and resolving records waits on events, which a
+// capture forbids)
+ProfScope::ProfScope(int c, cudaStream_t s, double f, double b, const int* dcount, int units)
     : cls(c), st(s), flops(f), bytes(b), rec(nullptr) {
   Profiler& p = prof();
-  if (!p.on) return;
+  if (!p.on || t_capturing) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  if (cs != cudaStreamCaptureStatusNone) return;
   std::lock_guard<std::mutex> g(p.mu);
   if (p.pending.size() >= 8192) p.resolve();
   Rec r;
@@ -91,6 +150,12 @@ ProfScope::ProfScope(int c, cudaStream_t s, double f, double b)
   r.flops = f;
   r.bytes = b;
   r.closed = false;
+  r.slot = nullptr;
+  r.units = units;
+  if (dcount && units > 0) {
+    r.slot = p.slot();
+    if (r.slot) cudaMemcpyAsync(r.slot, dcount, sizeof(int), cudaMemcpyDeviceToDevice, s);
+  }
   cudaEventRecord(r.a, s);
   p.pending.push_back(r);
   rec = &p.pending.back();

@@ -17,14 +17,29 @@ enum ProfClass : int {
   PC_EIGH = 8,
   PC_OTHER = 9,
   PC_GEMM_TF32 = 10,  // tensor-core (3xTF32) FP32 projections
+  PC_CG_GRAPH_F32 = 11,  // whole captured CG loops (FP32 steps; their kernels are not
+  PC_CG_GRAPH_F64 = 12,  // timed one by one inside a graph)
+  PC_COLS_DF = 13,       // double-float transforms (mixed-precision refinement)
+  PC_SLAB_DF = 14,
 };
 
-// counts one kernel launch (always cheap)
+// counts one kernel launch (always cheap); while this thread captures a
+// graph the launches are counted for the capture instead (capture_end
+// returns that count) and ProfScope records nothing
 void count_launch();
+void capture_begin();
+int capture_end();
+// kernels launched by this process outside graph captures (always counted)
+long long launch_count();
 
-// RAII timer around one launch: events are recorded only while profiling
+// RAII timer around one launch: events are recorded only while profiling.
+// flops and bytes are those of a launch over 'units' work units; when the
+// launch reads its unit count from the device (dcount), that count is
+// copied aside with the launch and the counts are scaled by dcount/units
+// when the record is resolved.
 struct ProfScope {
-  ProfScope(int cls, cudaStream_t st, double flops, double bytes);
+  ProfScope(int cls, cudaStream_t st, double flops, double bytes, const int* dcount = nullptr,
+            int units = 0);
   ~ProfScope();
   int cls;
   cudaStream_t st;

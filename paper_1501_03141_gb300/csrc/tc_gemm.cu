@@ -69,12 +69,14 @@ __global__ void __launch_bounds__(128)
     k_tc_coeffs(int M, int N, int K, const float* __restrict__ P, long long ldp,
                 const float* __restrict__ X, long long ldx, const int* __restrict__ bmap,
                 const float* __restrict__ sigma, float* __restrict__ S, long long lds,
-                int kchunk) {
+                int kchunk, const int* __restrict__ ndev) {
   __shared__ __align__(16) float As[2][C_BM][C_PAD];
   __shared__ __align__(16) float Bs[2][C_BN][C_PAD];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, t = lane & 3;
   const int row0 = blockIdx.x * C_BM, col0 = blockIdx.y * C_BN;
+  if (ndev) N = min(N, *ndev);  // device count of the mapped columns
+  if (col0 >= N) return;
   const int kbeg = blockIdx.z * kchunk;
   const int kend = min(K, kbeg + kchunk);
 
@@ -188,13 +190,15 @@ constexpr int U_BM = 64, U_BN = 64, U_BK = 16, U_APAD = 72, U_BPAD = 20;
 __global__ void __launch_bounds__(128)
     k_tc_update(int M, int N, int K, const float* __restrict__ P, long long ldp,
                 const float* __restrict__ S, long long lds, float* __restrict__ Y, long long ldy,
-                const int* __restrict__ cmap) {
+                const int* __restrict__ cmap, const int* __restrict__ ndev) {
   __shared__ __align__(16) float As[2][U_BK][U_APAD];  // A(r, w) at As[w][r]
   __shared__ __align__(16) float Bs[2][U_BN][U_BPAD];  // B(w, j) at Bs[j][w]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, t = lane & 3;
   const int wm = warp >> 1, wn = warp & 1;
   const int row0 = blockIdx.x * U_BM, col0 = blockIdx.y * U_BN;
+  if (ndev) N = min(N, *ndev);
+  if (col0 >= N) return;
 
   auto load = [&](int stage, int k0) {
     // A: 16 state columns x 16 chunks of 4 rows
@@ -303,7 +307,7 @@ __global__ void __launch_bounds__(128)
 
 cudaError_t tc_proj_coeffs(int M, int N, int K, const float* P, long long ldp, const float* X,
                            long long ldx, const int* bmap, const float* sigma, float* S,
-                           long long lds, cudaStream_t st) {
+                           long long lds, cudaStream_t st, const int* ndev) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   dim3 grid((M + C_BM - 1) / C_BM, (N + C_BN - 1) / C_BN);
   if (grid.y > 65535) return cudaErrorInvalidValue;
@@ -320,22 +324,22 @@ cudaError_t tc_proj_coeffs(int M, int N, int K, const float* P, long long ldp, c
   cudaError_t e = cudaMemsetAsync(S, 0, sizeof(float) * (size_t)lds * N, st);
   if (e != cudaSuccess) return e;
   ProfScope ps(PC_GEMM_TF32, st, 2.0 * M * N * (double)K,
-               ((double)M * K + (double)K * N + (double)M * N) * sizeof(float));
+               ((double)M * K + (double)K * N + (double)M * N) * sizeof(float), ndev, N);
   count_launch();
-  k_tc_coeffs<<<grid, 128, 0, st>>>(M, N, K, P, ldp, X, ldx, bmap, sigma, S, lds, kchunk);
+  k_tc_coeffs<<<grid, 128, 0, st>>>(M, N, K, P, ldp, X, ldx, bmap, sigma, S, lds, kchunk, ndev);
   return cudaGetLastError();
 }
 
 cudaError_t tc_proj_update(int M, int N, int K, const float* P, long long ldp, const float* S,
                            long long lds, float* Y, long long ldy, const int* cmap,
-                           cudaStream_t st) {
+                           cudaStream_t st, const int* ndev) {
   if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
   dim3 grid((M + U_BM - 1) / U_BM, (N + U_BN - 1) / U_BN);
   if (grid.y > 65535) return cudaErrorInvalidValue;
   ProfScope ps(PC_GEMM_TF32, st, 2.0 * M * N * (double)K,
-               ((double)M * K + (double)K * N + 2.0 * M * N) * sizeof(float));
+               ((double)M * K + (double)K * N + 2.0 * M * N) * sizeof(float), ndev, N);
   count_launch();
-  k_tc_update<<<grid, 128, 0, st>>>(M, N, K, P, ldp, S, lds, Y, ldy, cmap);
+  k_tc_update<<<grid, 128, 0, st>>>(M, N, K, P, ldp, S, lds, Y, ldy, cmap, ndev);
   return cudaGetLastError();
 }
 

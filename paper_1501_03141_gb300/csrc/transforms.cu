@@ -1,5 +1,9 @@
 // Plane-wave sphere <-> grid transforms (see transforms.cuh for the scheme).
 #include <atomic>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <type_traits>
 
 #include "fft.cuh"
 #include "transforms.cuh"
@@ -12,6 +16,7 @@ cudaError_t upload_local_twiddles() {
   static const int sizes[] = {6, 8, 10, 12, 16, 20, 24, 32, 48, 64};
   double2 hd[LOCAL_TW_SIZE];
   float2 hf[LOCAL_TW_SIZE];
+  float4 hdf[LOCAL_TW_SIZE];
   const double two_pi = 6.283185307179586476925286766559;
   for (int M : sizes) {
     int off = local_tw_offset(M);
@@ -19,9 +24,13 @@ cudaError_t upload_local_twiddles() {
       double a = two_pi * (double)j / (double)M;
       hd[off + j] = make_double2(cos(a), sin(a));
       hf[off + j] = make_float2((float)cos(a), (float)sin(a));
+      const df re(cos(a)), im(sin(a));
+      hdf[off + j] = make_float4(re.hi, re.lo, im.hi, im.lo);
     }
   }
   cudaError_t e = cudaMemcpyToSymbol(c_local_tw_d, hd, sizeof(hd));
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyToSymbol(c_local_tw_df, hdf, sizeof(hdf));
   if (e != cudaSuccess) return e;
   return cudaMemcpyToSymbol(c_local_tw_f, hf, sizeof(hf));
 }
@@ -45,6 +54,12 @@ bool grid_supported(int N1, int N2, int N3) {
   return n1 && (cube || slab);
 }
 
+// profile class of a launch by arithmetic type
+template <typename R>
+static int prof_class(int f64, int f32, int fdf) {
+  return std::is_same<R, df>::value ? fdf : std::is_same<R, float>::value ? f32 : f64;
+}
+
 static __device__ __forceinline__ int iabs(int a) { return a < 0 ? -a : a; }
 
 template <typename R>
@@ -52,7 +67,7 @@ __device__ __forceinline__ cpx<R> zero() { return mk(R(0), R(0)); }
 
 template <typename R>
 __device__ __forceinline__ R coef_of(int kind, const double* __restrict__ g2, int k) {
-  if (kind == COEF_SQRT_COULOMB) return (R)sqrt(12.566370614359172953850573533118 / g2[k]);
+  if (kind == COEF_SQRT_COULOMB) return R(sqrt(12.566370614359172953850573533118 / g2[k]));
   return R(1);
 }
 
@@ -60,23 +75,46 @@ __device__ __forceinline__ R coef_of(int kind, const double* __restrict__ g2, in
 // column pass: sphere -> x-lines (inverse transform, S = +1)
 // ---------------------------------------------------------------------------
 template <typename R, int N1>
-__global__ void __launch_bounds__(128) k_cols_fwd(SphereDev<R> s, const R* __restrict__ x,
+__device__ __forceinline__ void cols_fwd_line(const SphereDev<R>& s,
+                                              const typename Io<R>::T* __restrict__ x,
+                                              long long ldx, const ItemMap& map, int nl,
+                                              int coef, cpx<R>* __restrict__ b1, long long g,
+                                              long long total);
+
+template <typename R, int N1>
+__global__ void __launch_bounds__(128) k_cols_fwd(SphereDev<R> s,
+                                                  const typename Io<R>::T* __restrict__ x,
                                                   long long ldx, ItemMap map, int n_items,
                                                   int coef, cpx<R>* __restrict__ b1) {
+  const int nl = listed_count(map);
+  const long long total = (long long)items_of(map, n_items, nl) * s.n_ucol;
+  const int per = blockDim.x / Tpl<R, N1>::v;
+  // the launch covers the largest count; blocks past the device count exit
+  // (a grid-stride loop here costs 40-70% more registers)
+  const long long g0 = (long long)blockIdx.x * per;
+  if (g0 < total)
+    cols_fwd_line<R, N1>(s, x, ldx, map, nl, coef, b1, g0 + threadIdx.x / Tpl<R, N1>::v, total);
+}
+
+template <typename R, int N1>
+__device__ __forceinline__ void cols_fwd_line(const SphereDev<R>& s,
+                                              const typename Io<R>::T* __restrict__ x,
+                                              long long ldx, const ItemMap& map, int nl,
+                                              int coef, cpx<R>* __restrict__ b1, long long g,
+                                              long long total) {
   constexpr int TPL = Tpl<R, N1>::v;
   constexpr int M = N1 / TPL;
   const int t = threadIdx.x & (TPL - 1);
-  const long long g = (long long)blockIdx.x * (blockDim.x / TPL) + threadIdx.x / TPL;
-  const long long total = (long long)n_items * s.n_ucol;
   const bool live = g < total;
   const int item = live ? (int)(g / s.n_ucol) : 0;
   const int uc = live ? (int)(g - (long long)item * s.n_ucol) : 0;
   const UCol c = s.ucol[uc];
   const bool active = live && ucol_in_range(s, c);
   const bool self = (c.col == c.mcol);
-  const int ia = map.vec(item, 0), ib = map.vec(item, 1);
-  const R* xa = (active && ia >= 0) ? x + (long long)ia * ldx : nullptr;
-  const R* xb = (active && ib >= 0) ? x + (long long)ib * ldx : nullptr;
+  const int ia = map.vec(item, 0, nl), ib = map.vec(item, 1, nl);
+  using T = typename Io<R>::T;
+  const T* xa = (active && ia >= 0) ? x + (long long)ia * ldx : nullptr;
+  const T* xb = (active && ib >= 0) ? x + (long long)ib * ldx : nullptr;
   const R rs2 = R(0.70710678118654752440084436210485);
 
   cpx<R> v0[M], v1[M];
@@ -93,23 +131,23 @@ __global__ void __launch_bounds__(128) k_cols_fwd(SphereDev<R> s, const R* __res
         const int k2 = c.h0 - n1 + c.R1;
         const R w = coef_of<R>(coef, s.g2, k) * rs2;
         const R w2 = coef_of<R>(coef, s.g2, k2) * rs2;
-        cpx<R> A = xa ? mk(xa[2 * k] * w, xa[2 * k + 1] * w) : zero<R>();
-        cpx<R> B = xb ? mk(xb[2 * k] * w, xb[2 * k + 1] * w) : zero<R>();
+        cpx<R> A = xa ? mk(ld_io<R>(xa + 2 * k) * w, ld_io<R>(xa + 2 * k + 1) * w) : zero<R>();
+        cpx<R> B = xb ? mk(ld_io<R>(xb + 2 * k) * w, ld_io<R>(xb + 2 * k + 1) * w) : zero<R>();
         v0[i] = mk(A.x - B.y, A.y + B.x);
-        cpx<R> A2 = xa ? mk(xa[2 * k2] * w2, xa[2 * k2 + 1] * w2) : zero<R>();
-        cpx<R> B2 = xb ? mk(xb[2 * k2] * w2, xb[2 * k2 + 1] * w2) : zero<R>();
+        cpx<R> A2 = xa ? mk(ld_io<R>(xa + 2 * k2) * w2, ld_io<R>(xa + 2 * k2 + 1) * w2) : zero<R>();
+        cpx<R> B2 = xb ? mk(ld_io<R>(xb + 2 * k2) * w2, ld_io<R>(xb + 2 * k2 + 1) * w2) : zero<R>();
         v1[i] = mk(A2.x + B2.y, B2.x - A2.y);
       }
     } else {
       if (n1 == 0) {
         const R w = (coef == COEF_ONE) ? R(1) : R(0);
         const int k0 = 2 * s.n_half;
-        v0[i] = mk(xa ? xa[k0] * w : R(0), xb ? xb[k0] * w : R(0));
+        v0[i] = mk(xa ? ld_io<R>(xa + k0) * w : R(0), xb ? ld_io<R>(xb + k0) * w : R(0));
       } else if (iabs(n1) <= c.R1) {
         const int k = c.h0 + iabs(n1) - 1;
         const R w = coef_of<R>(coef, s.g2, k) * rs2;
-        cpx<R> A = xa ? mk(xa[2 * k] * w, xa[2 * k + 1] * w) : zero<R>();
-        cpx<R> B = xb ? mk(xb[2 * k] * w, xb[2 * k + 1] * w) : zero<R>();
+        cpx<R> A = xa ? mk(ld_io<R>(xa + 2 * k) * w, ld_io<R>(xa + 2 * k + 1) * w) : zero<R>();
+        cpx<R> B = xb ? mk(ld_io<R>(xb + 2 * k) * w, ld_io<R>(xb + 2 * k + 1) * w) : zero<R>();
         v0[i] = n1 > 0 ? mk(A.x - B.y, A.y + B.x) : mk(A.x + B.y, B.x - A.y);
       }
     }
@@ -133,25 +171,42 @@ __global__ void __launch_bounds__(128) k_cols_fwd(SphereDev<R> s, const R* __res
 template <typename R>
 __device__ __forceinline__ void write_out(const Epilogue<R>& ep, int vec, int j, R val, R coefv,
                                           R diag) {
-  R* y = ep.y + (long long)vec * ep.ldy;
+  typename Io<R>::T* y = ep.y + (long long)vec * ep.ldy;
   R r = ep.scale * coefv * val;
   if (ep.x_in) {
-    const R sh = ep.shift ? ep.shift[vec % ep.shift_period] : R(0);
-    r += (diag + sh) * ep.x_in[(long long)vec * ep.ldx + j];
+    const R sh = ep.shift ? ld_io<R>(ep.shift + vec % ep.shift_period) : R(0);
+    r += (diag + sh) * ld_io<R>(ep.x_in + (long long)vec * ep.ldx + j);
   }
-  if (ep.beta != R(0)) r += ep.beta * y[j];
-  y[j] = r;
+  if (ep.beta != 0) r += R(ep.beta) * ld_io<R>(y + j);
+  y[j] = io_of<R>(r);
 }
+
+template <typename R, int N1>
+__device__ __forceinline__ void cols_bwd_line(const SphereDev<R>& s,
+                                              const cpx<R>* __restrict__ b1, const ItemMap& map,
+                                              int nl, const Epilogue<R>& ep, long long g,
+                                              long long total);
 
 template <typename R, int N1>
 __global__ void __launch_bounds__(128) k_cols_bwd(SphereDev<R> s, const cpx<R>* __restrict__ b1,
                                                   ItemMap map, int n_items, Epilogue<R> ep) {
+  const int nl = listed_count(map);
+  const long long total = (long long)items_of(map, n_items, nl) * s.n_ucol;
+  const int per = blockDim.x / Tpl<R, N1>::v;
+  const long long g0 = (long long)blockIdx.x * per;
+  if (g0 < total)
+    cols_bwd_line<R, N1>(s, b1, map, nl, ep, g0 + threadIdx.x / Tpl<R, N1>::v, total);
+}
+
+template <typename R, int N1>
+__device__ __forceinline__ void cols_bwd_line(const SphereDev<R>& s,
+                                              const cpx<R>* __restrict__ b1, const ItemMap& map,
+                                              int nl, const Epilogue<R>& ep, long long g,
+                                              long long total) {
   constexpr int TPL = Tpl<R, N1>::v;
   constexpr int M = N1 / TPL;
   const int lane = threadIdx.x & 31;
   const int t = threadIdx.x & (TPL - 1);
-  const long long g = (long long)blockIdx.x * (blockDim.x / TPL) + threadIdx.x / TPL;
-  const long long total = (long long)n_items * s.n_ucol;
   const bool live = g < total;
   const int item = live ? (int)(g / s.n_ucol) : 0;
   const int uc = live ? (int)(g - (long long)item * s.n_ucol) : 0;
@@ -171,7 +226,7 @@ __global__ void __launch_bounds__(128) k_cols_bwd(SphereDev<R> s, const cpx<R>* 
   fft_b2a<R, N1, TPL, -1>(v1, t, s.tw1);
 
   const int src = (lane & ~(TPL - 1)) | ((TPL - t) & (TPL - 1));
-  const int ia = map.vec(item, 0), ib = map.vec(item, 1);
+  const int ia = map.vec(item, 0, nl), ib = map.vec(item, 1, nl);
   const R rs2 = R(0.70710678118654752440084436210485);
 #pragma unroll
   for (int i = 0; i < M; ++i) {
@@ -224,10 +279,17 @@ struct SlabThreads {
 // FP32 slabs keep three blocks of up to 256 threads per SM resident
 // (register budget ~85-110); FP64 slabs are bound by the FP64 pipe at one
 // block per SM.
+// Double-float slabs run on the FP32 pipe: two resident blocks per SM (at
+// most 170 registers for 192 threads) give its dependent add chains more
+// warps to hide latency behind.
 template <typename R, int N2, int N3>
 struct SlabMinBlocks {
   static constexpr int t = SlabThreads<R, N2, N3>::v;
-  static constexpr int v = sizeof(R) != 4 ? 1 : t <= 128 ? 384 / t : t <= 256 ? 3 : 1;
+  static constexpr int v = std::is_same<R, df>::value ? (t <= 192 ? 2 : 1)
+                           : sizeof(R) != 4                ? 1
+                           : t <= 128                      ? 384 / t
+                           : t <= 256                      ? 3
+                                                           : 1;
 };
 // Row stride of the (n3, i2) shared-memory plane (FP32 rows padded by 8
 // complex) and, in FP32, a column swizzle: element (row, col) sits at
@@ -308,22 +370,18 @@ __device__ __forceinline__ void y_forward(const SphereDev<R>& s, const cpx<R>* T
   }
 }
 
+// one x-plane i1 of one item
 template <typename R, int N2, int N3>
-__global__ void __launch_bounds__(SlabThreads<R, N2, N3>::v, (SlabMinBlocks<R, N2, N3>::v))
-    k_slab(SphereDev<R> s, SlabArgs<R> a) {
+__device__ __forceinline__ void slab_unit(const SphereDev<R>& s, const SlabArgs<R>& a, int nl,
+                                          int item, int i1, cpx<R>* S1, cpx<R>* T2) {
   constexpr int TL3 = Tpl<R, N3>::v;
   constexpr int M3 = N3 / TL3;
   constexpr int TS = T2Stride<R, N2>::v;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cpx<R>* S1 = reinterpret_cast<cpx<R>*>(smem_raw);
-  cpx<R>* T2 = S1 + s.n_col;
-  const int i1 = blockIdx.y;
   const int R3 = s.R3;
   const int t3 = threadIdx.x & (TL3 - 1);
   const int zper = blockDim.x / TL3;
   const long long plane = (long long)i1 * N2 * N3;
 
-  const int item = blockIdx.x;
   cpx<R>* row = a.b1 + ((long long)item * s.N1 + i1) * s.n_col;
   if (a.mode != SLAB_FROM_GRID) {
     for (int j = threadIdx.x; j < s.n_col; j += blockDim.x) S1[j] = row[j];
@@ -341,15 +399,16 @@ __global__ void __launch_bounds__(SlabThreads<R, N2, N3>::v, (SlabMinBlocks<R, N
       const int w = item - grp * a.map.items_per_group;
       const int va = 2 * w, vb = 2 * w + 1;
       const long long off = plane + (long long)i2 * N3;
-      const R* f = (act && a.src.f) ? a.src.f + (long long)grp * a.src.f_stride + off : nullptr;
-      const R* ga = act ? a.src.g + (long long)va * a.src.g_stride + off : nullptr;
-      const R* gb = (act && vb < a.map.vecs_per_group) ? a.src.g + (long long)vb * a.src.g_stride + off
+      using T = typename Io<R>::T;
+      const T* f = (act && a.src.f) ? a.src.f + (long long)grp * a.src.f_stride + off : nullptr;
+      const T* ga = act ? a.src.g + (long long)va * a.src.g_stride + off : nullptr;
+      const T* gb = (act && vb < a.map.vecs_per_group) ? a.src.g + (long long)vb * a.src.g_stride + off
                                                         : nullptr;
 #pragma unroll
       for (int i = 0; i < M3; ++i) {
         const int i3 = pos_b<N3, TL3>(t3, i);
-        const R fv = f ? f[i3] : R(1);
-        v[i] = act ? mk(fv * ga[i3], gb ? fv * gb[i3] : R(0)) : zero<R>();
+        const R fv = f ? ld_io<R>(f + i3) : R(1);
+        v[i] = act ? mk(fv * ld_io<R>(ga + i3), gb ? fv * ld_io<R>(gb + i3) : R(0)) : zero<R>();
       }
     } else {
 #pragma unroll
@@ -360,24 +419,24 @@ __global__ void __launch_bounds__(SlabThreads<R, N2, N3>::v, (SlabMinBlocks<R, N
       fft_a2b<R, N3, TL3, +1>(v, t3, s.tw3);
       if (a.mode == SLAB_TO_GRID) {
         if (act) {
-          const int ia = a.map.vec(item, 0), ib = a.map.vec(item, 1);
+          const int ia = a.map.vec(item, 0, nl), ib = a.map.vec(item, 1, nl);
           const long long off = plane + (long long)i2 * N3;
-          R* oa = ia >= 0 ? a.out + (long long)ia * a.out_stride + off : nullptr;
-          R* ob = ib >= 0 ? a.out + (long long)ib * a.out_stride + off : nullptr;
+          typename Io<R>::T* oa = ia >= 0 ? a.out + (long long)ia * a.out_stride + off : nullptr;
+          typename Io<R>::T* ob = ib >= 0 ? a.out + (long long)ib * a.out_stride + off : nullptr;
 #pragma unroll
           for (int i = 0; i < M3; ++i) {
             const int i3 = pos_b<N3, TL3>(t3, i);
-            if (oa) oa[i3] = v[i].x * (R)a.out_scale;
-            if (ob) ob[i3] = v[i].y * (R)a.out_scale;
+            if (oa) oa[i3] = io_of<R>(v[i].x * R(a.out_scale));
+            if (ob) ob[i3] = io_of<R>(v[i].y * R(a.out_scale));
           }
         }
         continue;
       }
-      if constexpr (sizeof(R) == 8) {
+      if constexpr (!std::is_same<R, float>::value) {
         if (a.dn && act) {
           // density response of the two vectors of the item on this z-line
           // (Eq. deltani), accumulated over the occupied states v
-          const int ia = a.map.vec(item, 0), ib = a.map.vec(item, 1);
+          const int ia = a.map.vec(item, 0, nl), ib = a.map.vec(item, 1, nl);
           const long long off = plane + (long long)i2 * N3;
           const int ja = ia / a.dn_nocc, vb_a = ia - ja * a.dn_nocc;
           const double* ua = a.u + (long long)vb_a * a.dn_stride + off;
@@ -390,9 +449,9 @@ __global__ void __launch_bounds__(SlabThreads<R, N2, N3>::v, (SlabMinBlocks<R, N
 #pragma unroll
           for (int i = 0; i < M3; ++i) {
             const int i3 = pos_b<N3, TL3>(t3, i);
-            const double ca = sc * v[i].x * ua[i3];
+            const double ca = sc * as_double(v[i].x) * ua[i3];
             if (ub) {
-              const double cb = sc * v[i].y * ub[i3];
+              const double cb = sc * as_double(v[i].y) * ub[i3];
               if (jb == ja) {
                 atomicAdd(da + i3, ca + cb);
               } else {
@@ -426,6 +485,64 @@ __global__ void __launch_bounds__(SlabThreads<R, N2, N3>::v, (SlabMinBlocks<R, N
   for (int j = threadIdx.x; j < s.n_col; j += blockDim.x) row[j] = S1[j];
 }
 
+// FP64 and double-float: one block per (item, x-plane i1), grid (largest
+// item count, N1); with a device count, blocks past it exit at once.
+// FP32: a persistent grid of the resident blocks strides over the
+// (item, plane) units, so a launch sized for a whole batch whose device
+// count has shrunk costs no empty blocks (for the FP32 slab the loop costs
+// no registers, unlike the FP64 one).
+template <typename R, int N2, int N3>
+__global__ void __launch_bounds__(SlabThreads<R, N2, N3>::v, (SlabMinBlocks<R, N2, N3>::v))
+    k_slab(SphereDev<R> s, SlabArgs<R> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<R>* S1 = reinterpret_cast<cpx<R>*>(smem_raw);
+  cpx<R>* T2 = S1 + s.n_col;
+  const int nl = listed_count(a.map);
+  const int n_items = items_of(a.map, a.n_items, nl);
+  if constexpr (std::is_same<R, float>::value) {
+    const int units = n_items * s.N1;
+#pragma unroll 1
+    for (int w = blockIdx.x; w < units; w += gridDim.x) {
+      const int item = w / s.N1;
+      __syncthreads();  // the previous unit's shared-memory reads are done
+      slab_unit<R, N2, N3>(s, a, nl, item, w - item * s.N1, S1, T2);
+    }
+  } else {
+    const int item = blockIdx.x;
+    if (item >= n_items) return;
+    slab_unit<R, N2, N3>(s, a, nl, item, blockIdx.y, S1, T2);
+  }
+}
+
+// resident blocks per SM of a kernel at a block size and shared memory
+// (queried once per combination)
+template <typename K>
+static int occupancy(K kern, int threads, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::tuple<const void*, int, size_t>, int> cache;
+  std::lock_guard<std::mutex> g(mu);
+  const auto key = std::make_tuple((const void*)kern, threads, smem);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int o = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, threads, smem) != cudaSuccess || o < 1) {
+    cudaGetLastError();
+    o = 1;
+  }
+  cache[key] = o;
+  return o;
+}
+
+static int sm_count() {
+  static const int n = [] {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 152;
+  }();
+  return n;
+}
+
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
@@ -441,7 +558,8 @@ static int threads_for(int lines) {
 }
 
 template <typename R, int N1>
-static cudaError_t cols_fwd_impl(const SphereDev<R>& s, const R* x, long long ldx, ItemMap map,
+static cudaError_t cols_fwd_impl(const SphereDev<R>& s, const typename Io<R>::T* x, long long ldx,
+                                 ItemMap map,
                                  int n_items, int coef, cpx<R>* b1, cudaStream_t st) {
   const int per = 128 / Tpl<R, N1>::v;
   const long long total = (long long)n_items * s.n_ucol;
@@ -449,8 +567,11 @@ static cudaError_t cols_fwd_impl(const SphereDev<R>& s, const R* x, long long ld
   const long long blocks = (total + per - 1) / per;
   // one x-line per column (n_col lines per item): 5 L log2 L flops each
   const double lines = (double)n_items * s.n_col;
-  ProfScope ps(sizeof(R) == 8 ? PC_COLS_F64 : PC_COLS_F32, st, lines * 5.0 * N1 * log2((double)N1),
-               (double)n_items * 2.0 * s.n_pw * sizeof(R) + lines * N1 * 2.0 * sizeof(R));
+  ProfScope ps(prof_class<R>(PC_COLS_F64, PC_COLS_F32, PC_COLS_DF), st,
+               lines * 5.0 * N1 * log2((double)N1),
+               (double)n_items * 2.0 * s.n_pw * sizeof(typename Io<R>::T) +
+                   lines * N1 * 2.0 * sizeof(R),
+               map.list ? map.n_dev : nullptr, map.n_list);
   count_launch();
   k_cols_fwd<R, N1><<<(unsigned)blocks, 128, 0, st>>>(s, x, ldx, map, n_items, coef, b1);
   return cudaGetLastError();
@@ -464,10 +585,12 @@ static cudaError_t cols_bwd_impl(const SphereDev<R>& s, const cpx<R>* b1, ItemMa
   if (total == 0) return cudaSuccess;
   const long long blocks = (total + per - 1) / per;
   const double lines = (double)n_items * s.n_col;
-  const double vecs = (double)n_items * 2.0 * s.n_pw * sizeof(R);
-  ProfScope ps(sizeof(R) == 8 ? PC_COLS_F64 : PC_COLS_F32, st, lines * 5.0 * N1 * log2((double)N1),
+  const double vecs = (double)n_items * 2.0 * s.n_pw * sizeof(typename Io<R>::T);
+  ProfScope ps(prof_class<R>(PC_COLS_F64, PC_COLS_F32, PC_COLS_DF), st,
+               lines * 5.0 * N1 * log2((double)N1),
                lines * N1 * 2.0 * sizeof(R) + vecs * (1.0 + (ep.x_in ? 1.0 : 0.0) +
-                                                      (ep.beta != R(0) ? 1.0 : 0.0)));
+                                                      (ep.beta != 0 ? 1.0 : 0.0)),
+               map.list ? map.n_dev : nullptr, map.n_list);
   count_launch();
   k_cols_bwd<R, N1><<<(unsigned)blocks, 128, 0, st>>>(s, b1, map, n_items, ep);
   return cudaGetLastError();
@@ -490,6 +613,10 @@ static cudaError_t slab_impl(const SphereDev<R>& s, const SlabArgs<R>& a, cudaSt
   const int gx = a.n_items;
   if (gx == 0) return cudaSuccess;
   dim3 grid(gx, s.N1);
+  if (std::is_same<R, float>::value) {
+    const long long units = (long long)gx * s.N1;
+    grid = dim3((unsigned)std::min<long long>(units, (long long)occupancy(kern, nt, smem) * sm_count()));
+  }
   // algorithmic work: y-lines over the |n3| <= R3 planes and z-lines over the
   // N2 rows of each x-plane, 5 L log2 L flops per complex line FFT
   const double ylines = (double)(2 * s.R3 + 1), zlines = (double)N2;
@@ -514,15 +641,16 @@ static cudaError_t slab_impl(const SphereDev<R>& s, const SlabArgs<R>& a, cudaSt
     case SLAB_FROM_GRID: fl = planes * (ylines * fy + zlines * fz + 3.0 * N2 * N3);
                          by = planes * (colb + 3 * gridb); break;
   }
-  ProfScope ps(sizeof(R) == 8 ? PC_SLAB_F64 : PC_SLAB_F32, st, fl, by);
+  ProfScope ps(prof_class<R>(PC_SLAB_F64, PC_SLAB_F32, PC_SLAB_DF), st, fl, by,
+               a.map.list ? a.map.n_dev : nullptr, a.map.n_list);
   count_launch();
   kern<<<grid, nt, smem, st>>>(s, a);
   return cudaGetLastError();
 }
 
 template <typename R>
-cudaError_t launch_cols_fwd(const SphereDev<R>& s, const R* x, long long ldx, ItemMap map,
-                            int n_items, int coef, cpx<R>* b1, cudaStream_t st) {
+cudaError_t launch_cols_fwd(const SphereDev<R>& s, const typename Io<R>::T* x, long long ldx,
+                            ItemMap map, int n_items, int coef, cpx<R>* b1, cudaStream_t st) {
   switch (s.N1) {
     case 24: return cols_fwd_impl<R, 24>(s, x, ldx, map, n_items, coef, b1, st);
     case 32: return cols_fwd_impl<R, 32>(s, x, ldx, map, n_items, coef, b1, st);
@@ -574,5 +702,10 @@ template cudaError_t launch_slab<double>(const SphereDev<double>&, const SlabArg
                                          cudaStream_t);
 template cudaError_t launch_slab<float>(const SphereDev<float>&, const SlabArgs<float>&,
                                         cudaStream_t);
+template cudaError_t launch_cols_fwd<df>(const SphereDev<df>&, const double*, long long, ItemMap,
+                                         int, int, cpx<df>*, cudaStream_t);
+template cudaError_t launch_cols_bwd<df>(const SphereDev<df>&, const cpx<df>*, ItemMap, int,
+                                         const Epilogue<df>&, cudaStream_t);
+template cudaError_t launch_slab<df>(const SphereDev<df>&, const SlabArgs<df>&, cudaStream_t);
 
 }  // namespace pdep

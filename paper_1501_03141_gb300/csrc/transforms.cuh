@@ -13,6 +13,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "df64.cuh"
 
 namespace pdep {
 
@@ -74,11 +75,16 @@ struct ItemMap {
   int vecs_per_group;
   int items_per_group;
   const int* list = nullptr;  // optional explicit vector list (pairs of entries)
-  int n_list = 0;
-  __host__ __device__ int vec(int item, int slot) const {
+  int n_list = 0;             // listed vectors (the largest count when n_dev is set)
+  const int* n_dev = nullptr; // device count of listed vectors (<= n_list): kernels read it
+                              // at launch, so a launch sized for n_list can be enqueued or
+                              // captured before the count is known
+  __host__ __device__ int vec(int item, int slot) const { return vec(item, slot, n_list); }
+  // with the listed-vector count nl (the device count when n_dev is set)
+  __host__ __device__ int vec(int item, int slot, int nl) const {
     if (list) {
       int idx = 2 * item + slot;
-      return idx < n_list ? list[idx] : -1;
+      return idx < nl ? list[idx] : -1;
     }
     int g = item / items_per_group;
     int w = item - g * items_per_group;
@@ -87,32 +93,46 @@ struct ItemMap {
   }
 };
 
+// The listed-vector count a kernel works with (read once per kernel; the
+// map itself stays unmodified in parameter space).
+__device__ __forceinline__ int listed_count(const ItemMap& m) {
+  return (m.list && m.n_dev) ? *m.n_dev : m.n_list;
+}
+// Number of FFT items to process, given that count.
+__device__ __forceinline__ int items_of(const ItemMap& m, int n_items, int nl) {
+  return (m.list && m.n_dev) ? (nl + 1) / 2 : n_items;
+}
+
 // Per-component multiplier applied to sphere data on the way in / out.
 enum CoefKind : int { COEF_ONE = 0, COEF_SQRT_COULOMB = 1 };
 
 // Epilogue of the column pass back:
 //   y = scale * coef(G) * (transform) + (kin * |G|^2/2 + shift[vec]) * x_in
 //       (+ beta * y_old)
+// R is the arithmetic type of the transform; vectors are stored in
+// Io<R>::T (FP64 for the double-float transforms, else R itself).
 template <typename R>
 struct Epilogue {
-  R* y;                 // output vectors (real layout)
+  using T = typename Io<R>::T;
+  T* y;                 // output vectors (real layout)
   long long ldy;
-  const R* x_in;        // vectors for the diagonal term (may be null)
+  const T* x_in;        // vectors for the diagonal term (may be null)
   long long ldx;
-  const R* shift;       // per vector, indexed vec % shift_period (may be null)
+  const T* shift;       // per vector, indexed vec % shift_period (may be null)
   int shift_period;
   R scale;
   R kin;                // 0 or 1
-  R beta;               // 0: overwrite
+  T beta;               // 0: overwrite
   int coef;             // CoefKind
 };
 
 // Grid source of the grid -> sphere slab pass: field = f(r) * (ga(r) + i gb(r))
 template <typename R>
 struct GridSrc {
-  const R* f;          // may be null (f = 1)
+  using T = typename Io<R>::T;
+  const T* f;          // may be null (f = 1)
   long long f_stride;  // per group (item_map group)
-  const R* g;          // ga/gb are vectors of g with stride g_stride
+  const T* g;          // ga/gb are vectors of g with stride g_stride
   long long g_stride;
 };
 
@@ -127,8 +147,8 @@ struct SlabArgs {
   int mode;
   cpx<R>* b1;            // [n_items][N1][n_col]
   int n_items;
-  const R* v;            // local potential [N_r] (HPSI)
-  R* out;                // TO_GRID: two fields per item at vec(item,s)*out_stride
+  const R* v;            // local potential [N_r] (HPSI), in the arithmetic type
+  typename Io<R>::T* out;  // TO_GRID: two fields per item at vec(item,s)*out_stride
   long long out_stride;
   double out_scale;
   GridSrc<R> src;        // FROM_GRID (f: one grid per group, g: per-vector grids)
@@ -142,10 +162,11 @@ struct SlabArgs {
   double dn_scale = 0.0;
 };
 
-// Host launchers (stream-ordered; no synchronisation).
+// Host launchers (stream-ordered; no synchronisation).  R = float, double or
+// df (double-float arithmetic on FP64 vectors).
 template <typename R>
-cudaError_t launch_cols_fwd(const SphereDev<R>& s, const R* x, long long ldx, ItemMap map,
-                            int n_items, int coef, cpx<R>* b1, cudaStream_t st);
+cudaError_t launch_cols_fwd(const SphereDev<R>& s, const typename Io<R>::T* x, long long ldx,
+                            ItemMap map, int n_items, int coef, cpx<R>* b1, cudaStream_t st);
 template <typename R>
 cudaError_t launch_slab(const SphereDev<R>& s, const SlabArgs<R>& a, cudaStream_t st);
 template <typename R>

@@ -48,6 +48,8 @@ def test_to_grid_and_hpsi(grid, cell):
         ref = apply_hamiltonian_grid(b, s.v_r, x)
         assert rel(ctx.apply_hamiltonian(x), ref) < 1e-14
         assert rel(ctx.apply_hamiltonian(x, precision=pg.PDEP_MIXED), ref) < 2e-7
+        # double-float transforms (the mixed refinement's A delta): ~48-bit arithmetic
+        assert rel(ctx.apply_hamiltonian(x, precision=pg.PDEP_APPLY_DF64), ref) < 1e-13
         # single vector (odd item) and a per-vector check
         one = ctx.apply_hamiltonian(x[1:2].copy())
         assert rel(one[0], ref[1]) < 1e-14
