@@ -43,6 +43,12 @@ WORKLOAD = ("cube48: 48^3 grid, L=20 bohr, 64 Gaussian wells (seed 1501031411), 
 # Nominal units x clocks of a GB300 (152 SMs, 128 FP32 lanes each, 2070 MHz):
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12     # 80.5 TFLOP/s FFMA
 FP64_PEAK_TFLOPS = 1.25                                # nominal FP64 rate of GB300
+# Double-float arithmetic (pairs of FP32 numbers) on the FP32 pipe: a line-FFT
+# flop costs about 9.4 FP32 instructions on average (a double-float add is
+# 11 instructions, a multiply 7; a radix-2 butterfly with twiddle is 4
+# multiplies and 6 adds for 10 algorithmic flops), against the pipe's
+# 152 x 128 instructions per clock
+DF64_PEAK_TFLOPS = 152 * 128 * 2.070e9 / 9.4 / 1e12     # 4.28 TFLOP/s FP64-equivalent
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
 CSRC = os.path.join(ROOT, "paper_1501_03141_gb300", "csrc")
@@ -253,7 +259,8 @@ def roofline(prof):
     per = c["ms"] / c["launches"] / 1e3                     # seconds per launch
     gbs = c["bytes"] / c["launches"] / per / 1e9
     tfl = c["flops"] / c["launches"] / per / 1e12
-    alu_peak = FP64_PEAK_TFLOPS if name.endswith("f64") else FP32_PEAK_TFLOPS
+    alu_peak = (DF64_PEAK_TFLOPS if name.endswith("df64") else
+                FP64_PEAK_TFLOPS if name.endswith("f64") else FP32_PEAK_TFLOPS)
     f_hbm, f_alu = gbs / hbm, tfl / alu_peak
     share = c["ms"] / sum(v["ms"] for v in prof["classes"].values())
     tr = traffic_for(name, c["bytes"] / c["launches"])
@@ -261,7 +268,9 @@ def roofline(prof):
         r = {"bound": "alu", "achieved": round(tfl, 3), "peak": round(alu_peak, 3),
              "unit": "TFLOP/s", "frac": round(f_alu, 4),
              "peak_source": "derived from unit counts x 2070 MHz (" +
-                            ("FP64 nominal 1.25 TFLOP/s" if name.endswith("f64") else
+                            ("152 SM x 128 FP32 lanes / 9.4 instructions per double-float "
+                             "flop" if name.endswith("df64") else
+                             "FP64 nominal 1.25 TFLOP/s" if name.endswith("f64") else
                              "152 SM x 128 FP32 lanes x 2") + ")",
              "hbm_frac_of_" + src: round(f_hbm, 4)}
     else:
@@ -292,7 +301,7 @@ def run_ours(args):
 
     dev = torch.device("cuda", local)
     system = synthetic.make_system("cube48")
-    opts = dict(dav_tol=0.0, dav_max_iter=6)
+    opts = dict(dav_tol=0.0, dav_max_iter=6, use_graph=0 if args.eager else 1)
     stream = torch.cuda.current_stream(dev)
     ctx = pg.Context(system, precision=pg.PDEP_MIXED, stream=stream.cuda_stream, **opts)
     ctx_deflate = ctx.options.n_deflate
@@ -563,6 +572,112 @@ def run_small(args):
         print(json.dumps({"case": args.case, "norm": float(out.norm())}))
 
 
+def _timed(fn, stream, steps):
+    """CUDA-event time of `steps` calls of fn() on `stream` (seconds)."""
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    out = [fn() for _ in range(steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3, out
+
+
+def run_batch(args):
+    """The uneven batch (32 systems, N in {24..64}, N_occ ~ U{8..96}, N_pdep =
+    2 N_occ): pdep_solve(sys = -1) over every member, dav_max_iter Davidson
+    iterations, in the mixed and the FP64 paths; solves/s, eigenpairs/s, the
+    autotuned shapes and the largest mixed-vs-FP64 eigenvalue error per
+    member.  One line of its own (not the headline workload)."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1501_03141_gb300 as pg
+    import synthetic
+    batch = synthetic.make_batch()
+    stream = torch.cuda.current_stream()
+    res = {}
+    for name, prec in (("mixed", pg.PDEP_MIXED), ("fp64", pg.PDEP_FP64)):
+        with pg.Context(batch, precision=prec, dav_tol=0.0, dav_max_iter=args.batch_dav,
+                        stream=stream.cuda_stream) as ctx:
+            for _ in range(args.warmup if name == "mixed" else 1):
+                ctx.pdep_solve(sys=-1)
+            steps = args.steps if name == "mixed" else 1
+            t, out = _timed(lambda: ctx.pdep_solve(sys=-1), stream, steps)
+            ev, _, st = out[-1]
+            res[name] = {"seconds_per_step": t / steps, "ev": ev.copy(), "stats": st}
+    err, off = [], 0
+    for s in batch:
+        a = res["mixed"]["ev"][off:off + s.n_pdep]
+        b = res["fp64"]["ev"][off:off + s.n_pdep]
+        off += s.n_pdep
+        err.append(float((np.abs(a - b) / np.abs(b)).max()))
+    line = {"case": "batch", "workload": "uneven batch: 32 systems, N in {24,32,40,48,64}, "
+            "L=10N/24 bohr, N_occ~U{8..96}, N_pdep=2N_occ (seeds 1501031430+k), "
+            f"{args.batch_dav} Davidson iterations per member, Sternheimer tol 1e-10",
+            "n_systems": len(batch)}
+    for name in ("mixed", "fp64"):
+        r = res[name]
+        st = r["stats"]
+        line[name] = {"solves_per_s": round(st["sternheimer_solves"] / r["seconds_per_step"], 1),
+                      "eigenpairs_per_s": round(sum(s.n_pdep for s in batch) /
+                                                r["seconds_per_step"], 2),
+                      "ms_per_step": round(1e3 * r["seconds_per_step"], 1),
+                      "solves_per_step": st["sternheimer_solves"],
+                      "max_cg_residual": st["max_cg_residual"],
+                      "cg_step_variant_autotuned": st["cg_variant"],
+                      "projection_kernel_autotuned": st["proj_variant"],
+                      "graph_launches_per_step": st["graph_launches"]}
+    line["mixed_vs_fp64_max_rel_err_per_member"] = [float(f"{e:.3e}") for e in err]
+    line["mixed_vs_fp64_max_rel_err"] = max(err)
+    print(json.dumps(line), flush=True)
+
+
+def run_interface(args):
+    """The 64x64x192 interface (49 095 plane waves, 512 occupied states): one
+    chi0bar application of args.interface_pert seeded perturbations (each a
+    batch of 512 Sternheimer solves), mixed and FP64; solves/s, the kernel
+    profile and the dominant kernel's roofline.  One line of its own."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1501_03141_gb300 as pg
+    import synthetic
+    s = synthetic.make_system("interface")
+    stream = torch.cuda.current_stream()
+    line = {"case": "interface", "workload": "interface: 64x64x192 grid, 20x20x60 bohr, two slabs "
+            "of Gaussian wells (seed 1501031414), N_occ=512, 49 095 plane waves; one chi0bar "
+            f"application of {args.interface_pert} perturbations, Sternheimer tol 1e-10"}
+    vals = {}
+    for name, prec in (("mixed", pg.PDEP_MIXED), ("fp64", pg.PDEP_FP64)):
+        with pg.Context(s, precision=prec, stream=stream.cuda_stream) as ctx:
+            dim = ctx.sizes()["n_pdep_dim"]
+            phi = torch.tensor(synthetic.random_vectors(5, args.interface_pert, dim),
+                               device="cuda")
+            out = torch.empty_like(phi)
+            ctx.chi0_apply(phi, out=out)              # warm-up (autotuner, graphs)
+            pg.profile_start()
+            t, _ = _timed(lambda: ctx.chi0_apply(phi, out=out, sync=False), stream, 1)
+            prof = pg.profile_stop()
+            st = ctx.stats()
+            vals[name] = out.cpu().numpy()
+            line[name] = {"solves_per_s": round(st["sternheimer_solves"] / t, 1),
+                          "seconds": round(t, 3), "solves": st["sternheimer_solves"],
+                          "cg_iterations": st["cg_iterations"],
+                          "max_cg_residual": st["max_cg_residual"],
+                          "chi0_chunks": st["chi0_chunks"],
+                          "roofline": roofline(prof), "tensor_gemm": tensor_gemm(prof),
+                          "kernel_profile": {k: {"launches": v["launches"], "ms": round(v["ms"], 2)}
+                                             for k, v in prof["classes"].items() if v["launches"]}}
+    a, b = vals["mixed"], vals["fp64"]
+    line["mixed_vs_fp64_rel"] = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    print(json.dumps(line), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -573,14 +688,27 @@ def main(argv=None):
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--fp64-warmup", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--eager", action="store_true",
+                    help="diagnostics: CG loops from a host loop instead of CUDA graphs, so that "
+                         "the per-kernel profile sees every CG kernel")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--proj", type=int, default=1, choices=[0, 1],
                     help="small cases: FP32 projection kernel (0 CUDA cores, 1 tensor cores)")
-    ap.add_argument("--case", choices=["bench", "small", "small64"], default="bench",
+    ap.add_argument("--case", choices=["bench", "small", "small64", "batch", "interface"],
+                    default="bench",
                     help="small/small64: one chi0bar application of 16 perturbations "
-                         "(mixed/FP64), for profiler captures")
+                         "(mixed/FP64), for profiler captures; batch: the 32-system uneven "
+                         "batch; interface: the 64x64x192 interface")
+    ap.add_argument("--batch-dav", type=int, default=3,
+                    help="batch case: Davidson iterations per member")
+    ap.add_argument("--interface-pert", type=int, default=32,
+                    help="interface case: perturbations of the timed chi0bar application")
     args = ap.parse_args(argv)
-    if args.case != "bench":
+    if args.case == "batch":
+        run_batch(args)
+    elif args.case == "interface":
+        run_interface(args)
+    elif args.case != "bench":
         run_small(args)
     elif args.impl == "reference":
         run_reference(args)

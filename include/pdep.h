@@ -117,10 +117,15 @@ typedef struct {
 typedef struct {
   int precision;             /* pdep_precision */
   double cg_tol;             /* Sternheimer: ||b - A x|| / ||b|| target (1e-10) */
-  int cg_max_iter;           /* CG iteration cap per solve (FP64 path) */
+  int cg_max_iter;           /* FP64 path: CG iteration cap of each refinement round */
   double inner_tol;          /* mixed: FP32 inner CG reduction per refinement round */
   int inner_max_iter;        /* mixed: FP32 CG iteration cap per round */
-  int max_refine;            /* mixed: refinement rounds cap */
+  int max_refine;            /* refinement rounds cap (both paths).  Every solve runs in
+                                rounds: an inner CG on the residual scaled to unit norm
+                                (FP64, or FP32 in the mixed modes), then x += delta and
+                                the FP64 residual r -= A delta; the FP64 path's first
+                                round normally meets cg_tol, a further round catching
+                                solves whose recomputed residual drifted above it. */
   double dav_tol;            /* Davidson: max ||chi0bar x - theta x|| / |theta_1|; 0 = run dav_max_iter */
   int dav_max_iter;          /* Davidson iterations cap (each applies chi0bar once) */
   int dav_subspace_factor;   /* subspace holds at most factor * n_pdep vectors (>= 2) */
@@ -157,6 +162,10 @@ typedef struct {
                                 significant bits; the FP32 pipe runs 64x the FP64 rate),
                                 vectors, residuals and projections in FP64; 0 = FP64
                                 transforms */
+  int fused_hpsi;            /* 1 (default): the FP32 H x of the inner CG on the cubic grids
+                                24^3 .. 48^3 in one launch that keeps each item's column
+                                scratch in shared memory; 0: three launches through a
+                                global-memory scratch (always used for other grids) */
 } pdep_options;
 
 typedef struct {
@@ -329,7 +338,8 @@ int pdep_apply_hamiltonian(pdep_ctx* ctx, int sys, const double* x, int n, doubl
  *     PDEP_ERR_UNSUPPORTED.
  *   - The first call on a device looks up the device address of that array
  *     (cudaGetSymbolAddress, once per device, with the device current); make
- *     that first call before any stream capture.
+ *     that first call before any stream capture.  The context's device must
+ *     be the current device (PDEP_ERR_INVALID_ARG otherwise).
  *   - All calls share the array and it keeps the last call's contents; the
  *     transforms overwrite every scratch element before reading it, so
  *     nothing needs clearing.  Calls that overlap on the GPU (other streams,
@@ -349,7 +359,7 @@ int pdep_to_grid(pdep_ctx* ctx, int sys, const double* x, int n, double* u, void
  * waits for the recorded events and fills *out (may be NULL).  flops and
  * bytes are the algorithmic counts of the launches (complex line FFT:
  * 5 L log2 L flops; bytes: every input read and output written once). */
-#define PDEP_PROFILE_CLASSES 15
+#define PDEP_PROFILE_CLASSES 17
 typedef struct {
   char name[24];
   long long launches;

@@ -46,7 +46,7 @@ EXPORTS = (
     "pdep_chibar_apply", "pdep_sync_status", "pdep_bounds_checked", "pdep_get_stats",
 )
 
-PDEP_PROFILE_CLASSES = 15
+PDEP_PROFILE_CLASSES = 17
 
 
 class pdep_system_desc(ctypes.Structure):
@@ -82,6 +82,7 @@ class pdep_options(ctypes.Structure):
         ("autotune", ctypes.c_int),
         ("use_graph", ctypes.c_int),
         ("df_refine", ctypes.c_int),
+        ("fused_hpsi", ctypes.c_int),
     ]
 
 

@@ -9,6 +9,7 @@
 #include <functional>
 #include <map>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -115,7 +116,7 @@ struct DevBuf {
 struct CgGraph {
   int prec, sys, n, max_iter, cg_variant, proj_variant;
   double tol;
-  const void *b, *x, *sc, *mask;
+  const void *b, *x, *sc, *mask, *tolv;
   unsigned long long ws_gen, budget_ns;
   cudaGraphExec_t exec;
 };
@@ -457,7 +458,27 @@ int apply_h(pdep_ctx* c, SysData& s, const R* X, R* Y, int n, const int* d_list,
     map.n_dev = d_count;
     n_items = (n_list + 1) / 2;
   }
-  if (n_items > 0) {
+  bool fused = false;
+  if constexpr (std::is_same<C, float>::value) {
+    // FP32 on 24^3 .. 48^3: the whole transform in one launch, the column
+    // scratch in shared memory
+    if (n_items > 0 && c->opt.fused_hpsi && hpsi_fused_smem(s.sf) > 0) {
+      Epilogue<float> ep{};
+      ep.y = Y;
+      ep.ldy = s.ld;
+      ep.x_in = X;
+      ep.ldx = s.ld;
+      ep.shift = with_shift ? s.d_negeps32 : nullptr;
+      ep.shift_period = with_shift ? s.n_occ : 1;
+      ep.scale = 1.0f / s.n_r;
+      ep.kin = 1.0f;
+      ep.beta = 0.0f;
+      ep.coef = COEF_ONE;
+      CK(launch_hpsi_fused(s.sf, X, s.ld, map, n_items, s.d_vf, ep, st));
+      fused = true;
+    }
+  }
+  if (n_items > 0 && !fused) {
     cpx<C>* b1;   // double-float shares the FP64 scratch (16 bytes per complex)
     RET(ws(c, sizeof(C) == 8 ? "b1_64" : "b1_32", b1_count(s, n_items), &b1));
     const SphereDev<C>& sd = sph(s, (C*)nullptr);
@@ -533,12 +554,15 @@ int apply_h(pdep_ctx* c, SysData& s, const R* X, R* Y, int n, const int* d_list,
     R* S;
     // shift of the occupied and the deflated empty states: state w moves to
     // eps_{n_ext} - eps_v, the bottom of the spectrum the CG still sees
+    // (double-float transforms take double-float GEMMs too: FP64 matrices,
+    // arithmetic on the FP32 pipe)
+    using G = typename std::conditional<std::is_same<C, df>::value, df, R>::type;
     RET(ws(c, sizeof(R) == 8 ? "pv_64" : "pv_32", (size_t)s.n_ext * std::max(m, 1), &S));
     const R* P = psi_of(s, (R*)nullptr);
-    CK(gemm<R>(true, s.n_ext, m, s.n_pw, 1.0, P, s.ld, X, s.ld, 0.0, S, s.n_ext, st, d_list,
+    CK(gemm<G>(true, s.n_ext, m, s.n_pw, 1.0, P, s.ld, X, s.ld, 0.0, S, s.n_ext, st, d_list,
                nullptr, d_count));
     CK(scale_rows<R>(S, s.n_ext, s.n_ext, m, sigma_of(s, (R*)nullptr), st));
-    CK(gemm<R>(false, s.n_pw, m, s.n_ext, 1.0, P, s.ld, S, s.n_ext, 1.0, Y, s.ld, st, nullptr,
+    CK(gemm<G>(false, s.n_pw, m, s.n_ext, 1.0, P, s.ld, S, s.n_ext, 1.0, Y, s.ld, st, nullptr,
                d_list, d_count));
   }
   return PDEP_OK;
@@ -547,17 +571,24 @@ int apply_h(pdep_ctx* c, SysData& s, const R* X, R* Y, int n, const int* d_list,
 // RHS split for deflation: S = Psi_ext^T B; the deflated states' part of the
 // solution is Xd = sum_c psi_c S_c,i / (eps_c - eps_v(i)) (exact, H psi_c =
 // eps_c psi_c); then B <- B - Psi_ext S leaves the part the CG solves.
-int split_rhs(pdep_ctx* c, SysData& s, double* B, int n, double* Xd, cudaStream_t st) {
+// (G: FP64, or double-float arithmetic on the FP64 matrices in the mixed modes)
+template <typename G>
+int split_rhs_t(pdep_ctx* c, SysData& s, double* B, int n, double* Xd, cudaStream_t st) {
   double* S;
   RET(ws(c, "pc_64", (size_t)s.n_ext * n, &S));
-  CK(gemm<double>(true, s.n_ext, n, s.n_pw, 1.0, s.d_psi, s.ld, B, s.ld, 0.0, S, s.n_ext, st));
-  CK(gemm<double>(false, s.n_pw, n, s.n_ext, -1.0, s.d_psi, s.ld, S, s.n_ext, 1.0, B, s.ld, st));
+  CK(gemm<G>(true, s.n_ext, n, s.n_pw, 1.0, s.d_psi, s.ld, B, s.ld, 0.0, S, s.n_ext, st));
+  CK(gemm<G>(false, s.n_pw, n, s.n_ext, -1.0, s.d_psi, s.ld, S, s.n_ext, 1.0, B, s.ld, st));
   if (s.n_defl > 0) {
     CK(deflation_coefficients(S, s.n_ext, s.n_occ, s.n_defl, n, s.d_eps_ext, st));
-    CK(gemm<double>(false, s.n_pw, n, s.n_defl, 1.0, s.d_psi + (size_t)s.n_occ * s.ld, s.ld,
-                    S + s.n_occ, s.n_ext, 0.0, Xd, s.ld, st));
+    CK(gemm<G>(false, s.n_pw, n, s.n_defl, 1.0, s.d_psi + (size_t)s.n_occ * s.ld, s.ld,
+               S + s.n_occ, s.n_ext, 0.0, Xd, s.ld, st));
   }
   return PDEP_OK;
+}
+int split_rhs(pdep_ctx* c, SysData& s, double* B, int n, double* Xd, cudaStream_t st) {
+  if (c->opt.precision != PDEP_FP64 && c->opt.df_refine)
+    return split_rhs_t<df>(c, s, B, n, Xd, st);
+  return split_rhs_t<double>(c, s, B, n, Xd, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -1080,7 +1111,7 @@ int capture_cg_graph(pdep_ctx* c, SysData& s, CgArgs<R> a, const R* b, int n, in
 // from a host loop that reads the control flag after each step.
 template <typename R>
 int cg_loop(pdep_ctx* c, SysData& s, const R* b, R* x, int n, double tol, int max_iter,
-            CgScal* sc, const double* mask, cudaStream_t st) {
+            CgScal* sc, const double* mask, cudaStream_t st, const double* tolv) {
   const int si = (int)(&s - c->sys.data());
   R *r, *p, *ap;
   int* list;
@@ -1102,6 +1133,7 @@ int cg_loop(pdep_ctx* c, SysData& s, const R* b, R* x, int n, double tol, int ma
   a.status = c->d_status;
   a.n_active = &c->d_loop->active;
   a.mask = mask;
+  a.tolv = tolv;
   // loops under 256 RHS are never timed by the autotuner: they run the
   // current (or default) shapes and are captured right away
   const bool graph = c->opt.use_graph && (tuned(c, pi) || n < 256);
@@ -1153,7 +1185,8 @@ int cg_loop(pdep_ctx* c, SysData& s, const R* b, R* x, int n, double tol, int ma
   CgGraph* g = nullptr;
   for (CgGraph& e : c->cg_graphs)
     if (e.prec == pi && e.sys == si && e.n == n && e.max_iter == max_iter && e.tol == tol &&
-        e.b == b && e.x == x && e.sc == sc && e.mask == mask && e.ws_gen == c->ws_gen &&
+        e.b == b && e.x == x && e.sc == sc && e.mask == mask && e.tolv == tolv &&
+        e.ws_gen == c->ws_gen &&
         e.cg_variant == a.variant && e.proj_variant == pv && e.budget_ns == c->budget_ns) {
       g = &e;
       break;
@@ -1169,6 +1202,7 @@ int cg_loop(pdep_ctx* c, SysData& s, const R* b, R* x, int n, double tol, int ma
     e.x = x;
     e.sc = sc;
     e.mask = mask;
+    e.tolv = tolv;
     e.ws_gen = c->ws_gen;
     e.cg_variant = a.variant;
     e.proj_variant = pv;
@@ -1189,8 +1223,64 @@ int cg_loop(pdep_ctx* c, SysData& s, const R* b, R* x, int n, double tol, int ma
   return PDEP_OK;
 }
 
-// d_refine[0] holds the refinement round's unconverged count: the FP64 A delta
-// and the residual update run on that many listed RHS (launches sized for n).
+// Refinement rounds (iterative refinement written in solution updates):
+// round k solves A delta = r for every RHS still above cg_tol, with an inner
+// CG in precision Ri on the residual scaled to unit norm, then x += delta
+// and r -= A delta with A delta in FP64 arithmetic (or double-float, mixed
+// modes) and the density response of delta accumulated by that same
+// transform (dn is linear in x).  The FP64 path runs its inner solve to
+// 0.9 cg_tol (round 0) or 0.5 cg_tol (later rounds) of ||b_i|| through
+// per-RHS inner tolerances, so a second round only catches RHS whose
+// recomputed residual drifted above the recursion's; the mixed modes run
+// each FP32 inner solve to inner_tol.  d_refine[0] holds a round's
+// unconverged count: the A delta and the residual update run on that many
+// listed RHS (launches sized for n).  Rounds whose list is empty cost only
+// their launches.
+template <typename Ri>
+int refine_rounds(pdep_ctx* c, SysData& s, const double* b, const double* xd, double* x, int n,
+                  double* dn, int* its_total, double* rel, double* r64, double* ad,
+                  cudaStream_t st) {
+  const bool fp64 = sizeof(Ri) == 8;
+  const double tol = c->opt.cg_tol;
+  const char* tag = fp64 ? "64" : "32";
+  Ri *ri, *di;
+  double *rn, *dl, *tolv = nullptr;
+  CgScal* sc;
+  int* list;
+  RET(ws(c, (std::string("rf_r") + tag).c_str(), (size_t)n * s.ld, &ri));
+  RET(ws(c, (std::string("rf_d") + tag).c_str(), (size_t)n * s.ld, &di));
+  RET(ws(c, "mx_rn", (size_t)n, &rn));
+  RET(ws(c, (std::string("cg_sc") + tag).c_str(), (size_t)n, &sc));
+  RET(ws(c, "mx_list", (size_t)n, &list));
+  RET(ws(c, "sv_dl", (size_t)n * s.ld, &dl));
+  if (fp64) RET(ws(c, "rf_tolv", (size_t)n, &tolv));
+  CK(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)n * s.ld, st));
+  CK(fill_value(rel, n, 1.0, st));
+  int* n_un = c->d_refine;
+  for (int round = 0; round < c->opt.max_refine; ++round) {
+    NvtxRange nv("refinement_round");
+    CK(unconverged_list(rel, tol, n, list, n_un, st, &c->d_dstats->rounds_cur));
+    CK(refine_prepare<Ri>(r64, s.ld, s.n_pw, n, rel, tol, ri, s.ld, rn, st, tolv,
+                          (round == 0 ? 0.9 : 0.5) * tol, 0.5));
+    if (fp64)
+      RET(cg_loop<Ri>(c, s, ri, di, n, 0.0, c->opt.cg_max_iter, sc, rn, st, tolv));
+    else
+      RET(cg_loop<Ri>(c, s, ri, di, n, c->opt.inner_tol, c->opt.inner_max_iter, sc, rn, st,
+                      nullptr));
+    CK(cg_collect(sc, n, its_total, c->d_dstats, st));
+    // delta = rn d (+ xd in the first round, when every RHS is listed)
+    const double* xr = round == 0 ? xd : nullptr;
+    CK(refine_delta<Ri>(x, dl, s.ld, di, s.ld, s.n_pw, n, rn, xr, st));
+    if (!fp64 && c->opt.df_refine)
+      RET(apply_h<df>(c, s, dl, ad, n, list, n, true, true, st, dn, n_un));
+    else
+      RET(apply_h<double>(c, s, dl, ad, n, list, n, true, true, st, dn, n_un));
+    CK(residual_update(r64, ad, b, s.ld, s.n_pw, n, rel, list, xr, s.d_sigma64, s.n_occ, st,
+                       n_un));
+  }
+  return PDEP_OK;
+}
+
 // Solve for n right-hand sides b (FP64, [n][ld]); x out (FP64).  Nothing is
 // read back to the host: per-RHS iteration counts accumulate in its_total
 // (device, may be null), the FP64 relative residuals are left in 'rel'
@@ -1198,7 +1288,6 @@ int cg_loop(pdep_ctx* c, SysData& s, const R* b, R* x, int n, double tol, int ma
 // device statistics and status word.
 int solve_rhs(pdep_ctx* c, SysData& s, const double* b, const double* xd, double* x, int n,
               double* dn, int* its_total, double** rel_out, cudaStream_t st) {
-  const double tol = c->opt.cg_tol;
   double *rel, *r64, *ad;
   RET(ws(c, "sv_rel", (size_t)n, &rel));
   RET(ws(c, "sv_r64", (size_t)n * s.ld, &r64));
@@ -1210,69 +1299,15 @@ int solve_rhs(pdep_ctx* c, SysData& s, const double* b, const double* xd, double
   // delta of x (and checked against b's norm)
   CK(cudaMemcpyAsync(r64, b, sizeof(double) * (size_t)n * s.ld, cudaMemcpyDeviceToDevice, st));
   if (dn) CK(cudaMemsetAsync(dn, 0, sizeof(double) * (size_t)(n / s.n_occ) * s.n_r, st));
-  if (c->opt.precision == PDEP_FP64) {
-    CgScal* sc;
-    RET(ws(c, "cg_sc64", (size_t)n, &sc));
-    // stop the recursion a little below tol so that the FP64 residual
-    // recomputed from x (which drifts slightly from the recursion) meets it
-    RET(cg_loop<double>(c, s, b, x, n, 0.9 * tol, c->opt.cg_max_iter, sc, nullptr, st));
-    CK(cg_collect(sc, n, its_total, c->d_dstats, st));
-    CK(cudaMemsetAsync(&c->d_dstats->rounds_cur, 0, sizeof(int), st));
-    // x += xd (the deflated states' exact share); then the FP64 residual
-    // b - A x of the CG part, with the density response of the whole x
-    // accumulated by the same transform
-    const double* hx = x;
-    if (xd) {
-      double* dl;
-      RET(ws(c, "sv_dl", (size_t)n * s.ld, &dl));
-      CK(refine_delta(x, dl, s.ld, nullptr, 0, s.n_pw, n, nullptr, xd, st));
-      hx = dl;
-    }
-    RET(apply_h<double>(c, s, hx, ad, n, nullptr, 0, true, true, st, dn));
-    CK(residual_update(r64, ad, b, s.ld, s.n_pw, n, rel, nullptr, xd, s.d_sigma64, s.n_occ, st));
-    int one = 1;
-    CK(cudaMemcpyAsync(&c->d_dstats->rounds_cur, &one, sizeof(int), cudaMemcpyHostToDevice, st));
-  } else {
-    // mixed: FP32 inner CG on the scaled residual, FP64 residual refinement.
-    // Every round is enqueued; a round whose list is empty costs only its
-    // launches (each kernel exits on the zero count).
-    float *r32, *d32;
-    double *rn, *dl;
-    CgScal* sc;
-    int* list;
-    RET(ws(c, "mx_r32", (size_t)n * s.ld, &r32));
-    RET(ws(c, "mx_d32", (size_t)n * s.ld, &d32));
-    RET(ws(c, "mx_rn", (size_t)n, &rn));
-    RET(ws(c, "cg_sc32", (size_t)n, &sc));
-    RET(ws(c, "mx_list", (size_t)n, &list));
-    RET(ws(c, "sv_dl", (size_t)n * s.ld, &dl));
-    CK(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)n * s.ld, st));
-    CK(fill_value(rel, n, 1.0, st));
-    int* n_un = c->d_refine;
-    for (int round = 0; round < c->opt.max_refine; ++round) {
-      NvtxRange nv("refinement_round");
-      CK(unconverged_list(rel, tol, n, list, n_un, st, &c->d_dstats->rounds_cur));
-      CK(refine_prepare(r64, s.ld, s.n_pw, n, rel, tol, r32, s.ld, rn, st));
-      RET(cg_loop<float>(c, s, r32, d32, n, c->opt.inner_tol, c->opt.inner_max_iter, sc, rn, st));
-      CK(cg_collect(sc, n, its_total, c->d_dstats, st));
-      // delta = rn d32 (+ xd in the first round, when every RHS is listed);
-      // x += delta; r -= A delta in FP64, and the density response of delta
-      // is accumulated by the same transform (dn is linear in x)
-      const double* xr = round == 0 ? xd : nullptr;
-      CK(refine_delta(x, dl, s.ld, d32, s.ld, s.n_pw, n, rn, xr, st));
-      if (c->opt.df_refine)
-        RET(apply_h<df>(c, s, dl, ad, n, list, n, true, true, st, dn, n_un));
-      else
-        RET(apply_h<double>(c, s, dl, ad, n, list, n, true, true, st, dn, n_un));
-      CK(residual_update(r64, ad, b, s.ld, s.n_pw, n, rel, list, xr, s.d_sigma64, s.n_occ, st,
-                         n_un));
-    }
-  }
+  if (c->opt.precision == PDEP_FP64)
+    RET(refine_rounds<double>(c, s, b, xd, x, n, dn, its_total, rel, r64, ad, st));
+  else
+    RET(refine_rounds<float>(c, s, b, xd, x, n, dn, its_total, rel, r64, ad, st));
   // rel holds the FP64 residual of every RHS from its last update.  No final
   // P_c projection is needed: the shifted operator lifts occupied state w to
   // eps_{n_ext} - eps_v > 0, so the occupied component of x is at most
   // ||b - A x|| / (eps_{n_ext} - eps_v).
-  CK(solve_finish(rel, n, tol, c->d_dstats, c->d_status, st));
+  CK(solve_finish(rel, n, c->opt.cg_tol, c->d_dstats, c->d_status, st));
   c->st_solves += n;
   return PDEP_OK;
 }
@@ -1282,14 +1317,17 @@ int solve_rhs(pdep_ctx* c, SysData& s, const double* b, const double* xd, double
 // and xdefl [m*n_occ][ld] receives their exact share of the solution.
 // occupied_only: bvec = -P_c [dV_j psi_v] with P_c over the occupied states
 // alone (no deflation split; xdefl unused).
-int build_rhs(pdep_ctx* c, SysData& s, const double* dv, int m, double* bvec, double* xdefl,
-              cudaStream_t st, bool occupied_only = false) {
+// The products dV_j psi_v and their transforms to the sphere (C: FP64, or
+// double-float in the mixed modes; vectors FP64 either way).
+template <typename C>
+int rhs_transform(pdep_ctx* c, SysData& s, const double* dv, int m, double* bvec,
+                  cudaStream_t st) {
   const int nocc = s.n_occ;
   ItemMap map{nocc, (nocc + 1) / 2};
   const int n_items = m * ((nocc + 1) / 2);
-  cpx<double>* b1;
+  cpx<C>* b1;
   RET(ws(c, "b1_64", b1_count(s, n_items), &b1));
-  SlabArgs<double> a{};
+  SlabArgs<C> a{};
   a.mode = SLAB_FROM_GRID;
   a.b1 = b1;
   a.n_items = n_items;
@@ -1298,14 +1336,25 @@ int build_rhs(pdep_ctx* c, SysData& s, const double* dv, int m, double* bvec, do
   a.src.g = s.d_u;
   a.src.g_stride = s.n_r;
   a.map = map;
-  CK(launch_slab<double>(s.sd, a, st));
-  Epilogue<double> ep{};
+  const SphereDev<C>& sd = sph(s, (C*)nullptr);
+  CK(launch_slab<C>(sd, a, st));
+  Epilogue<C> ep{};
   ep.y = bvec;
   ep.ldy = s.ld;
   ep.shift_period = 1;
-  ep.scale = -1.0 / s.n_r;
+  ep.scale = C(-1.0 / s.n_r);
   ep.coef = COEF_ONE;
-  CK(launch_cols_bwd<double>(s.sd, b1, map, n_items, ep, st));
+  CK(launch_cols_bwd<C>(sd, b1, map, n_items, ep, st));
+  return PDEP_OK;
+}
+
+int build_rhs(pdep_ctx* c, SysData& s, const double* dv, int m, double* bvec, double* xdefl,
+              cudaStream_t st, bool occupied_only = false) {
+  const int nocc = s.n_occ;
+  if (c->opt.precision != PDEP_FP64 && c->opt.df_refine)
+    RET(rhs_transform<df>(c, s, dv, m, bvec, st));
+  else
+    RET(rhs_transform<double>(c, s, dv, m, bvec, st));
   if (occupied_only) {
     double* S;
     RET(ws(c, "po_S", (size_t)nocc * m * nocc, &S));
@@ -1487,12 +1536,14 @@ int solve_one(pdep_ctx* c, int si, const double* phi0, double* eigvals, double* 
 
 namespace pdep {
 // Sphere description and potential of one system for pdep_apply_hamiltonian_noalloc.
-int noalloc_sphere(pdep_ctx* c, int sys, SphereDev<double>* sd, const double** v, int* n_pw) {
+int noalloc_sphere(pdep_ctx* c, int sys, SphereDev<double>* sd, const double** v, int* n_pw,
+                   int* device) {
   RET(check_sys(c, sys));
   const SysData& s = c->sys[sys];
   *sd = s.sd;
   *v = s.d_v;
   *n_pw = s.n_pw;
+  *device = c->device;
   return PDEP_OK;
 }
 }  // namespace pdep
@@ -1560,6 +1611,7 @@ void pdep_default_options(pdep_options* o) {
   o->autotune = 1;
   o->use_graph = 1;
   o->df_refine = 1;
+  o->fused_hpsi = 1;
 }
 
 const char* pdep_status_string(int s) {
@@ -1639,6 +1691,7 @@ int pdep_setup(const pdep_system_desc* sys, int n_sys, const pdep_options* opt, 
   };
   if (cudaGetDevice(&c->device) != cudaSuccess) return bail(fail(PDEP_ERR_CUDA, "no CUDA device"));
   if (upload_local_twiddles() != cudaSuccess) return bail(fail(PDEP_ERR_CUDA, "twiddle upload"));
+  if (dev_timers_init() != 0) return bail(fail(PDEP_ERR_OOM, "device timers"));
   if (c->opt.precision != PDEP_FP64 && c->opt.precision != PDEP_MIXED_TF32 &&
       c->opt.precision != PDEP_MIXED_BF16)
     return bail(fail(PDEP_ERR_INVALID_ARG, "unknown precision mode"));

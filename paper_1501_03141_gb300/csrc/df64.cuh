@@ -65,6 +65,28 @@ __device__ __forceinline__ df& operator+=(df& a, df b) {
   return a;
 }
 
+// c + a b with one rounding of the exact product's error terms: the product's
+// high part and c's high part are summed exactly (TwoSum), the product error
+// (one FMA per cross term) and the low parts added, then renormalised
+__device__ __forceinline__ df fma_df(df a, df b, df c) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  const df s = two_sum(p, c.hi);
+  const float l = __fadd_rn(s.lo, __fadd_rn(e, c.lo));
+  return fast_two_sum(s.hi, l);
+}
+// acc + a b in the arithmetic of the type (an FMA for float and double)
+template <typename R>
+__device__ __forceinline__ R mad(R a, R b, R acc) {
+  return acc + a * b;
+}
+template <>
+__device__ __forceinline__ df mad<df>(df a, df b, df acc) {
+  return fma_df(a, b, acc);
+}
+
 // complex helpers the line FFTs need for df (the generic ones use __ldg and
 // one shuffle per component)
 template <>

@@ -1,4 +1,6 @@
 // Dense linear algebra, vector and CG kernels (see linalg.cuh).
+#include <type_traits>
+
 #include "linalg.cuh"
 #include "profile.cuh"
 
@@ -82,13 +84,17 @@ __device__ __forceinline__ double2 block_sum2_r(R a, R b) {
 // outputs), K tiles of 16 staged in shared memory.  TM = 5 gives 80-row tiles
 // for the 80-state projection coefficients (n_occ + n_deflate on the 48^3
 // workload), which 64-row tiles would cover with 37% padding.
+// R: arithmetic type (float, double, or df: double-float on FP64 matrices);
+// matrices are stored in Io<R>::T.
 template <typename R, bool TA, int TM>
-__global__ void __launch_bounds__(256) k_gemm(int m, int n, int k, R alpha, const R* __restrict__ A,
-                                              long long lda, const R* __restrict__ B, long long ldb,
-                                              R beta, R* __restrict__ C, long long ldc, int kchunk,
+__global__ void __launch_bounds__(256) k_gemm(int m, int n, int k, R alpha,
+                                              const typename Io<R>::T* __restrict__ A,
+                                              long long lda, const typename Io<R>::T* __restrict__ B,
+                                              long long ldb, R beta, typename Io<R>::T* __restrict__ C,
+                                              long long ldc, int kchunk,
                                               int atomic, const int* __restrict__ bmap,
                                               const int* __restrict__ cmap,
-                                              const int* __restrict__ ndev) {
+                                              const int* __restrict__ ndev, int has_beta) {
   constexpr int BM = 16 * TM, BN = 64, BK = 16;
   __shared__ R As[BK][BM + 1];
   __shared__ R Bs[BK][BN + 1];
@@ -113,11 +119,11 @@ __global__ void __launch_bounds__(256) k_gemm(int m, int n, int k, R alpha, cons
         // A is k x m: consecutive threads read consecutive k of one row
         const int i = e >> 4, kk = e & 15;
         const int gi = row0 + i, gk = kb + kk;
-        As[kk][i] = (gi < m && gk < kend) ? A[gk + (long long)gi * lda] : R(0);
+        As[kk][i] = (gi < m && gk < kend) ? R(A[gk + (long long)gi * lda]) : R(0);
       } else {
         const int i = e % BM, kk = e / BM;
         const int gi = row0 + i, gk = kb + kk;
-        As[kk][i] = (gi < m && gk < kend) ? A[gi + (long long)gk * lda] : R(0);
+        As[kk][i] = (gi < m && gk < kend) ? R(A[gi + (long long)gk * lda]) : R(0);
       }
     }
     {
@@ -127,7 +133,7 @@ __global__ void __launch_bounds__(256) k_gemm(int m, int n, int k, R alpha, cons
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int gk = kb + kk0 + q;
-        Bs[kk0 + q][j] = (gj < n && gk < kend) ? B[gk + bc] : R(0);
+        Bs[kk0 + q][j] = (gj < n && gk < kend) ? R(B[gk + bc]) : R(0);
       }
     }
     __syncthreads();
@@ -141,7 +147,7 @@ __global__ void __launch_bounds__(256) k_gemm(int m, int n, int k, R alpha, cons
 #pragma unroll
       for (int a = 0; a < TM; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+        for (int b = 0; b < 4; ++b) acc[a][b] = mad(av[a], bv[b], acc[a][b]);
     }
     __syncthreads();
   }
@@ -153,13 +159,13 @@ __global__ void __launch_bounds__(256) k_gemm(int m, int n, int k, R alpha, cons
     for (int b = 0; b < 4; ++b) {
       const int gj = col0 + ty + 16 * b;
       if (gj >= n) continue;
-      R* c = C + gi + (long long)(cmap ? cmap[gj] : gj) * ldc;
+      typename Io<R>::T* c = C + gi + (long long)(cmap ? cmap[gj] : gj) * ldc;
       if (atomic) {
-        atomicAdd(c, alpha * acc[a][b]);
+        atomicAdd(c, io_of<R>(alpha * acc[a][b]));
       } else {
         R v = alpha * acc[a][b];
-        if (beta != R(0)) v += beta * *c;
-        *c = v;
+        if (has_beta) v += beta * R(*c);
+        *c = io_of<R>(v);
       }
     }
   }
@@ -179,9 +185,11 @@ __global__ void k_scale_mat(R* C, long long ldc, int m, int n, R beta, const int
 }
 
 template <typename R>
-cudaError_t gemm(bool transA, int m, int n, int k, double alpha, const R* A, long long lda,
-                 const R* B, long long ldb, double beta, R* C, long long ldc, cudaStream_t st,
-                 const int* bmap, const int* cmap, const int* ndev) {
+cudaError_t gemm(bool transA, int m, int n, int k, double alpha, const typename Io<R>::T* A,
+                 long long lda, const typename Io<R>::T* B, long long ldb, double beta,
+                 typename Io<R>::T* C, long long ldc, cudaStream_t st, const int* bmap,
+                 const int* cmap, const int* ndev) {
+  using T = typename Io<R>::T;
   if (m <= 0 || n <= 0) return cudaSuccess;
   // 80-row tiles when they pad m less than 64-row tiles do
   const bool t80 = ((m + 79) / 80) * 80 < ((m + 63) / 64) * 64;
@@ -204,30 +212,32 @@ cudaError_t gemm(bool transA, int m, int n, int k, double alpha, const R* A, lon
     const long long tot = (long long)m * n;
     const int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
     count_launch();
-    k_scale_mat<R><<<blocks, 256, 0, st>>>(C, ldc, m, n, (R)beta, cmap, ndev);
+    k_scale_mat<T><<<blocks, 256, 0, st>>>(C, ldc, m, n, (T)beta, cmap, ndev);
     if (k <= 0) return cudaGetLastError();
     atomic = 1;
   }
   dim3 grid(tm, tn, splits);
-  ProfScope ps(sizeof(R) == 8 ? PC_GEMM_F64 : PC_GEMM_F32, st, 2.0 * m * n * (double)k,
-               ((double)m * k + (double)k * n + (beta != 0.0 ? 2.0 : 1.0) * m * n) * sizeof(R),
+  ProfScope ps(std::is_same<R, df>::value ? PC_GEMM_DF : sizeof(R) == 8 ? PC_GEMM_F64 : PC_GEMM_F32,
+               st, 2.0 * m * n * (double)k,
+               ((double)m * k + (double)k * n + (beta != 0.0 ? 2.0 : 1.0) * m * n) * sizeof(T),
                ndev, n);
   count_launch();
-  const R al = (R)alpha, be = (R)beta;
+  const R al = R(alpha), be = R(beta);
+  const int hb = beta != 0.0 ? 1 : 0;
   if (transA) {
     if (t80)
       k_gemm<R, true, 5><<<grid, 256, 0, st>>>(m, n, k, al, A, lda, B, ldb, be, C, ldc, kchunk,
-                                               atomic, bmap, cmap, ndev);
+                                               atomic, bmap, cmap, ndev, hb);
     else
       k_gemm<R, true, 4><<<grid, 256, 0, st>>>(m, n, k, al, A, lda, B, ldb, be, C, ldc, kchunk,
-                                               atomic, bmap, cmap, ndev);
+                                               atomic, bmap, cmap, ndev, hb);
   } else {
     if (t80)
       k_gemm<R, false, 5><<<grid, 256, 0, st>>>(m, n, k, al, A, lda, B, ldb, be, C, ldc, kchunk,
-                                                atomic, bmap, cmap, ndev);
+                                                atomic, bmap, cmap, ndev, hb);
     else
       k_gemm<R, false, 4><<<grid, 256, 0, st>>>(m, n, k, al, A, lda, B, ldb, be, C, ldc, kchunk,
-                                                atomic, bmap, cmap, ndev);
+                                                atomic, bmap, cmap, ndev, hb);
   }
   return cudaGetLastError();
 }
@@ -235,6 +245,9 @@ cudaError_t gemm(bool transA, int m, int n, int k, double alpha, const R* A, lon
 template cudaError_t gemm<double>(bool, int, int, int, double, const double*, long long,
                                   const double*, long long, double, double*, long long,
                                   cudaStream_t, const int*, const int*, const int*);
+template cudaError_t gemm<df>(bool, int, int, int, double, const double*, long long,
+                              const double*, long long, double, double*, long long, cudaStream_t,
+                              const int*, const int*, const int*);
 template cudaError_t gemm<float>(bool, int, int, int, double, const float*, long long,
                                  const float*, long long, double, float*, long long, cudaStream_t,
                                  const int*, const int*, const int*);
@@ -1298,7 +1311,7 @@ __global__ void __launch_bounds__(512) k_cg_step_reg(CgArgs<R> a, const int* __r
   const double2 t2 = block_sum2_r<R>(rr, rkr);
   if (threadIdx.x == 0) {
     const double rn = sqrt(t2.x);
-    const bool done = rn <= a.tol * s.bnorm;
+    const bool done = rn <= (a.tolv ? a.tolv[i] : a.tol) * s.bnorm;
     flag = done ? 2 : 0;
     coef[1] = (R)(t2.y / s.rz);
     cg_finish(a, i, s, rn, t2.y, done);
@@ -1356,7 +1369,7 @@ __global__ void __launch_bounds__(512) k_cg_step(CgArgs<R> a, const int* __restr
   const double2 t2 = block_sum2_r<R>(rr, rkr);
   if (threadIdx.x == 0) {
     const double rn = sqrt(t2.x);
-    const bool done = rn <= a.tol * s.bnorm;
+    const bool done = rn <= (a.tolv ? a.tolv[i] : a.tol) * s.bnorm;
     flag = done ? 2 : 0;
     coef[1] = (R)(t2.y / s.rz);
     cg_finish(a, i, s, rn, t2.y, done);
@@ -1562,9 +1575,15 @@ cudaError_t fill_value(double* x, int n, double v, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Ri: the inner solve's precision (float: mixed modes, double: FP64 path).
+// tolv (may be null): per-RHS relative tolerance of the inner solve,
+// min(inner_cap, target / rel_i), so that the inner solve ends at an FP64
+// residual of target x ||b_i||.
+template <typename Ri>
 __global__ void k_refine_prepare(const double* __restrict__ r64, long long ld64, int n_pw,
-                                 const double* __restrict__ rel, double tol, float* r32,
-                                 long long ld32, double* rn) {
+                                 const double* __restrict__ rel, double tol, Ri* ri,
+                                 long long ldi, double* rn, double* tolv, double target,
+                                 double inner_cap) {
   const int i = blockIdx.x;
   const bool act = rel[i] > tol;
   double ss = 0.0;
@@ -1576,16 +1595,32 @@ __global__ void k_refine_prepare(const double* __restrict__ r64, long long ld64,
   const double2 t = block_sum2(ss, 0.0);
   const double nrm = sqrt(t.x);
   const double f = (act && nrm > 0.0) ? 1.0 / nrm : 0.0;
-  for (int j = threadIdx.x; j < n_pw; j += blockDim.x)
-    r32[(long long)i * ld32 + j] = (float)(f * r64[(long long)i * ld64 + j]);
-  if (threadIdx.x == 0) rn[i] = act ? nrm : 0.0;
+  // a converged RHS keeps rn = 0 and takes no part in the inner solve (its
+  // scaled residual is not written)
+  if (act)
+    for (int j = threadIdx.x; j < n_pw; j += blockDim.x)
+      ri[(long long)i * ldi + j] = (Ri)(f * r64[(long long)i * ld64 + j]);
+  if (threadIdx.x == 0) {
+    rn[i] = act ? nrm : 0.0;
+    if (tolv) tolv[i] = act ? fmin(inner_cap, target / rel[i]) : inner_cap;
+  }
 }
+template <typename Ri>
 cudaError_t refine_prepare(const double* r64, long long ld64, int n_pw, int n, const double* rel,
-                           double tol, float* r32, long long ld32, double* rn, cudaStream_t st) {
+                           double tol, Ri* ri, long long ldi, double* rn, cudaStream_t st,
+                           double* tolv, double target, double inner_cap) {
   if (n <= 0) return cudaSuccess;
-  { count_launch(); k_refine_prepare<<<n, 256, 0, st>>>(r64, ld64, n_pw, rel, tol, r32, ld32, rn); }
+  count_launch();
+  k_refine_prepare<Ri><<<n, 256, 0, st>>>(r64, ld64, n_pw, rel, tol, ri, ldi, rn, tolv, target,
+                                          inner_cap);
   return cudaGetLastError();
 }
+template cudaError_t refine_prepare<float>(const double*, long long, int, int, const double*, double,
+                                           float*, long long, double*, cudaStream_t, double*,
+                                           double, double);
+template cudaError_t refine_prepare<double>(const double*, long long, int, int, const double*,
+                                            double, double*, long long, double*, cudaStream_t,
+                                            double*, double, double);
 __global__ void k_refine_accumulate(double* x64, long long ld64, const float* __restrict__ d32,
                                     long long ld32, int n_pw, const double* __restrict__ rn) {
   const int i = blockIdx.x;
@@ -1605,7 +1640,8 @@ cudaError_t refine_accumulate(double* x64, long long ld64, const float* d32, lon
 // vectors with rn_i = 0 and no xd are skipped.  Without d32 (the FP64 path,
 // x holding the whole CG solution): delta_i = x_i + xd_i.  Then x_i += delta_i
 // (x_i = delta_i without d32) and dl_i = delta_i.
-__global__ void k_refine_delta(double* x, double* dl, long long ld, const float* __restrict__ d32,
+template <typename Ri>
+__global__ void k_refine_delta(double* x, double* dl, long long ld, const Ri* __restrict__ d32,
                                long long ld32, int n_pw, const double* __restrict__ rn,
                                const double* __restrict__ xd) {
   const int i = blockIdx.x;
@@ -1626,12 +1662,17 @@ __global__ void k_refine_delta(double* x, double* dl, long long ld, const float*
     di[j] = d;
   }
 }
-cudaError_t refine_delta(double* x, double* dl, long long ld, const float* d32, long long ld32,
+template <typename Ri>
+cudaError_t refine_delta(double* x, double* dl, long long ld, const Ri* d32, long long ld32,
                          int n_pw, int n, const double* rn, const double* xd, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  { count_launch(); k_refine_delta<<<n, 256, 0, st>>>(x, dl, ld, d32, ld32, n_pw, rn, xd); }
+  { count_launch(); k_refine_delta<Ri><<<n, 256, 0, st>>>(x, dl, ld, d32, ld32, n_pw, rn, xd); }
   return cudaGetLastError();
 }
+template cudaError_t refine_delta<float>(double*, double*, long long, const float*, long long, int,
+                                         int, const double*, const double*, cudaStream_t);
+template cudaError_t refine_delta<double>(double*, double*, long long, const double*, long long,
+                                          int, int, const double*, const double*, cudaStream_t);
 
 // r_i -= ad_i (+ s_{i mod n_occ} xd_i), rel_i = ||r_i|| / ||b_i|| for the
 // listed (or all) vectors.  s_v = eps_{n_ext} - eps_v is the shifted

@@ -15,12 +15,14 @@ namespace pdep {
 // Split over k (atomic accumulation) when the tile count is small.  Optional
 // column maps: column j of B is B[:, bmap[j]] and column j of C is C[:, cmap[j]].
 // ndev (optional): device count of the mapped columns (<= n); the launch is
-// sized for n and columns from *ndev on are left untouched.
+// sized for n and columns from *ndev on are left untouched.  R is the
+// arithmetic type: float, double, or df (double-float arithmetic on the FP32
+// pipe; the matrices are FP64).
 template <typename R>
-cudaError_t gemm(bool transA, int m, int n, int k, double alpha, const R* A, long long lda,
-                 const R* B, long long ldb, double beta, R* C, long long ldc, cudaStream_t st,
-                 const int* bmap = nullptr, const int* cmap = nullptr,
-                 const int* ndev = nullptr);
+cudaError_t gemm(bool transA, int m, int n, int k, double alpha, const typename Io<R>::T* A,
+                 long long lda, const typename Io<R>::T* B, long long ldb, double beta,
+                 typename Io<R>::T* C, long long ldc, cudaStream_t st, const int* bmap = nullptr,
+                 const int* cmap = nullptr, const int* ndev = nullptr);
 
 // Symmetric eigendecomposition of the n x n matrix M (lda), FP64:
 // one-sided (Hestenes) Jacobi on M - sigma I (sigma = twice the Gershgorin
@@ -160,6 +162,7 @@ struct CgArgs {
   const int* list_count = nullptr;  // device length of the active list (cg_step sized for
                                     // the largest; blocks past it exit)
   const double* mask = nullptr;     // cg_start: RHS i takes part only if mask[i] != 0
+  const double* tolv = nullptr;     // per-RHS relative tolerance (replaces tol when set)
 };
 
 // Device state of one Sternheimer CG loop (context-owned device memory).
@@ -230,17 +233,23 @@ cudaError_t unconverged_list(const double* rel, double tol, int n, int* list, in
 cudaError_t active_list_reset(const CgScal* sc, int n, int* list, int* count, int* reset,
                               cudaStream_t st);
 
-// Mixed-precision refinement: for i with rel[i] > tol, rn[i] = ||r64_i|| and
-// r32_i = r64_i / rn[i]; otherwise rn[i] = 0 and r32_i = 0.
+// Refinement rounds: for i with rel[i] > tol, rn[i] = ||r64_i|| and ri_i =
+// r64_i / rn[i] in the inner precision Ri (float or double); otherwise rn[i]
+// = 0 and ri_i is left as it is.  tolv (optional): tolv[i] = min(inner_cap,
+// target / rel[i]), the relative tolerance that brings the FP64 residual to
+// target x ||b_i||.
+template <typename Ri>
 cudaError_t refine_prepare(const double* r64, long long ld64, int n_pw, int n, const double* rel,
-                           double tol, float* r32, long long ld32, double* rn, cudaStream_t st);
+                           double tol, Ri* ri, long long ldi, double* rn, cudaStream_t st,
+                           double* tolv = nullptr, double target = 0.0, double inner_cap = 0.0);
 // x64_i += rn[i] * d32_i
 cudaError_t refine_accumulate(double* x64, long long ld64, const float* d32, long long ld32,
                               int n_pw, int n, const double* rn, cudaStream_t st);
 
-// Refinement update in FP64: delta_i = rn_i d32_i (+ xd_i), x_i += delta_i,
-// dl_i = delta_i; with d32 = null, delta_i = x_i + xd_i and x_i = delta_i.
-cudaError_t refine_delta(double* x, double* dl, long long ld, const float* d32, long long ld32,
+// Refinement update in FP64: delta_i = rn_i d_i (+ xd_i), x_i += delta_i,
+// dl_i = delta_i; with d = null, delta_i = x_i + xd_i and x_i = delta_i.
+template <typename Ri>
+cudaError_t refine_delta(double* x, double* dl, long long ld, const Ri* d, long long ldd,
                          int n_pw, int n, const double* rn, const double* xd, cudaStream_t st);
 // r_i -= ad_i (+ sv[i % n_occ] xd_i); rel_i = ||r_i|| / ||b_i|| (listed vectors;
 // ndev: device length of the list, <= n)

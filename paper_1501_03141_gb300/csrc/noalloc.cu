@@ -8,6 +8,7 @@
 // pdep_apply_hamiltonian, but its transform scratch lives in the fixed,
 // file-scope device array below instead of the context's growable workspace,
 // and it stages nothing: x and y must already be device buffers.
+#include <atomic>
 #include <cstring>
 
 #include "common.cuh"
@@ -23,27 +24,35 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratch
 
 namespace {
 constexpr int kMaxDevices = 64;
-void* g_scratch_addr[kMaxDevices] = {nullptr};
+// concurrent first calls may both look the address up; they store the same
+// value, and the atomics keep that free of data races
+std::atomic<void*> g_scratch_addr[kMaxDevices] = {};
 
 // Host code must not use g_noalloc_scratch directly: its host-side name is a
 // stand-in, not a device address.  Look the address up once per device, with
-// that device current.
-int scratch_address(void** out) {
+// that device current: the context's device, which must be the current one
+// (the scratch of another GPU would be given to this GPU's kernels).
+int scratch_address(int ctx_device, void** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     cudaGetLastError();
     return PDEP_ERR_CUDA;
   }
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
+  if (dev != ctx_device) {
+    set_last_error(__FILE__, __LINE__,
+                   "the current device is not the context's: make it current before the call");
+    return PDEP_ERR_INVALID_ARG;
+  }
+  void* p = g_scratch_addr[dev].load();
+  if (!p) {
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) {
       set_last_error(__FILE__, __LINE__, cudaGetErrorString(e));
       return PDEP_ERR_CUDA;
     }
-    g_scratch_addr[dev] = p;
+    g_scratch_addr[dev].store(p);
   }
-  *out = g_scratch_addr[dev];
+  *out = p;
   return PDEP_OK;
 }
 
@@ -57,8 +66,10 @@ bool on_device(const void* p) {
 }
 }  // namespace
 
-// Sphere description of one system, filled from the context (no copies).
-int noalloc_sphere(pdep_ctx* ctx, int sys, SphereDev<double>* sd, const double** v, int* n_pw);
+// Sphere description of one system and the context's device, filled from the
+// context (no copies).
+int noalloc_sphere(pdep_ctx* ctx, int sys, SphereDev<double>* sd, const double** v, int* n_pw,
+                   int* device);
 
 }  // namespace pdep
 
@@ -68,8 +79,8 @@ extern "C" int pdep_apply_hamiltonian_noalloc(pdep_ctx* ctx, int sys, const doub
                                               double* y, void* stream) {
   SphereDev<double> sd{};
   const double* v = nullptr;
-  int n_pw = 0;
-  int r = noalloc_sphere(ctx, sys, &sd, &v, &n_pw);
+  int n_pw = 0, device = 0;
+  int r = noalloc_sphere(ctx, sys, &sd, &v, &n_pw, &device);
   if (r != PDEP_OK) return r;
   if (n < 0 || (n > 0 && (!x || !y))) {
     set_last_error(__FILE__, __LINE__, "bad arguments");
@@ -88,7 +99,7 @@ extern "C" int pdep_apply_hamiltonian_noalloc(pdep_ctx* ctx, int sys, const doub
     return PDEP_ERR_UNSUPPORTED;
   }
   void* scratch = nullptr;
-  r = scratch_address(&scratch);
+  r = scratch_address(device, &scratch);
   if (r != PDEP_OK) return r;
   cudaStream_t st = (cudaStream_t)stream;
   cpx<double>* b1 = reinterpret_cast<cpx<double>*>(scratch);

@@ -26,7 +26,8 @@ struct Acc {
 const char* kNames[PDEP_PROFILE_CLASSES] = {"cols_f64", "cols_f32",    "slab_f64",    "slab_f32",
                                             "gemm_f64", "gemm_f32",    "cg_f64",      "cg_f32",
                                             "eigh",     "other",       "gemm_tf32x3", "cg_graph_f32",
-                                            "cg_graph_f64", "cols_df64", "slab_df64"};
+                                            "cg_graph_f64", "cols_df64", "slab_df64",
+                                            "hpsi_fused_f32", "gemm_df64"};
 thread_local bool t_capturing = false;
 thread_local int t_capture_launches = 0;
 std::atomic<long long> g_launches{0};
@@ -128,6 +129,34 @@ int capture_end() {
 
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
+namespace {
+DevTimer* g_timers = nullptr;  // [PDEP_PROFILE_CLASSES], device memory
+std::mutex g_timer_mu;
+void reset_timers() {
+  if (!g_timers) return;
+  std::vector<DevTimer> h(PDEP_PROFILE_CLASSES);
+  for (DevTimer& t : h) {
+    memset(&t, 0, sizeof(t));
+    t.t_min = ~0ull;
+  }
+  cudaMemcpy(g_timers, h.data(), sizeof(DevTimer) * h.size(), cudaMemcpyHostToDevice);
+}
+}  // namespace
+
+int dev_timers_init() {
+  std::lock_guard<std::mutex> g(g_timer_mu);
+  if (g_timers) return 0;
+  if (cudaMalloc(&g_timers, sizeof(DevTimer) * PDEP_PROFILE_CLASSES) != cudaSuccess) {
+    cudaGetLastError();
+    g_timers = nullptr;
+    return 1;
+  }
+  reset_timers();
+  return 0;
+}
+
+DevTimer* dev_timer(int cls) { return g_timers ? g_timers + cls : nullptr; }
+
 // records nothing while the stream is being captured (events cannot time a
 // kernel inside a graph, and resolving records waits on events, which a
 // capture forbids)
@@ -180,11 +209,35 @@ extern "C" int pdep_profile(int enable, pdep_profile_t* out) {
     p.resolve();
     for (auto& a : p.acc) a = Acc();
     p.launches = 0;
+    {
+      std::lock_guard<std::mutex> tg(g_timer_mu);
+      cudaDeviceSynchronize();
+      reset_timers();
+    }
     p.on = true;
     return PDEP_OK;
   }
   p.resolve();
   p.on = false;
+  {
+    // kernels timed on the device (also those inside graphs)
+    std::lock_guard<std::mutex> tg(g_timer_mu);
+    if (g_timers) {
+      std::vector<DevTimer> h(PDEP_PROFILE_CLASSES);
+      cudaDeviceSynchronize();
+      if (cudaMemcpy(h.data(), g_timers, sizeof(DevTimer) * h.size(), cudaMemcpyDeviceToHost) ==
+          cudaSuccess) {
+        for (int i = 0; i < PDEP_PROFILE_CLASSES; ++i) {
+          p.acc[i].launches += (long long)h[i].launches;
+          p.acc[i].ms += h[i].total_ns * 1e-6;
+          p.acc[i].flops += h[i].flops;
+          p.acc[i].bytes += h[i].bytes;
+        }
+      } else {
+        cudaGetLastError();
+      }
+    }
+  }
   if (out) {
     memset(out, 0, sizeof(*out));
     out->launches = p.launches.load();

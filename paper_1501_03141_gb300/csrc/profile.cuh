@@ -21,6 +21,8 @@ enum ProfClass : int {
   PC_CG_GRAPH_F64 = 12,  // timed one by one inside a graph)
   PC_COLS_DF = 13,       // double-float transforms (mixed-precision refinement)
   PC_SLAB_DF = 14,
+  PC_HPSI_FUSED = 15,    // FP32 H x in one launch (column scratch in shared memory)
+  PC_GEMM_DF = 16,       // double-float GEMMs (mixed-precision projections)
 };
 
 // counts one kernel launch (always cheap); while this thread captures a
@@ -31,6 +33,47 @@ void capture_begin();
 int capture_end();
 // kernels launched by this process outside graph captures (always counted)
 long long launch_count();
+
+// Device-side timing of kernels that also run inside CUDA graphs, where
+// events cannot time a single kernel: thread 0 of every block records
+// %globaltimer at the block's start and end; the last block of a launch adds
+// max(end) - min(start) and the launch's work to its class.  pdep_profile
+// resets the timers when it starts and folds them into the profile when it
+// stops.  The timers live in device memory allocated by dev_timers_init (on
+// the current device, once per process, before any capture).
+struct DevTimer {
+  unsigned long long t_min, t_max;
+  unsigned long long total_ns, launches;
+  double flops, bytes;
+  unsigned int done, pad;
+};
+int dev_timers_init();
+DevTimer* dev_timer(int cls);
+
+__device__ __forceinline__ unsigned long long dev_clock_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// called by thread 0 of every block at its end (t0: its start)
+__device__ __forceinline__ void dev_timer_block_end(DevTimer* t, unsigned long long t0,
+                                                    double flops, double bytes) {
+  if (!t) return;
+  atomicMin(&t->t_min, t0);
+  atomicMax(&t->t_max, dev_clock_ns());
+  if (flops != 0.0) atomicAdd(&t->flops, flops);
+  if (bytes != 0.0) atomicAdd(&t->bytes, bytes);
+  __threadfence();
+  if (atomicAdd(&t->done, 1u) == gridDim.x - 1) {
+    __threadfence();
+    const unsigned long long lo = atomicOr(&t->t_min, 0ull), hi = atomicOr(&t->t_max, 0ull);
+    t->total_ns += hi > lo ? hi - lo : 0ull;
+    t->launches += 1;
+    t->t_min = ~0ull;
+    t->t_max = 0ull;
+    t->done = 0u;
+  }
+}
 
 // RAII timer around one launch: events are recorded only while profiling.
 // flops and bytes are those of a launch over 'units' work units; when the

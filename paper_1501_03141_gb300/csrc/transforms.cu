@@ -80,6 +80,11 @@ __device__ __forceinline__ void cols_fwd_line(const SphereDev<R>& s,
                                               long long ldx, const ItemMap& map, int nl,
                                               int coef, cpx<R>* __restrict__ b1, long long g,
                                               long long total);
+template <typename R, int N1>
+__device__ __forceinline__ void xline_inverse(const SphereDev<R>& s,
+                                              const typename Io<R>::T* __restrict__ x,
+                                              long long ldx, const ItemMap& map, int nl, int coef,
+                                              int item, int uc, bool live, cpx<R>* base);
 
 template <typename R, int N1>
 __global__ void __launch_bounds__(128) k_cols_fwd(SphereDev<R> s,
@@ -102,13 +107,25 @@ __device__ __forceinline__ void cols_fwd_line(const SphereDev<R>& s,
                                               long long ldx, const ItemMap& map, int nl,
                                               int coef, cpx<R>* __restrict__ b1, long long g,
                                               long long total) {
-  constexpr int TPL = Tpl<R, N1>::v;
-  constexpr int M = N1 / TPL;
-  const int t = threadIdx.x & (TPL - 1);
   const bool live = g < total;
   const int item = live ? (int)(g / s.n_ucol) : 0;
   const int uc = live ? (int)(g - (long long)item * s.n_ucol) : 0;
-  const UCol c = s.ucol[uc];
+  xline_inverse<R, N1>(s, x, ldx, map, nl, coef, item, uc, live,
+                       b1 + (long long)item * N1 * s.n_col);
+}
+
+// x-line uc of item (both members of its mirror pair) from the sphere into
+// the item's column scratch 'base' ([N1][n_col], global or shared memory);
+// every lane of the warp must call it (the FFT shuffles), live or not.
+template <typename R, int N1>
+__device__ __forceinline__ void xline_inverse(const SphereDev<R>& s,
+                                              const typename Io<R>::T* __restrict__ x,
+                                              long long ldx, const ItemMap& map, int nl, int coef,
+                                              int item, int uc, bool live, cpx<R>* base) {
+  constexpr int TPL = Tpl<R, N1>::v;
+  constexpr int M = N1 / TPL;
+  const int t = threadIdx.x & (TPL - 1);
+  const UCol c = s.ucol[live ? uc : 0];
   const bool active = live && ucol_in_range(s, c);
   const bool self = (c.col == c.mcol);
   const int ia = map.vec(item, 0, nl), ib = map.vec(item, 1, nl);
@@ -155,7 +172,6 @@ __device__ __forceinline__ void cols_fwd_line(const SphereDev<R>& s,
   fft_a2b<R, N1, TPL, +1>(v0, t, s.tw1);
   fft_a2b<R, N1, TPL, +1>(v1, t, s.tw1);
   if (!active) return;
-  cpx<R>* base = b1 + (long long)item * N1 * s.n_col;
 #pragma unroll
   for (int i = 0; i < M; ++i) {
     const int i1 = pos_b<N1, TPL>(t, i);
@@ -186,6 +202,10 @@ __device__ __forceinline__ void cols_bwd_line(const SphereDev<R>& s,
                                               const cpx<R>* __restrict__ b1, const ItemMap& map,
                                               int nl, const Epilogue<R>& ep, long long g,
                                               long long total);
+template <typename R, int N1>
+__device__ __forceinline__ void xline_forward(const SphereDev<R>& s, const cpx<R>* base,
+                                              const ItemMap& map, int nl, const Epilogue<R>& ep,
+                                              int item, int uc, bool live);
 
 template <typename R, int N1>
 __global__ void __launch_bounds__(128) k_cols_bwd(SphereDev<R> s, const cpx<R>* __restrict__ b1,
@@ -203,18 +223,27 @@ __device__ __forceinline__ void cols_bwd_line(const SphereDev<R>& s,
                                               const cpx<R>* __restrict__ b1, const ItemMap& map,
                                               int nl, const Epilogue<R>& ep, long long g,
                                               long long total) {
+  const bool live = g < total;
+  const int item = live ? (int)(g / s.n_ucol) : 0;
+  const int uc = live ? (int)(g - (long long)item * s.n_ucol) : 0;
+  xline_forward<R, N1>(s, b1 + (long long)item * N1 * s.n_col, map, nl, ep, item, uc, live);
+}
+
+// x-line uc of item from its column scratch 'base' back to the sphere, the
+// two real fields unpacked, through the epilogue; every lane of the warp
+// must call it.
+template <typename R, int N1>
+__device__ __forceinline__ void xline_forward(const SphereDev<R>& s, const cpx<R>* base,
+                                              const ItemMap& map, int nl, const Epilogue<R>& ep,
+                                              int item, int uc, bool live) {
   constexpr int TPL = Tpl<R, N1>::v;
   constexpr int M = N1 / TPL;
   const int lane = threadIdx.x & 31;
   const int t = threadIdx.x & (TPL - 1);
-  const bool live = g < total;
-  const int item = live ? (int)(g / s.n_ucol) : 0;
-  const int uc = live ? (int)(g - (long long)item * s.n_ucol) : 0;
-  const UCol c = s.ucol[uc];
+  const UCol c = s.ucol[live ? uc : 0];
   const bool active = live && ucol_in_range(s, c);
   const bool self = (c.col == c.mcol);
 
-  const cpx<R>* base = b1 + (long long)item * N1 * s.n_col;
   cpx<R> v0[M], v1[M];
 #pragma unroll
   for (int i = 0; i < M; ++i) {
@@ -310,20 +339,23 @@ __device__ __forceinline__ int t2_at(int row, int col, int ts) {
   return row * ts + col;
 }
 
+// tid / nthreads: the thread's index in, and the size of, the (warp-aligned)
+// group of threads that transforms this plane
 template <typename R, int N2>
-__device__ __forceinline__ void y_inverse(const SphereDev<R>& s, const cpx<R>* S1, cpx<R>* T2) {
+__device__ __forceinline__ void y_inverse(const SphereDev<R>& s, const cpx<R>* S1, cpx<R>* T2,
+                                          int tid, int nthreads) {
   constexpr int TL = Tpl<R, N2>::v;
   constexpr int TS = T2Stride<R, N2>::v;
   constexpr int M = N2 / TL;
   const int nslot = 2 * s.R3 + 1;
-  const int per = blockDim.x / TL;
-  const int t = threadIdx.x & (TL - 1);
+  const int per = nthreads / TL;
+  const int t = tid & (TL - 1);
   // first slot of this warp in a round: warps whose slots all lie past the
   // last (n3) row skip the line FFTs instead of transforming zeros
-  const int wslot0 = (threadIdx.x & ~31) / TL;
+  const int wslot0 = (tid & ~31) / TL;
   for (int base = 0; base < nslot; base += per) {
     if (base + wslot0 >= nslot) break;
-    const int sl = base + threadIdx.x / TL;
+    const int sl = base + tid / TL;
     const bool live = sl < nslot;
     const int2 info = live ? s.slot[sl] : make_int2(-1, 0);
     const bool act = live && slot_in_range(s, info);
@@ -342,17 +374,18 @@ __device__ __forceinline__ void y_inverse(const SphereDev<R>& s, const cpx<R>* S
 }
 
 template <typename R, int N2>
-__device__ __forceinline__ void y_forward(const SphereDev<R>& s, const cpx<R>* T2, cpx<R>* S1) {
+__device__ __forceinline__ void y_forward(const SphereDev<R>& s, const cpx<R>* T2, cpx<R>* S1,
+                                          int tid, int nthreads) {
   constexpr int TL = Tpl<R, N2>::v;
   constexpr int TS = T2Stride<R, N2>::v;
   constexpr int M = N2 / TL;
   const int nslot = 2 * s.R3 + 1;
-  const int per = blockDim.x / TL;
-  const int t = threadIdx.x & (TL - 1);
-  const int wslot0 = (threadIdx.x & ~31) / TL;
+  const int per = nthreads / TL;
+  const int t = tid & (TL - 1);
+  const int wslot0 = (tid & ~31) / TL;
   for (int base = 0; base < nslot; base += per) {
     if (base + wslot0 >= nslot) break;
-    const int sl = base + threadIdx.x / TL;
+    const int sl = base + tid / TL;
     const bool live = sl < nslot;
     const int2 info = live ? s.slot[sl] : make_int2(-1, 0);
     const bool act = live && slot_in_range(s, info);
@@ -386,7 +419,7 @@ __device__ __forceinline__ void slab_unit(const SphereDev<R>& s, const SlabArgs<
   if (a.mode != SLAB_FROM_GRID) {
     for (int j = threadIdx.x; j < s.n_col; j += blockDim.x) S1[j] = row[j];
     __syncthreads();
-    y_inverse<R, N2>(s, S1, T2);
+    y_inverse<R, N2>(s, S1, T2, threadIdx.x, blockDim.x);
     __syncthreads();
   }
 
@@ -480,7 +513,7 @@ __device__ __forceinline__ void slab_unit(const SphereDev<R>& s, const SlabArgs<
   }
   if (a.mode == SLAB_TO_GRID) return;
   __syncthreads();
-  y_forward<R, N2>(s, T2, S1);
+  y_forward<R, N2>(s, T2, S1, threadIdx.x, blockDim.x);
   __syncthreads();
   for (int j = threadIdx.x; j < s.n_col; j += blockDim.x) row[j] = S1[j];
 }
@@ -511,6 +544,107 @@ __global__ void __launch_bounds__(SlabThreads<R, N2, N3>::v, (SlabMinBlocks<R, N
     const int item = blockIdx.x;
     if (item >= n_items) return;
     slab_unit<R, N2, N3>(s, a, nl, item, blockIdx.y, S1, T2);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// fused FP32 H x: the whole transform of one item in one block
+// ---------------------------------------------------------------------------
+// For cubic grids whose column scratch of one item (N x n_col complex) fits
+// in shared memory (24^3 .. 48^3), one block of 512 threads runs, per item:
+// the x-line inverse FFTs of every column into shared memory, then the y and
+// z passes of G x-planes at a time (each plane on its own warp-aligned group
+// of 512/G threads, the potential multiplied between the z inverse and
+// forward FFTs), then the x-line forward FFTs with the epilogue.  The column
+// scratch never leaves the SM: per item the HBM traffic is the two input
+// vectors (read for the transform and for the diagonal term) and the two
+// outputs, against a write, a read-modify-write and a read of the whole
+// scratch by the three-launch form.  Blocks are persistent over the items.
+constexpr int FUSED_THREADS = 512;
+
+// z-lines of one x-plane (T2: its (n3 slot, i2) plane), the potential
+// multiplied on the grid between the inverse and forward FFTs
+template <int N>
+__device__ __forceinline__ void z_hpsi(const SphereDev<float>& s, cpx<float>* T2,
+                                       const float* __restrict__ vplane, int tid, int nthreads) {
+  constexpr int TL3 = Tpl<float, N>::v;
+  constexpr int M3 = N / TL3;
+  constexpr int TS = T2Stride<float, N>::v;
+  const int R3 = s.R3;
+  const int t3 = tid & (TL3 - 1);
+  const int zper = nthreads / TL3;
+  for (int base = 0; base < N; base += zper) {
+    const int i2 = base + tid / TL3;
+    const bool act = i2 < N;
+    cpx<float> v[M3];
+#pragma unroll
+    for (int i = 0; i < M3; ++i) {
+      const int n3 = freq_of(pos_a<N, TL3>(t3, i), N);
+      v[i] = (act && iabs(n3) <= R3) ? T2[t2_at<float>(n3 + R3, i2, TS)] : zero<float>();
+    }
+    fft_a2b<float, N, TL3, +1>(v, t3, s.tw3);
+    const float* vr = vplane + (act ? i2 : 0) * N;
+#pragma unroll
+    for (int i = 0; i < M3; ++i) v[i] = scale(v[i], act ? vr[pos_b<N, TL3>(t3, i)] : 0.f);
+    fft_b2a<float, N, TL3, -1>(v, t3, s.tw3);
+    if (act) {
+#pragma unroll
+      for (int i = 0; i < M3; ++i) {
+        const int n3 = freq_of(pos_a<N, TL3>(t3, i), N);
+        if (iabs(n3) <= R3) T2[t2_at<float>(n3 + R3, i2, TS)] = v[i];
+      }
+    }
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(FUSED_THREADS, 1)
+    k_hpsi_fused(SphereDev<float> s, const float* __restrict__ x, long long ldx, ItemMap map,
+                 int n_items, const float* __restrict__ v, Epilogue<float> ep, int G,
+                 DevTimer* timer, double item_flops, double item_bytes) {
+  const unsigned long long t0 = dev_clock_ns();
+  constexpr int TL = Tpl<float, N>::v;
+  constexpr int TS = T2Stride<float, N>::v;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<float>* B1 = reinterpret_cast<cpx<float>*>(smem_raw);
+  const int nslot = 2 * s.R3 + 1;
+  const int nl = listed_count(map);
+  const int items = items_of(map, n_items, nl);
+  const int VT = blockDim.x / G;  // threads per plane: a multiple of 32
+  const int g = threadIdx.x / VT;
+  const int vt = threadIdx.x - g * VT;
+  cpx<float>* T2 = B1 + (size_t)N * s.n_col + (size_t)g * nslot * TS;
+  const int lines = blockDim.x / TL;
+#pragma unroll 1
+  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    __syncthreads();  // the previous item's reads of B1 are done
+#pragma unroll 1
+    for (int base = 0; base < s.n_ucol; base += lines) {
+      const int uc = base + threadIdx.x / TL;
+      xline_inverse<float, N>(s, x, ldx, map, nl, COEF_ONE, item, uc, uc < s.n_ucol, B1);
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int p0 = 0; p0 < N; p0 += G) {
+      const int i1 = p0 + g;
+      const bool plane = i1 < N;  // uniform over the plane's warps
+      cpx<float>* S1 = B1 + (size_t)(plane ? i1 : 0) * s.n_col;
+      if (plane) y_inverse<float, N>(s, S1, T2, vt, VT);
+      __syncthreads();
+      if (plane) z_hpsi<N>(s, T2, v + (size_t)i1 * N * N, vt, VT);
+      __syncthreads();
+      if (plane) y_forward<float, N>(s, T2, S1, vt, VT);
+      __syncthreads();
+    }
+#pragma unroll 1
+    for (int base = 0; base < s.n_ucol; base += lines) {
+      const int uc = base + threadIdx.x / TL;
+      xline_forward<float, N>(s, B1, map, nl, ep, item, uc, uc < s.n_ucol);
+    }
+  }
+  if (threadIdx.x == 0) {
+    const int mine = items > (int)blockIdx.x ? (items - 1 - (int)blockIdx.x) / gridDim.x + 1 : 0;
+    dev_timer_block_end(timer, t0, mine * item_flops, mine * item_bytes);
   }
 }
 
@@ -686,6 +820,75 @@ cudaError_t launch_slab(const SphereDev<R>& s, const SlabArgs<R>& a, cudaStream_
     }
   } else if (s.N2 == 64 && s.N3 == 192) {
     return slab_impl<R, 64, 192>(s, a, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// planes per group of the fused kernel: the fewest planes whose thread
+// group (a power of two, at least a warp) covers every y-line slot at once
+static int fused_planes(int nslot, int tl) {
+  int vt = 32;
+  while (vt < nslot * tl && vt < FUSED_THREADS) vt *= 2;
+  return FUSED_THREADS / vt;
+}
+
+size_t hpsi_fused_smem(const SphereDev<float>& s) {
+  if (s.N1 != s.N2 || s.N2 != s.N3) return 0;
+  int tl = 0;
+  switch (s.N1) {
+    case 24: tl = Tpl<float, 24>::v; break;
+    case 32: tl = Tpl<float, 32>::v; break;
+    case 40: tl = Tpl<float, 40>::v; break;
+    case 48: tl = Tpl<float, 48>::v; break;
+    default: return 0;
+  }
+  const int nslot = 2 * s.R3 + 1;
+  const int G = fused_planes(nslot, tl);
+  const size_t bytes = ((size_t)s.N1 * s.n_col + (size_t)G * nslot * (s.N2 + 8)) * sizeof(cpx<float>);
+  return bytes <= 225 * 1024 ? bytes : 0;
+}
+
+template <int N>
+static cudaError_t hpsi_fused_impl(const SphereDev<float>& s, const float* x, long long ldx,
+                                   ItemMap map, int n_items, const float* v,
+                                   const Epilogue<float>& ep, size_t smem, cudaStream_t st) {
+  auto kern = k_hpsi_fused<N>;
+  static std::atomic<bool> attr_set{false};
+  if (!attr_set.load()) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         225 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_set.store(true);
+  }
+  const int G = fused_planes(2 * s.R3 + 1, Tpl<float, N>::v);
+  const unsigned grid = (unsigned)std::min<long long>(
+      n_items, (long long)occupancy(kern, FUSED_THREADS, smem) * sm_count());
+  // algorithmic work: as the three launches it replaces (x-lines both ways,
+  // y- and z-lines both ways, V products); bytes: the vectors only
+  const double planes = (double)n_items * s.N1;
+  const double fl = (double)n_items * 2.0 * s.n_col * 5.0 * N * log2((double)N) +
+                    planes * (2.0 * (2 * s.R3 + 1) * 5.0 * N * log2((double)N) +
+                              2.0 * N * 5.0 * N * log2((double)N) + 2.0 * N * N);
+  const double by = (double)n_items * 2.0 * s.n_pw * sizeof(float) * 3.0;
+  // timed on the device (this kernel also runs inside the CG graphs): the
+  // work is counted per processed item
+  count_launch();
+  kern<<<grid, FUSED_THREADS, smem, st>>>(s, x, ldx, map, n_items, v, ep, G,
+                                          dev_timer(PC_HPSI_FUSED), fl / n_items, by / n_items);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hpsi_fused(const SphereDev<float>& s, const float* x, long long ldx, ItemMap map,
+                              int n_items, const float* v, const Epilogue<float>& ep,
+                              cudaStream_t st) {
+  const size_t smem = hpsi_fused_smem(s);
+  if (smem == 0) return cudaErrorInvalidValue;
+  if (n_items <= 0) return cudaSuccess;
+  switch (s.N1) {
+    case 24: return hpsi_fused_impl<24>(s, x, ldx, map, n_items, v, ep, smem, st);
+    case 32: return hpsi_fused_impl<32>(s, x, ldx, map, n_items, v, ep, smem, st);
+    case 40: return hpsi_fused_impl<40>(s, x, ldx, map, n_items, v, ep, smem, st);
+    case 48: return hpsi_fused_impl<48>(s, x, ldx, map, n_items, v, ep, smem, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -173,6 +173,15 @@ template <typename R>
 cudaError_t launch_cols_bwd(const SphereDev<R>& s, const cpx<R>* b1, ItemMap map, int n_items,
                             const Epilogue<R>& ep, cudaStream_t st);
 
+// H x in FP32 by one fused launch (column scratch in shared memory) for the
+// cubic grids 24^3 .. 48^3: the same result as cols_fwd + slab (HPSI) +
+// cols_bwd with that epilogue.  hpsi_fused_smem returns its shared memory
+// per block, 0 where the fused form does not apply.
+size_t hpsi_fused_smem(const SphereDev<float>& s);
+cudaError_t launch_hpsi_fused(const SphereDev<float>& s, const float* x, long long ldx, ItemMap map,
+                              int n_items, const float* v, const Epilogue<float>& ep,
+                              cudaStream_t st);
+
 bool grid_supported(int N1, int N2, int N3);
 cudaError_t upload_local_twiddles();
 size_t slab_smem_bytes(int n_col, int R3, int N2, size_t elem);

@@ -184,3 +184,19 @@ def test_double_float_refinement_matches_fp64_refinement(tiny):
             out[df_refine] = (w, dpsi)
     assert rel(out[1][0], out[0][0]) < 1e-8
     assert rel(out[1][1], out[0][1]) < 1e-8
+
+
+def test_fused_transform_matches_three_launch_form(tiny):
+    """The inner CG with the fused FP32 H x (one launch, column scratch in
+    shared memory) reaches the same FP64-refined solutions as the three-launch
+    transforms."""
+    pg = _pg()
+    n = 32
+    out = {}
+    for fused in (0, 1):
+        with pg.Context(tiny, precision=pg.PDEP_MIXED, fused_hpsi=fused) as ctx:
+            dim = ctx.sizes()["n_pdep_dim"]
+            phi = _phi(n, dim, seed=79)
+            out[fused] = ctx.chi0_apply(phi)
+            assert ctx.stats()["max_cg_residual"] <= 1e-10
+    assert rel(out[1], out[0]) < 1e-8

@@ -56,7 +56,8 @@ def test_iteration_cap_reports_not_converged():
             ctx.sternheimer_solve(dv)
         assert e.value.status == 5
         dpsi, its, res = ctx.sternheimer_solve(dv, allow_unconverged=True)
-        assert its.max() <= 3 and res.max() > 1e-10
+        # the cap holds for each refinement round
+        assert its.max() <= 3 * ctx.options.max_refine and res.max() > 1e-10
 
 
 def test_workspace_limit():

@@ -53,6 +53,13 @@ def test_to_grid_and_hpsi(grid, cell):
         # single vector (odd item) and a per-vector check
         one = ctx.apply_hamiltonian(x[1:2].copy())
         assert rel(one[0], ref[1]) < 1e-14
+    # FP32: the fused one-launch transform (cubic 24^3 .. 48^3) and the
+    # three-launch form agree to FP32 rounding
+    with pg.Context(s, fused_hpsi=0) as ctx:
+        y3 = ctx.apply_hamiltonian(x, precision=pg.PDEP_MIXED)
+    with pg.Context(s) as ctx:
+        y1 = ctx.apply_hamiltonian(x, precision=pg.PDEP_MIXED)
+    assert rel(y1, ref) < 2e-7 and rel(y3, ref) < 2e-7 and rel(y1, y3) < 2e-7
 
 
 @pytest.mark.parametrize("grid,cell", SHAPES[:4])
