@@ -428,6 +428,11 @@ def run_ours(args):
                        "cg_step_variant_autotuned": stats["cg_variant"],
                        "projection_kernel_autotuned": {0: "cuda-core fp32", 1: "tensor-core 3xtf32"}
                        .get(stats["proj_variant"], "untuned"),
+                       "fused_transform_planes_autotuned": stats["fused_planes"],
+                       "projection_gemm_tile_autotuned": {0: "64 rows", 1: "80 rows",
+                                                          2: "80 rows, half split-K",
+                                                          3: "80 rows, twice split-K"}
+                       .get(stats["gemm_shape"], "untuned"),
                        "n_deflate": int(ctx_deflate)},
             "eigenpairs_per_s": round(eigpairs, 4),
             "fp64": fp64,

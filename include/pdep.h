@@ -98,9 +98,9 @@ typedef enum {
                           accuracy, FP32 accumulation); FP64 residual
                           refinement, density response, orthogonalisation and
                           Rayleigh-Ritz */
-  PDEP_MIXED_BF16 = 2  /* as PDEP_MIXED_TF32 with the projection term from BF16
-                          operands (each FP32 value split in three BF16 parts,
-                          FP32 accumulation) */
+  PDEP_MIXED_BF16 = 2  /* reserved for the projection term from BF16 operands;
+                          this build has no such kernel: pdep_setup returns
+                          PDEP_ERR_UNSUPPORTED */
 } pdep_precision;
 #define PDEP_MIXED PDEP_MIXED_TF32 /* the default mixed mode */
 
@@ -184,6 +184,11 @@ typedef struct {
   long long kernel_launches;    /* library kernels the call ran, those inside CUDA graphs
                                    included (graph steps counted on the device) */
   long long graph_launches;     /* CG-loop graphs launched */
+  int fused_planes;             /* x-planes per group of the fused FP32 transform the
+                                   autotuner chose (-1: untuned or not used) */
+  int gemm_shape;               /* tile shape of the FP64 / double-float projection GEMMs the
+                                   autotuner chose: 0 64-row tiles, 1 80-row, 2 80-row with
+                                   half the default split-K, 3 80-row with twice (-1 untuned) */
 } pdep_stats;
 
 /* Fill *opt with the defaults (FP64, cg_tol 1e-10, dav_tol 1e-8, ...). */

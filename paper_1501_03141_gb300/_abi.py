@@ -102,6 +102,8 @@ class pdep_stats(ctypes.Structure):
         ("chi0_chunks", ctypes.c_int),
         ("kernel_launches", ctypes.c_longlong),
         ("graph_launches", ctypes.c_longlong),
+        ("fused_planes", ctypes.c_int),
+        ("gemm_shape", ctypes.c_int),
     ]
 
 

@@ -111,10 +111,18 @@ struct DevBuf {
   size_t cap = 0;
 };
 
+// One autotuned choice: every candidate computes the same result, so each is
+// timed on real calls (two calls each, alternating), its time per unit of
+// work kept, and the fastest is used from then on.
+struct Tune {
+  int next = 0, calls = 0, best = -1;
+  double ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+};
+
 // One captured Sternheimer CG loop (prologue + while node over the steps),
 // valid for the buffers and settings it was captured with.
 struct CgGraph {
-  int prec, sys, n, max_iter, cg_variant, proj_variant;
+  int prec, sys, n, max_iter, cg_variant, proj_variant, tune_gen;
   double tol;
   const void *b, *x, *sc, *mask, *tolv;
   unsigned long long ws_gen, budget_ns;
@@ -161,6 +169,10 @@ struct pdep_ctx {
   int cg_tune_next[2] = {0, 0};
   // executable graphs of the Jacobi sweeps, released in pdep_destroy
   EighGraphCache eig_graphs;
+  // autotuner over the FFT batch (planes per group of the fused transform)
+  // and the GEMM tile shapes, keyed by kernel and problem shape
+  std::map<std::string, Tune> tunes;
+  int tune_gen = 0;  // bumped whenever a choice is made (graphs keyed by it)
 };
 
 namespace {
@@ -441,6 +453,56 @@ size_t b1_count(const SysData& s, int n_items) {
 // dn (FP64 only, may be null): the transform also accumulates the density
 // response dn_j(r) += (4/Omega) u_v(r) x_i(r) of every vector i = j n_occ + v
 // it transforms (Eq. deltani); dn must hold the (i / n_occ) perturbations.
+bool capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return cs != cudaStreamCaptureStatusNone;
+}
+
+// Runs fn(candidate): the tuned choice once made, the default while
+// autotuning is off or the call is too small (units < 256) or captured, else
+// the next candidate, timed with events on st (this synchronises: only the
+// first 2 x n_cand large calls of a shape do).
+template <typename F>
+int tuned_call(pdep_ctx* c, const std::string& key, int n_cand, int def, double units,
+               cudaStream_t st, F fn) {
+  auto it = c->tunes.find(key);
+  if (it != c->tunes.end() && it->second.best >= 0) return fn(it->second.best);
+  if (!c->opt.autotune || units < 256 || n_cand < 2 || capturing(st)) return fn(def);
+  Tune& t = c->tunes[key];
+  const int cand = t.next;
+  CK(cudaEventRecord(c->ev[0], st));
+  RET(fn(cand));
+  CK(cudaEventRecord(c->ev[1], st));
+  CK(cudaEventSynchronize(c->ev[1]));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+  t.ms[cand] += ms / units;
+  t.next = (t.next + 1) % n_cand;
+  if (++t.calls == 2 * n_cand) {
+    int best = 0;
+    for (int k = 1; k < n_cand; ++k)
+      if (t.ms[k] < t.ms[best]) best = k;
+    t.best = best;
+    ++c->tune_gen;
+  }
+  return PDEP_OK;
+}
+bool tune_done(const pdep_ctx* c, const std::string& key) {
+  auto it = c->tunes.find(key);
+  return it != c->tunes.end() && it->second.best >= 0;
+}
+
+// GEMM tile candidates of the projection GEMMs: tile height 64 or 80 rows,
+// split-K at the default, half or twice the default
+const GemmShape kGemmShapes[4] = {{4, 8}, {5, 8}, {5, 4}, {5, 16}};
+std::string shape_key(const char* what, const SysData& s) {
+  return std::string(what) + ":" + std::to_string(s.n_ext) + ":" + std::to_string(s.n_pw);
+}
+
 // d_count (with d_list): device length of the list; n_list is then the
 // largest length, which sizes the launches (kernels read the count).
 // C is the arithmetic type of the transforms (float, double, or df: double-
@@ -474,7 +536,16 @@ int apply_h(pdep_ctx* c, SysData& s, const R* X, R* Y, int n, const int* d_list,
       ep.kin = 1.0f;
       ep.beta = 0.0f;
       ep.coef = COEF_ONE;
-      CK(launch_hpsi_fused(s.sf, X, s.ld, map, n_items, s.d_vf, ep, st));
+      // FFT batch: x-planes per group of the fused transform (half, the
+      // default, or twice the default when shared memory allows)
+      const int G0 = hpsi_fused_planes(s.sf);
+      const int cands[3] = {G0, G0 / 2 > 0 ? G0 / 2 : G0,
+                            hpsi_fused_smem(s.sf, 2 * G0) ? 2 * G0 : G0};
+      RET(tuned_call(c, "fused_planes:" + std::to_string(s.N[0]), 3, 0, 2.0 * n_items, st,
+                     [&](int k) -> int {
+                       CK(launch_hpsi_fused(s.sf, X, s.ld, map, n_items, s.d_vf, ep, st, cands[k]));
+                       return PDEP_OK;
+                     }));
       fused = true;
     }
   }
@@ -559,11 +630,17 @@ int apply_h(pdep_ctx* c, SysData& s, const R* X, R* Y, int n, const int* d_list,
     using G = typename std::conditional<std::is_same<C, df>::value, df, R>::type;
     RET(ws(c, sizeof(R) == 8 ? "pv_64" : "pv_32", (size_t)s.n_ext * std::max(m, 1), &S));
     const R* P = psi_of(s, (R*)nullptr);
-    CK(gemm<G>(true, s.n_ext, m, s.n_pw, 1.0, P, s.ld, X, s.ld, 0.0, S, s.n_ext, st, d_list,
-               nullptr, d_count));
-    CK(scale_rows<R>(S, s.n_ext, s.n_ext, m, sigma_of(s, (R*)nullptr), st));
-    CK(gemm<G>(false, s.n_pw, m, s.n_ext, 1.0, P, s.ld, S, s.n_ext, 1.0, Y, s.ld, st, nullptr,
-               d_list, d_count));
+    // tile shapes of the pair, autotuned per problem shape
+    RET(tuned_call(c, shape_key(std::is_same<G, df>::value ? "pv_df" : "pv_64", s), 4, 1, m, st,
+                   [&](int k) -> int {
+                     const GemmShape sh = kGemmShapes[k];
+                     CK(gemm<G>(true, s.n_ext, m, s.n_pw, 1.0, P, s.ld, X, s.ld, 0.0, S,
+                                s.n_ext, st, d_list, nullptr, d_count, sh));
+                     CK(scale_rows<R>(S, s.n_ext, s.n_ext, m, sigma_of(s, (R*)nullptr), st));
+                     CK(gemm<G>(false, s.n_pw, m, s.n_ext, 1.0, P, s.ld, S, s.n_ext, 1.0, Y, s.ld,
+                                st, nullptr, d_list, d_count, sh));
+                     return PDEP_OK;
+                   }));
   }
   return PDEP_OK;
 }
@@ -576,8 +653,15 @@ template <typename G>
 int split_rhs_t(pdep_ctx* c, SysData& s, double* B, int n, double* Xd, cudaStream_t st) {
   double* S;
   RET(ws(c, "pc_64", (size_t)s.n_ext * n, &S));
-  CK(gemm<G>(true, s.n_ext, n, s.n_pw, 1.0, s.d_psi, s.ld, B, s.ld, 0.0, S, s.n_ext, st));
-  CK(gemm<G>(false, s.n_pw, n, s.n_ext, -1.0, s.d_psi, s.ld, S, s.n_ext, 1.0, B, s.ld, st));
+  RET(tuned_call(c, shape_key(std::is_same<G, df>::value ? "split_df" : "split_64", s), 4, 1, n, st,
+                 [&](int k) -> int {
+                   const GemmShape sh = kGemmShapes[k];
+                   CK(gemm<G>(true, s.n_ext, n, s.n_pw, 1.0, s.d_psi, s.ld, B, s.ld, 0.0, S,
+                              s.n_ext, st, nullptr, nullptr, nullptr, sh));
+                   CK(gemm<G>(false, s.n_pw, n, s.n_ext, -1.0, s.d_psi, s.ld, S, s.n_ext, 1.0, B,
+                              s.ld, st, nullptr, nullptr, nullptr, sh));
+                   return PDEP_OK;
+                 }));
   if (s.n_defl > 0) {
     CK(deflation_coefficients(S, s.n_ext, s.n_occ, s.n_defl, n, s.d_eps_ext, st));
     CK(gemm<G>(false, s.n_pw, n, s.n_defl, 1.0, s.d_psi + (size_t)s.n_occ * s.ld, s.ld,
@@ -989,10 +1073,12 @@ int setup_states(pdep_ctx* c, SysData& s, cudaStream_t st) {
 // The CG step's launch shape and the FP32 projection kernel are fixed once
 // the autotuner has timed them (or autotuning is off); only then is the loop
 // captured in a graph.
-bool tuned(const pdep_ctx* c, int pi) {
+bool tuned(const pdep_ctx* c, const SysData& s, int pi) {
   if (!c->opt.autotune) return true;
   const bool pv_ok = pi == 1 || c->opt.proj_variant >= 0 || c->proj_variant >= 0;
-  return c->cg_variant[pi] >= 0 && pv_ok;
+  const bool fused_ok = pi == 1 || !c->opt.fused_hpsi || hpsi_fused_smem(s.sf) == 0 ||
+                        tune_done(c, "fused_planes:" + std::to_string(s.N[0]));
+  return c->cg_variant[pi] >= 0 && pv_ok && fused_ok;
 }
 int cg_variant_of(const pdep_ctx* c, int pi) {
   return c->cg_variant[pi] >= 0 ? c->cg_variant[pi] : (int)CG_STREAM256;
@@ -1136,7 +1222,7 @@ int cg_loop(pdep_ctx* c, SysData& s, const R* b, R* x, int n, double tol, int ma
   a.tolv = tolv;
   // loops under 256 RHS are never timed by the autotuner: they run the
   // current (or default) shapes and are captured right away
-  const bool graph = c->opt.use_graph && (tuned(c, pi) || n < 256);
+  const bool graph = c->opt.use_graph && (tuned(c, s, pi) || n < 256);
   if (!graph) {
     // eager: host loop, one 8-byte read of the loop state per step
     CK(cudaMemsetAsync(&c->d_loop->active, 0, sizeof(int), st));
@@ -1187,7 +1273,8 @@ int cg_loop(pdep_ctx* c, SysData& s, const R* b, R* x, int n, double tol, int ma
     if (e.prec == pi && e.sys == si && e.n == n && e.max_iter == max_iter && e.tol == tol &&
         e.b == b && e.x == x && e.sc == sc && e.mask == mask && e.tolv == tolv &&
         e.ws_gen == c->ws_gen &&
-        e.cg_variant == a.variant && e.proj_variant == pv && e.budget_ns == c->budget_ns) {
+        e.cg_variant == a.variant && e.proj_variant == pv && e.budget_ns == c->budget_ns &&
+        e.tune_gen == c->tune_gen) {
       g = &e;
       break;
     }
@@ -1207,6 +1294,7 @@ int cg_loop(pdep_ctx* c, SysData& s, const R* b, R* x, int n, double tol, int ma
     e.cg_variant = a.variant;
     e.proj_variant = pv;
     e.budget_ns = c->budget_ns;
+    e.tune_gen = c->tune_gen;
     RET(capture_cg_graph<R>(c, s, a, b, n, max_iter, list, &e.exec));
     if (c->cg_graphs.size() >= 16) {
       cudaGraphExecDestroy(c->cg_graphs.front().exec);
@@ -1489,6 +1577,17 @@ int read_stats(pdep_ctx* c, pdep_stats* out, cudaStream_t st) {
     in_graphs += ((long long)steps[pi] - c->eager_steps[pi]) * c->body_launches[pi];
   out->kernel_launches = (launch_count() - c->st_launch0) + in_graphs;
   out->graph_launches = c->graph_launches;
+  out->fused_planes = -1;
+  out->gemm_shape = -1;
+  for (const auto& kv : c->tunes) {
+    if (kv.second.best < 0) continue;
+    if (kv.first.rfind("fused_planes:", 0) == 0 && !c->sys.empty()) {
+      const int G0 = hpsi_fused_planes(c->sys[0].sf);
+      const int k = kv.second.best;
+      out->fused_planes = k == 0 ? G0 : k == 1 ? std::max(1, G0 / 2) : 2 * G0;
+    }
+    if (kv.first.rfind("pv_", 0) == 0) out->gemm_shape = kv.second.best;
+  }
   return PDEP_OK;
 }
 
@@ -1695,6 +1794,8 @@ int pdep_setup(const pdep_system_desc* sys, int n_sys, const pdep_options* opt, 
   if (c->opt.precision != PDEP_FP64 && c->opt.precision != PDEP_MIXED_TF32 &&
       c->opt.precision != PDEP_MIXED_BF16)
     return bail(fail(PDEP_ERR_INVALID_ARG, "unknown precision mode"));
+  if (c->opt.precision == PDEP_MIXED_BF16)
+    return bail(fail(PDEP_ERR_UNSUPPORTED, "PDEP_MIXED_BF16: no BF16 projection kernel in this build"));
   if (c->opt.clock_budget_cycles < 0) return bail(fail(PDEP_ERR_INVALID_ARG, "negative clock budget"));
   if (cudaMalloc(&c->d_status, sizeof(unsigned)) != cudaSuccess ||
       cudaMalloc(&c->d_counter, 4 * sizeof(int)) != cudaSuccess ||

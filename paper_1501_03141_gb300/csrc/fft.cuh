@@ -211,7 +211,7 @@ __device__ __forceinline__ void fft_a2b(cpx<R> (&v)[N / TPL], int t, const cpx<R
   DFT<R, M, S>::run(v);
   if constexpr (TPL > 1) {
 #pragma unroll
-    for (int k2 = 1; k2 < M; ++k2) v[k2] = v[k2] * table_w<R, S>(tw, (t * k2) % N);
+    for (int k2 = 1; k2 < M; ++k2) v[k2] = v[k2] * table_w<R, S>(tw, t * k2);  // t k2 < TPL M = N
 #pragma unroll
     for (int half = TPL / 2; half >= 1; half >>= 1) {
       const int L = 2 * half;
@@ -269,7 +269,7 @@ __device__ __forceinline__ void fft_b2a(cpx<R> (&v)[N / TPL], int t, const cpx<R
       }
     }
 #pragma unroll
-    for (int k2 = 1; k2 < M; ++k2) v[k2] = v[k2] * table_w<R, S>(tw, (t * k2) % N);
+    for (int k2 = 1; k2 < M; ++k2) v[k2] = v[k2] * table_w<R, S>(tw, t * k2);  // t k2 < TPL M = N
   }
   DFT<R, M, S>::run(v);
 }

@@ -188,11 +188,11 @@ template <typename R>
 cudaError_t gemm(bool transA, int m, int n, int k, double alpha, const typename Io<R>::T* A,
                  long long lda, const typename Io<R>::T* B, long long ldb, double beta,
                  typename Io<R>::T* C, long long ldc, cudaStream_t st, const int* bmap,
-                 const int* cmap, const int* ndev) {
+                 const int* cmap, const int* ndev, GemmShape shape) {
   using T = typename Io<R>::T;
   if (m <= 0 || n <= 0) return cudaSuccess;
-  // 80-row tiles when they pad m less than 64-row tiles do
-  const bool t80 = ((m + 79) / 80) * 80 < ((m + 63) / 64) * 64;
+  // 80-row tiles when they pad m less than 64-row tiles do (or as tuned)
+  const bool t80 = shape.tm ? shape.tm == 5 : ((m + 79) / 80) * 80 < ((m + 63) / 64) * 64;
   const int bm = t80 ? 80 : 64;
   const int tm = (m + bm - 1) / bm, tn = (n + 63) / 64;
   int splits = 1;
@@ -202,6 +202,8 @@ cudaError_t gemm(bool transA, int m, int n, int k, double alpha, const typename 
     splits = std::min(splits, (k + 255) / 256);
     splits = std::max(splits, 1);
   }
+  if (shape.split_x8 > 0 && k > 256)
+    splits = std::max(1, std::min((k + 127) / 128, (splits * shape.split_x8 + 7) / 8));
   int kchunk = (k + splits - 1) / splits;
   kchunk = ((kchunk + 15) / 16) * 16;
   if (kchunk == 0) kchunk = 16;
@@ -244,13 +246,13 @@ cudaError_t gemm(bool transA, int m, int n, int k, double alpha, const typename 
 
 template cudaError_t gemm<double>(bool, int, int, int, double, const double*, long long,
                                   const double*, long long, double, double*, long long,
-                                  cudaStream_t, const int*, const int*, const int*);
+                                  cudaStream_t, const int*, const int*, const int*, GemmShape);
 template cudaError_t gemm<df>(bool, int, int, int, double, const double*, long long,
                               const double*, long long, double, double*, long long, cudaStream_t,
-                              const int*, const int*, const int*);
+                              const int*, const int*, const int*, GemmShape);
 template cudaError_t gemm<float>(bool, int, int, int, double, const float*, long long,
                                  const float*, long long, double, float*, long long, cudaStream_t,
-                                 const int*, const int*, const int*);
+                                 const int*, const int*, const int*, GemmShape);
 
 // ---------------------------------------------------------------------------
 // one-sided Jacobi eigensolver

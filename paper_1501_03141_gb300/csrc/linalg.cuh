@@ -18,11 +18,18 @@ namespace pdep {
 // sized for n and columns from *ndev on are left untouched.  R is the
 // arithmetic type: float, double, or df (double-float arithmetic on the FP32
 // pipe; the matrices are FP64).
+// shape (optional): tile height (tm 4: 64 rows, 5: 80 rows; 0 = the one that
+// pads m less) and split-K multiplier of the default split (split_x8 / 8,
+// 0 = default); the autotuner picks it per GEMM shape.
+struct GemmShape {
+  int tm = 0;
+  int split_x8 = 0;
+};
 template <typename R>
 cudaError_t gemm(bool transA, int m, int n, int k, double alpha, const typename Io<R>::T* A,
                  long long lda, const typename Io<R>::T* B, long long ldb, double beta,
                  typename Io<R>::T* C, long long ldc, cudaStream_t st, const int* bmap = nullptr,
-                 const int* cmap = nullptr, const int* ndev = nullptr);
+                 const int* cmap = nullptr, const int* ndev = nullptr, GemmShape shape = {});
 
 // Symmetric eigendecomposition of the n x n matrix M (lda), FP64:
 // one-sided (Hestenes) Jacobi on M - sigma I (sigma = twice the Gershgorin

@@ -597,6 +597,15 @@ __device__ __forceinline__ void z_hpsi(const SphereDev<float>& s, cpx<float>* T2
   }
 }
 
+// barrier of the warps of plane group g (nthreads of them, warp-aligned)
+__device__ __forceinline__ void group_sync(int g, int nthreads) {
+  if (nthreads == 32) {
+    __syncwarp();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(nthreads) : "memory");
+  }
+}
+
 template <int N>
 __global__ void __launch_bounds__(FUSED_THREADS, 1)
     k_hpsi_fused(SphereDev<float> s, const float* __restrict__ x, long long ldx, ItemMap map,
@@ -624,18 +633,23 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
       xline_inverse<float, N>(s, x, ldx, map, nl, COEF_ONE, item, uc, uc < s.n_ucol, B1);
     }
     __syncthreads();
+    // the plane groups touch disjoint data (their own plane row of B1 and
+    // their own T2), so each synchronises only its own warps: one warp with
+    // __syncwarp, several with a named barrier (ids 1..G)
 #pragma unroll 1
     for (int p0 = 0; p0 < N; p0 += G) {
       const int i1 = p0 + g;
-      const bool plane = i1 < N;  // uniform over the plane's warps
-      cpx<float>* S1 = B1 + (size_t)(plane ? i1 : 0) * s.n_col;
-      if (plane) y_inverse<float, N>(s, S1, T2, vt, VT);
-      __syncthreads();
-      if (plane) z_hpsi<N>(s, T2, v + (size_t)i1 * N * N, vt, VT);
-      __syncthreads();
-      if (plane) y_forward<float, N>(s, T2, S1, vt, VT);
-      __syncthreads();
+      if (i1 < N) {  // uniform over the plane group's warps
+        cpx<float>* S1 = B1 + (size_t)i1 * s.n_col;
+        y_inverse<float, N>(s, S1, T2, vt, VT);
+        group_sync(g, VT);
+        z_hpsi<N>(s, T2, v + (size_t)i1 * N * N, vt, VT);
+        group_sync(g, VT);
+        y_forward<float, N>(s, T2, S1, vt, VT);
+        group_sync(g, VT);
+      }
     }
+    __syncthreads();
 #pragma unroll 1
     for (int base = 0; base < s.n_ucol; base += lines) {
       const int uc = base + threadIdx.x / TL;
@@ -832,18 +846,32 @@ static int fused_planes(int nslot, int tl) {
   return FUSED_THREADS / vt;
 }
 
-size_t hpsi_fused_smem(const SphereDev<float>& s) {
-  if (s.N1 != s.N2 || s.N2 != s.N3) return 0;
-  int tl = 0;
-  switch (s.N1) {
-    case 24: tl = Tpl<float, 24>::v; break;
-    case 32: tl = Tpl<float, 32>::v; break;
-    case 40: tl = Tpl<float, 40>::v; break;
-    case 48: tl = Tpl<float, 48>::v; break;
-    default: return 0;
+static int fused_tl(int N) {
+  switch (N) {
+    case 24: return Tpl<float, 24>::v;
+    case 32: return Tpl<float, 32>::v;
+    case 40: return Tpl<float, 40>::v;
+    case 48: return Tpl<float, 48>::v;
   }
+  return 0;
+}
+
+int hpsi_fused_planes(const SphereDev<float>& s, int planes) {
+  const int tl = fused_tl(s.N1);
+  if (!tl) return 0;
   const int nslot = 2 * s.R3 + 1;
-  const int G = fused_planes(nslot, tl);
+  const int G0 = fused_planes(nslot, tl);
+  // a requested group must be a power of two whose thread groups (512/G
+  // threads) are at least a warp; fewer threads than a plane's y-lines take
+  // two rounds per pass
+  if (planes > 0 && FUSED_THREADS / planes >= 32 && (planes & (planes - 1)) == 0) return planes;
+  return G0;  // at most 16 groups: 16 single-warp groups, or <= 8 with named barriers 1..8
+}
+
+size_t hpsi_fused_smem(const SphereDev<float>& s, int planes) {
+  if (s.N1 != s.N2 || s.N2 != s.N3 || !fused_tl(s.N1)) return 0;
+  const int nslot = 2 * s.R3 + 1;
+  const int G = hpsi_fused_planes(s, planes);
   const size_t bytes = ((size_t)s.N1 * s.n_col + (size_t)G * nslot * (s.N2 + 8)) * sizeof(cpx<float>);
   return bytes <= 225 * 1024 ? bytes : 0;
 }
@@ -851,7 +879,8 @@ size_t hpsi_fused_smem(const SphereDev<float>& s) {
 template <int N>
 static cudaError_t hpsi_fused_impl(const SphereDev<float>& s, const float* x, long long ldx,
                                    ItemMap map, int n_items, const float* v,
-                                   const Epilogue<float>& ep, size_t smem, cudaStream_t st) {
+                                   const Epilogue<float>& ep, size_t smem, int G,
+                                   cudaStream_t st) {
   auto kern = k_hpsi_fused<N>;
   static std::atomic<bool> attr_set{false};
   if (!attr_set.load()) {
@@ -860,7 +889,6 @@ static cudaError_t hpsi_fused_impl(const SphereDev<float>& s, const float* x, lo
     if (e != cudaSuccess) return e;
     attr_set.store(true);
   }
-  const int G = fused_planes(2 * s.R3 + 1, Tpl<float, N>::v);
   const unsigned grid = (unsigned)std::min<long long>(
       n_items, (long long)occupancy(kern, FUSED_THREADS, smem) * sm_count());
   // algorithmic work: as the three launches it replaces (x-lines both ways,
@@ -880,15 +908,16 @@ static cudaError_t hpsi_fused_impl(const SphereDev<float>& s, const float* x, lo
 
 cudaError_t launch_hpsi_fused(const SphereDev<float>& s, const float* x, long long ldx, ItemMap map,
                               int n_items, const float* v, const Epilogue<float>& ep,
-                              cudaStream_t st) {
-  const size_t smem = hpsi_fused_smem(s);
+                              cudaStream_t st, int planes) {
+  const size_t smem = hpsi_fused_smem(s, planes);
   if (smem == 0) return cudaErrorInvalidValue;
   if (n_items <= 0) return cudaSuccess;
+  const int G = hpsi_fused_planes(s, planes);
   switch (s.N1) {
-    case 24: return hpsi_fused_impl<24>(s, x, ldx, map, n_items, v, ep, smem, st);
-    case 32: return hpsi_fused_impl<32>(s, x, ldx, map, n_items, v, ep, smem, st);
-    case 40: return hpsi_fused_impl<40>(s, x, ldx, map, n_items, v, ep, smem, st);
-    case 48: return hpsi_fused_impl<48>(s, x, ldx, map, n_items, v, ep, smem, st);
+    case 24: return hpsi_fused_impl<24>(s, x, ldx, map, n_items, v, ep, smem, G, st);
+    case 32: return hpsi_fused_impl<32>(s, x, ldx, map, n_items, v, ep, smem, G, st);
+    case 40: return hpsi_fused_impl<40>(s, x, ldx, map, n_items, v, ep, smem, G, st);
+    case 48: return hpsi_fused_impl<48>(s, x, ldx, map, n_items, v, ep, smem, G, st);
   }
   return cudaErrorInvalidValue;
 }

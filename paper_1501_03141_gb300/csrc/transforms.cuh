@@ -177,10 +177,14 @@ cudaError_t launch_cols_bwd(const SphereDev<R>& s, const cpx<R>* b1, ItemMap map
 // cubic grids 24^3 .. 48^3: the same result as cols_fwd + slab (HPSI) +
 // cols_bwd with that epilogue.  hpsi_fused_smem returns its shared memory
 // per block, 0 where the fused form does not apply.
-size_t hpsi_fused_smem(const SphereDev<float>& s);
+// planes (0 = default) sets the x-planes transformed at once by a block (the
+// autotuner's FFT batch; a power of two from 1 to 16 whose thread groups
+// still cover a plane's y-lines, else the default is used).
+size_t hpsi_fused_smem(const SphereDev<float>& s, int planes = 0);
+int hpsi_fused_planes(const SphereDev<float>& s, int planes = 0);
 cudaError_t launch_hpsi_fused(const SphereDev<float>& s, const float* x, long long ldx, ItemMap map,
                               int n_items, const float* v, const Epilogue<float>& ep,
-                              cudaStream_t st);
+                              cudaStream_t st, int planes = 0);
 
 bool grid_supported(int N1, int N2, int N3);
 cudaError_t upload_local_twiddles();
