@@ -426,7 +426,8 @@ def run_ours(args):
                        "refine_rounds_max": stats["refine_rounds_max"],
                        "max_cg_residual": stats["max_cg_residual"],
                        "cg_step_variant_autotuned": stats["cg_variant"],
-                       "projection_kernel_autotuned": {0: "cuda-core fp32", 1: "tensor-core 3xtf32"}
+                       "projection_kernel_autotuned": {0: "cuda-core fp32", 1: "mma.sync 3xtf32",
+                                                       2: "tcgen05 3xtf32 coefficients"}
                        .get(stats["proj_variant"], "untuned"),
                        "fused_transform_planes_autotuned": stats["fused_planes"],
                        "projection_gemm_tile_autotuned": {0: "64 rows", 1: "80 rows",
@@ -697,8 +698,9 @@ def main(argv=None):
                     help="diagnostics: CG loops from a host loop instead of CUDA graphs, so that "
                          "the per-kernel profile sees every CG kernel")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--proj", type=int, default=1, choices=[0, 1],
-                    help="small cases: FP32 projection kernel (0 CUDA cores, 1 tensor cores)")
+    ap.add_argument("--proj", type=int, default=2, choices=[0, 1, 2],
+                    help="small cases: FP32 projection kernel (0 CUDA cores, 1 mma.sync "
+                         "tensor cores, 2 tcgen05 coefficients)")
     ap.add_argument("--case", choices=["bench", "small", "small64", "batch", "interface"],
                     default="bench",
                     help="small/small64: one chi0bar application of 16 perturbations "

@@ -142,8 +142,12 @@ typedef struct {
                                 eps_{n_occ+n_deflate+1} - eps_v instead of the gap. */
   int proj_variant;          /* kernel of the FP32 (mixed-mode CG) projection term
                                 sum_w sigma_w |w><w| x: -1 = autotuned (default; the
-                                first large calls time both), 0 = FP32 CUDA-core GEMMs,
-                                1 = tensor-core GEMMs of the precision mode. */
+                                first large calls time all three), 0 = FP32 CUDA-core
+                                GEMMs, 1 = 3xTF32 tensor-core GEMMs on mma.sync,
+                                2 = the coefficient GEMM 3xTF32 on tcgen05 with
+                                tensor-memory accumulators (its waits on the tensor
+                                cores are bounded: one that runs out sets
+                                PDEP_ERR_TIMEOUT), the update as in 1. */
   long long clock_budget_cycles; /* device time budget of every CG loop, in SM clock
                                 cycles at the device's rated clock (0 = none).  A loop
                                 whose budget runs out with unconverged RHS stops after
@@ -179,7 +183,7 @@ typedef struct {
   double max_dav_residual;      /* largest final ||chi0bar x - theta x|| / |theta_1| */
   double seconds;               /* wall time of the call */
   int cg_variant;               /* CG-step launch shape the autotuner chose (-1: untuned) */
-  int proj_variant;             /* FP32 projection kernel in use (-1: untuned, 0, 1) */
+  int proj_variant;             /* FP32 projection kernel in use (-1: untuned, 0, 1, 2) */
   int chi0_chunks;              /* perturbation chunks of the last chi0bar application */
   long long kernel_launches;    /* library kernels the call ran, those inside CUDA graphs
                                    included (graph steps counted on the device) */

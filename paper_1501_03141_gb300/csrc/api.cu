@@ -87,6 +87,7 @@ struct SysData {
   df* d_kindf = nullptr;
   double* d_psi = nullptr;   // [n_occ][ld]
   float* d_psif = nullptr;
+  float* d_psit5 = nullptr;  // d_psif as TF32 hi / lo tiles of the tcgen05 coefficients
   double* d_u = nullptr;     // [n_occ][n_r]  u_v(r) = Omega^{1/2} psi_v(r)
   double* d_negeps = nullptr;   // -eps_v
   float* d_negeps32 = nullptr;
@@ -163,7 +164,7 @@ struct pdep_ctx {
   // autotuned FP32 projection kernel (0 CUDA-core, 1 tensor-core; -1 untuned)
   int proj_variant = -1;
   int proj_tune_next = 0;
-  double proj_tune_ms[2] = {0, 0};
+  double proj_tune_ms[3] = {0, 0, 0};
   int proj_tune_calls = 0;
   double cg_tune_ms[2][CG_NUM_VARIANTS] = {};
   int cg_tune_next[2] = {0, 0};
@@ -585,19 +586,25 @@ int apply_h(pdep_ctx* c, SysData& s, const R* X, R* Y, int n, const int* d_list,
     // only the listed columns when a list is given
     const int m = d_list ? n_list : n;
     if constexpr (sizeof(R) == 4) {
-      // FP32: CUDA-core GEMMs (variant 0) or tensor-core 3xTF32 (variant 1).
-      // While untuned, calls with many columns alternate the two and keep
-      // their time per column; afterwards the faster one is used.
+      // FP32: CUDA-core GEMMs (variant 0), 3xTF32 on mma.sync (variant 1),
+      // or the coefficients 3xTF32 on tcgen05 with tensor-memory
+      // accumulators and the update on mma.sync (variant 2).  While untuned,
+      // calls with many columns take the variants in turn and keep their
+      // time per column; afterwards the fastest one is used.
       int pv = c->opt.proj_variant >= 0 ? c->opt.proj_variant : c->proj_variant;
       const bool tuning = c->opt.autotune && pv < 0 && m >= 256;
-      if (pv < 0) pv = tuning ? c->proj_tune_next : 1;
+      if (pv < 0) pv = tuning ? c->proj_tune_next : 2;
       if (tuning) CK(cudaEventRecord(c->ev[0], st));
-      if (pv == 1) {
+      if (pv == 1 || pv == 2) {
         const long long lds = (s.n_ext + 3) & ~3;
         float* S;
         RET(ws(c, "pv_32", (size_t)lds * std::max(m, 1), &S));
-        CK(tc_proj_coeffs(s.n_ext, m, s.n_pw, s.d_psif, s.ld, X, s.ld, d_list, s.d_sigma32, S, lds,
-                          st, d_count));
+        if (pv == 1)
+          CK(tc_proj_coeffs(s.n_ext, m, s.n_pw, s.d_psif, s.ld, X, s.ld, d_list, s.d_sigma32, S,
+                            lds, st, d_count));
+        else
+          CK(tc5_proj_coeffs(s.n_ext, m, s.n_pw, s.d_psit5, X, s.ld, d_list, s.d_sigma32, S, lds,
+                             st, d_count, c->d_status));
         CK(tc_proj_update(s.n_pw, m, s.n_ext, s.d_psif, s.ld, S, lds, Y, s.ld, d_list, st,
                           d_count));
       } else {
@@ -615,10 +622,14 @@ int apply_h(pdep_ctx* c, SysData& s, const R* X, R* Y, int n, const int* d_list,
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
         c->proj_tune_ms[pv] += ms / m;
-        // two timed calls per variant, alternating
-        if (++c->proj_tune_next == 2) c->proj_tune_next = 0;
-        if (++c->proj_tune_calls == 4)
-          c->proj_variant = c->proj_tune_ms[1] <= c->proj_tune_ms[0] ? 1 : 0;
+        // two timed calls per variant, in turn
+        if (++c->proj_tune_next == 3) c->proj_tune_next = 0;
+        if (++c->proj_tune_calls == 6) {
+          int best = 0;
+          for (int v = 1; v < 3; ++v)
+            if (c->proj_tune_ms[v] <= c->proj_tune_ms[best]) best = v;
+          c->proj_variant = best;
+        }
       }
       return PDEP_OK;
     }
@@ -1034,6 +1045,8 @@ int setup_states(pdep_ctx* c, SysData& s, cudaStream_t st) {
   CK(cudaMemcpy2DAsync(s.d_psi, s.ld * sizeof(double), X, s.ld * sizeof(double),
                        s.n_pw * sizeof(double), next, cudaMemcpyDeviceToDevice, st));
   CK((convert<float, double>(s.d_psif, s.ld, s.d_psi, s.ld, s.ld, next, st)));
+  RET(persistent(c, &s.d_psit5, tc5_split_floats(next, s.n_pw)));
+  CK(tc5_split_states(next, s.n_pw, s.d_psif, s.ld, s.d_psit5, st));
   std::vector<double> ne(nocc);
   for (int v = 0; v < nocc; ++v) ne[v] = -s.eps[v];
   CK(cudaMemcpyAsync(s.d_negeps, ne.data(), sizeof(double) * nocc, cudaMemcpyHostToDevice, st));
@@ -1797,6 +1810,8 @@ int pdep_setup(const pdep_system_desc* sys, int n_sys, const pdep_options* opt, 
   if (c->opt.precision == PDEP_MIXED_BF16)
     return bail(fail(PDEP_ERR_UNSUPPORTED, "PDEP_MIXED_BF16: no BF16 projection kernel in this build"));
   if (c->opt.clock_budget_cycles < 0) return bail(fail(PDEP_ERR_INVALID_ARG, "negative clock budget"));
+  if (c->opt.proj_variant < -1 || c->opt.proj_variant > 2)
+    return bail(fail(PDEP_ERR_INVALID_ARG, "unknown projection kernel"));
   if (cudaMalloc(&c->d_status, sizeof(unsigned)) != cudaSuccess ||
       cudaMalloc(&c->d_counter, 4 * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&c->d_loop, sizeof(CgLoopState)) != cudaSuccess ||

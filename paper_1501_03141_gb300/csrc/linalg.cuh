@@ -140,6 +140,21 @@ cudaError_t tc_proj_update(int M, int N, int K, const float* P, long long ldp, c
                            long long lds, float* Y, long long ldy, const int* cmap,
                            cudaStream_t st, const int* ndev = nullptr);
 
+// The coefficients on the Blackwell tensor cores (tcgen05.mma kind::tf32
+// into tensor memory, 3xTF32, every 32-wide K stage flushed to FP32
+// registers; warp-specialised, one CTA per SM over equal shares of the
+// work).  The states come as hi / lo tiles written once by tc5_split_states
+// (tc5_split_floats(n_ext, K) floats, 16-byte aligned); X rows as above;
+// the result is S[j][w] = sigma_w <w|x_bmap(j)> at S + j lds + w (lds >=
+// n_ext, a multiple of 4).  A wait on the tensor cores or a copy that runs
+// out (about a second) sets DEV_TIMEOUT in *status and leaves S incomplete.
+size_t tc5_split_floats(int n_ext, int K);
+cudaError_t tc5_split_states(int n_ext, int K, const float* P, long long ldp, float* Pt,
+                             cudaStream_t st);
+cudaError_t tc5_proj_coeffs(int n_ext, int N, int K, const float* Pt, const float* X,
+                            long long ldx, const int* bmap, const float* sigma, float* S,
+                            long long lds, cudaStream_t st, const int* ndev, unsigned* status);
+
 // Per-RHS preconditioned CG kernels (one CTA per RHS vector).
 // State of one RHS: x, r, p (length n_pw, stride ld), scalars in CgScal.
 struct CgScal {

@@ -77,23 +77,28 @@ def test_deflation_does_not_change_the_solution():
 
 @pytest.mark.parametrize("name", ["tiny", "cube48"])
 def test_projection_kernels_agree(name):
-    """Mixed mode: the FP32 projection term on CUDA cores and on tensor cores
-    (3xTF32) give the same FP64-refined solutions and similar CG work."""
+    """Mixed mode: the FP32 projection term on CUDA cores, on mma.sync tensor
+    cores (3xTF32) and with the coefficients on tcgen05 tensor cores
+    (tensor-memory accumulators, 3xTF32) give the same FP64-refined solutions
+    and similar CG work."""
     need_gpu()
     lib_ready()
     import paper_1501_03141_gb300 as pg
     s = synthetic.make_system(name)
     n_pert = 2 if name == "tiny" else 4
     dv = synthetic.random_grid_potentials(31, n_pert, s.grid, s.cell).reshape(n_pert, -1)
-    out = {}
-    with pg.Context(s, precision=1, proj_variant=0) as ctx:
-        psi0, _ = ctx.occupied()
-        out[0] = ctx.sternheimer_solve(dv)
-    with pg.Context(s, precision=1, proj_variant=1) as ctx:
-        psi1, _ = ctx.occupied()
-        out[1] = ctx.sternheimer_solve(dv)
-    # same setup eigensolve in both contexts (FP64, deterministic up to sign)
-    sg = np.sign(np.sum(psi0 * psi1, axis=1))
-    assert np.all(out[0][2] <= 1e-10) and np.all(out[1][2] <= 1e-10)
-    assert rel(out[1][0] * sg[None, :, None], out[0][0]) < 1e-8
-    assert out[1][1].sum() <= 1.1 * out[0][1].sum()
+    out, psi = {}, {}
+    for pv in (0, 1, 2):
+        with pg.Context(s, precision=1, proj_variant=pv) as ctx:
+            psi[pv], _ = ctx.occupied()
+            out[pv] = ctx.sternheimer_solve(dv)
+            assert ctx.stats()["proj_variant"] == pv
+    for pv in (1, 2):
+        # same setup eigensolve in every context (FP64, deterministic up to sign)
+        sg = np.sign(np.sum(psi[0] * psi[pv], axis=1))
+        assert np.all(out[pv][2] <= 1e-10)
+        e = rel(out[pv][0] * sg[None, :, None], out[0][0])
+        print(f"{name}: projection variant {pv} vs CUDA-core FP32: {e:.2e}, CG iterations "
+              f"{out[pv][1].sum()} vs {out[0][1].sum()}")
+        assert e < 1e-8
+        assert out[pv][1].sum() <= 1.1 * out[0][1].sum()
