@@ -160,12 +160,15 @@ typedef struct {
                                 graph with a device-driven while node (no host round trip
                                 per step) once the autotuner has fixed the launch shapes;
                                 0: a host loop that reads the loop state after every step */
-  int df_refine;             /* mixed modes: 1 (default) = the refinement's A delta (and the
-                                density response accumulated with it) through transforms in
-                                double-float arithmetic (pairs of FP32 numbers, about 48
-                                significant bits; the FP32 pipe runs 64x the FP64 rate),
-                                vectors, residuals and projections in FP64; 0 = FP64
-                                transforms */
+  int df_refine;             /* mixed modes, precision of the refinement's A delta (and of
+                                the density response accumulated with it); vectors,
+                                residuals and the density stay FP64 throughout.
+                                2 (default): transforms in double-float arithmetic (pairs
+                                of FP32 numbers, about 48 significant bits; the FP32 pipe
+                                runs 64x the FP64 rate) in the first round, FP32 in later
+                                rounds, whose correction is about inner_tol of the
+                                solution, so that FP32 errs by ~1e-7 inner_tol ||b||;
+                                1: double-float in every round; 0: FP64 transforms */
   int fused_hpsi;            /* 1 (default): the FP32 H x of the inner CG on the cubic grids
                                 24^3 .. 48^3 in one launch that keeps each item's column
                                 scratch in shared memory; 0: three launches through a

@@ -525,7 +525,7 @@ int apply_h(pdep_ctx* c, SysData& s, const R* X, R* Y, int n, const int* d_list,
   if constexpr (std::is_same<C, float>::value) {
     // FP32 on 24^3 .. 48^3: the whole transform in one launch, the column
     // scratch in shared memory
-    if (n_items > 0 && c->opt.fused_hpsi && hpsi_fused_smem(s.sf) > 0) {
+    if (n_items > 0 && !dn && c->opt.fused_hpsi && hpsi_fused_smem(s.sf) > 0) {
       Epilogue<float> ep{};
       ep.y = Y;
       ep.ldy = s.ld;
@@ -1355,6 +1355,16 @@ int refine_rounds(pdep_ctx* c, SysData& s, const double* b, const double* xd, do
   RET(ws(c, "mx_list", (size_t)n, &list));
   RET(ws(c, "sv_dl", (size_t)n * s.ld, &dl));
   if (fp64) RET(ws(c, "rf_tolv", (size_t)n, &tolv));
+  // mixed modes, df_refine 2: after the first round the correction delta is
+  // about inner_tol of the solution, so its product A delta (and its share
+  // of the density response) in FP32 errs by ~1e-7 inner_tol ||b||, far
+  // below cg_tol: those rounds run the FP32 transforms on an FP32 copy
+  float *dlf = nullptr, *adf = nullptr;
+  const bool f32_later = !fp64 && c->opt.df_refine == 2;
+  if (f32_later) {
+    RET(ws(c, "rf_dlf", (size_t)n * s.ld, &dlf));
+    RET(ws(c, "rf_adf", (size_t)n * s.ld, &adf));
+  }
   CK(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)n * s.ld, st));
   CK(fill_value(rel, n, 1.0, st));
   int* n_un = c->d_refine;
@@ -1371,7 +1381,14 @@ int refine_rounds(pdep_ctx* c, SysData& s, const double* b, const double* xd, do
     CK(cg_collect(sc, n, its_total, c->d_dstats, st));
     // delta = rn d (+ xd in the first round, when every RHS is listed)
     const double* xr = round == 0 ? xd : nullptr;
-    CK(refine_delta<Ri>(x, dl, s.ld, di, s.ld, s.n_pw, n, rn, xr, st));
+    const bool f32_round = f32_later && round > 0;
+    CK(refine_delta<Ri>(x, dl, s.ld, di, s.ld, s.n_pw, n, rn, xr, st, f32_round ? dlf : nullptr));
+    if (f32_round) {
+      RET(apply_h<float>(c, s, dlf, adf, n, list, n, true, true, st, dn, n_un));
+      CK(residual_update(r64, adf, b, s.ld, s.n_pw, n, rel, list, xr, s.d_sigma64, s.n_occ, st,
+                         n_un));
+      continue;
+    }
     if (!fp64 && c->opt.df_refine)
       RET(apply_h<df>(c, s, dl, ad, n, list, n, true, true, st, dn, n_un));
     else
@@ -1495,7 +1512,7 @@ int chi0_internal(pdep_ctx* c, SysData& s, const double* phi, int m, double* out
   NvtxRange nv("chi0bar_apply");
   const int nocc = s.n_occ;
   // perturbation chunk: keep roughly 10 vectors of n_rhs*ld doubles bounded
-  size_t per = (size_t)nocc * s.ld * sizeof(double) * 9 + b1_count(s, (nocc + 1) / 2) * 16 +
+  size_t per = (size_t)nocc * s.ld * sizeof(double) * 10 + b1_count(s, (nocc + 1) / 2) * 24 +
                (size_t)s.n_r * 16;
   size_t budget = (size_t)24 << 30;
   if (c->opt.workspace_limit_bytes) budget = c->opt.workspace_limit_bytes / 2;
@@ -1722,7 +1739,7 @@ void pdep_default_options(pdep_options* o) {
   o->clock_budget_cycles = 0;
   o->autotune = 1;
   o->use_graph = 1;
-  o->df_refine = 1;
+  o->df_refine = 2;
   o->fused_hpsi = 1;
 }
 
@@ -1810,6 +1827,8 @@ int pdep_setup(const pdep_system_desc* sys, int n_sys, const pdep_options* opt, 
   if (c->opt.precision == PDEP_MIXED_BF16)
     return bail(fail(PDEP_ERR_UNSUPPORTED, "PDEP_MIXED_BF16: no BF16 projection kernel in this build"));
   if (c->opt.clock_budget_cycles < 0) return bail(fail(PDEP_ERR_INVALID_ARG, "negative clock budget"));
+  if (c->opt.df_refine < 0 || c->opt.df_refine > 2)
+    return bail(fail(PDEP_ERR_INVALID_ARG, "unknown df_refine mode"));
   if (c->opt.proj_variant < -1 || c->opt.proj_variant > 2)
     return bail(fail(PDEP_ERR_INVALID_ARG, "unknown projection kernel"));
   if (cudaMalloc(&c->d_status, sizeof(unsigned)) != cudaSuccess ||

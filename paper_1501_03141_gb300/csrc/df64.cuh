@@ -124,6 +124,7 @@ __device__ __forceinline__ double io_of<df>(df v) {
 }
 // to FP64 for the density accumulation
 __device__ __forceinline__ double as_double(double v) { return v; }
+__device__ __forceinline__ double as_double(float v) { return v; }
 __device__ __forceinline__ double as_double(df v) { return to_double(v); }
 
 }  // namespace pdep

@@ -1645,7 +1645,7 @@ cudaError_t refine_accumulate(double* x64, long long ld64, const float* d32, lon
 template <typename Ri>
 __global__ void k_refine_delta(double* x, double* dl, long long ld, const Ri* __restrict__ d32,
                                long long ld32, int n_pw, const double* __restrict__ rn,
-                               const double* __restrict__ xd) {
+                               const double* __restrict__ xd, float* dlf) {
   const int i = blockIdx.x;
   const double f = rn ? rn[i] : 0.0;
   if (d32 && f == 0.0 && !xd) return;
@@ -1662,24 +1662,31 @@ __global__ void k_refine_delta(double* x, double* dl, long long ld, const Ri* __
       xi[j] = d;
     }
     di[j] = d;
+    if (dlf) dlf[(long long)i * ld + j] = (float)d;
   }
 }
 template <typename Ri>
 cudaError_t refine_delta(double* x, double* dl, long long ld, const Ri* d32, long long ld32,
-                         int n_pw, int n, const double* rn, const double* xd, cudaStream_t st) {
+                         int n_pw, int n, const double* rn, const double* xd, cudaStream_t st,
+                         float* dlf) {
   if (n <= 0) return cudaSuccess;
-  { count_launch(); k_refine_delta<Ri><<<n, 256, 0, st>>>(x, dl, ld, d32, ld32, n_pw, rn, xd); }
+  {
+    count_launch();
+    k_refine_delta<Ri><<<n, 256, 0, st>>>(x, dl, ld, d32, ld32, n_pw, rn, xd, dlf);
+  }
   return cudaGetLastError();
 }
 template cudaError_t refine_delta<float>(double*, double*, long long, const float*, long long, int,
-                                         int, const double*, const double*, cudaStream_t);
+                                         int, const double*, const double*, cudaStream_t, float*);
 template cudaError_t refine_delta<double>(double*, double*, long long, const double*, long long,
-                                          int, int, const double*, const double*, cudaStream_t);
+                                          int, int, const double*, const double*, cudaStream_t,
+                                          float*);
 
 // r_i -= ad_i (+ s_{i mod n_occ} xd_i), rel_i = ||r_i|| / ||b_i|| for the
 // listed (or all) vectors.  s_v = eps_{n_ext} - eps_v is the shifted
 // operator's eigenvalue on the deflated states, so s_v xd_i = A xd_i.
-__global__ void k_residual_update(double* r, const double* __restrict__ ad,
+template <typename Ta>
+__global__ void k_residual_update(double* r, const Ta* __restrict__ ad,
                                   const double* __restrict__ b, long long ld, int n_pw,
                                   double* rel, const int* __restrict__ list,
                                   const double* __restrict__ xd, const double* __restrict__ sv,
@@ -1690,7 +1697,7 @@ __global__ void k_residual_update(double* r, const double* __restrict__ ad,
   const double s = xd ? sv[i % n_occ] : 0.0;
   double rr = 0.0, bb = 0.0;
   for (int j = threadIdx.x; j < n_pw; j += blockDim.x) {
-    double v = r[o + j] - ad[o + j];
+    double v = r[o + j] - (double)ad[o + j];
     if (xd) v += s * xd[o + j];
     r[o + j] = v;
     const double bv = b[o + j];
@@ -1700,16 +1707,23 @@ __global__ void k_residual_update(double* r, const double* __restrict__ ad,
   double2 t = block_sum2(rr, bb);
   if (threadIdx.x == 0) rel[i] = t.y > 0.0 ? sqrt(t.x / t.y) : 0.0;
 }
-cudaError_t residual_update(double* r, const double* ad, const double* b, long long ld, int n_pw,
+template <typename Ta>
+cudaError_t residual_update(double* r, const Ta* ad, const double* b, long long ld, int n_pw,
                             int n, double* rel, const int* list, const double* xd,
                             const double* sv, int n_occ, cudaStream_t st, const int* ndev) {
   if (n <= 0) return cudaSuccess;
   {
     count_launch();
-    k_residual_update<<<n, 256, 0, st>>>(r, ad, b, ld, n_pw, rel, list, xd, sv, n_occ, ndev);
+    k_residual_update<Ta><<<n, 256, 0, st>>>(r, ad, b, ld, n_pw, rel, list, xd, sv, n_occ, ndev);
   }
   return cudaGetLastError();
 }
+template cudaError_t residual_update<double>(double*, const double*, const double*, long long, int,
+                                             int, double*, const int*, const double*,
+                                             const double*, int, cudaStream_t, const int*);
+template cudaError_t residual_update<float>(double*, const float*, const double*, long long, int,
+                                            int, double*, const int*, const double*,
+                                            const double*, int, cudaStream_t, const int*);
 
 __global__ void k_kinetic(const double* __restrict__ X, long long ld, int n_half,
                           const double* __restrict__ g2, double* out) {

@@ -269,13 +269,17 @@ cudaError_t refine_accumulate(double* x64, long long ld64, const float* d32, lon
                               int n_pw, int n, const double* rn, cudaStream_t st);
 
 // Refinement update in FP64: delta_i = rn_i d_i (+ xd_i), x_i += delta_i,
-// dl_i = delta_i; with d = null, delta_i = x_i + xd_i and x_i = delta_i.
+// dl_i = delta_i (and dlf_i = fl32(delta_i) when dlf is given, stride ld);
+// with d = null, delta_i = x_i + xd_i and x_i = delta_i.
 template <typename Ri>
 cudaError_t refine_delta(double* x, double* dl, long long ld, const Ri* d, long long ldd,
-                         int n_pw, int n, const double* rn, const double* xd, cudaStream_t st);
-// r_i -= ad_i (+ sv[i % n_occ] xd_i); rel_i = ||r_i|| / ||b_i|| (listed vectors;
-// ndev: device length of the list, <= n)
-cudaError_t residual_update(double* r, const double* ad, const double* b, long long ld, int n_pw,
+                         int n_pw, int n, const double* rn, const double* xd, cudaStream_t st,
+                         float* dlf = nullptr);
+// r_i -= ad_i (+ sv[i % n_occ] xd_i) in FP64, ad in FP64 or FP32;
+// rel_i = ||r_i|| / ||b_i|| (listed vectors; ndev: device length of the
+// list, <= n)
+template <typename Ta>
+cudaError_t residual_update(double* r, const Ta* ad, const double* b, long long ld, int n_pw,
                             int n, double* rel, const int* list, const double* xd,
                             const double* sv, int n_occ, cudaStream_t st,
                             const int* ndev = nullptr);

@@ -465,7 +465,7 @@ __device__ __forceinline__ void slab_unit(const SphereDev<R>& s, const SlabArgs<
         }
         continue;
       }
-      if constexpr (!std::is_same<R, float>::value) {
+      {
         if (a.dn && act) {
           // density response of the two vectors of the item on this z-line
           // (Eq. deltani), accumulated over the occupied states v

@@ -153,7 +153,7 @@ struct SlabArgs {
   double out_scale;
   GridSrc<R> src;        // FROM_GRID (f: one grid per group, g: per-vector grids)
   ItemMap map;
-  // HPSI (FP64 only): also accumulate dn_j(r) += dn_scale u_v(r) x_vj(r) for
+  // HPSI: also accumulate dn_j(r) += dn_scale u_v(r) x_vj(r) for
   // every vector i = j * dn_nocc + v of the item (atomically; dn may be null)
   double* dn = nullptr;
   const double* u = nullptr;  // occupied grids [dn_nocc][dn_stride]
