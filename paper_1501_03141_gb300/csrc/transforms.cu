@@ -45,6 +45,10 @@ template <typename R> struct Tpl<R, 32> { static constexpr int v = 4; };
 template <typename R> struct Tpl<R, 40> { static constexpr int v = 4; };
 template <typename R> struct Tpl<R, 48> { static constexpr int v = 4; };
 template <typename R> struct Tpl<R, 64> { static constexpr int v = 4; };
+// FP32 48-point lines on 8 lanes (6 points each): measured 1.2% faster per
+// PDEP solve than 4 lanes and 15% faster than 2 (fewer registers, more
+// resident work, at the price of one more shuffle stage)
+template <> struct Tpl<float, 48> { static constexpr int v = 8; };
 template <typename R> struct Tpl<R, 192> { static constexpr int v = 8; };
 
 bool grid_supported(int N1, int N2, int N3) {
@@ -846,6 +850,10 @@ static int fused_planes(int nslot, int tl) {
   return FUSED_THREADS / vt;
 }
 
+// groups of more than one warp synchronise on named barriers 1..G, and the
+// hardware has barriers 0..15 only
+static bool fused_barriers_ok(int G) { return FUSED_THREADS / G == 32 || G <= 15; }
+
 static int fused_tl(int N) {
   switch (N) {
     case 24: return Tpl<float, 24>::v;
@@ -864,14 +872,17 @@ int hpsi_fused_planes(const SphereDev<float>& s, int planes) {
   // a requested group must be a power of two whose thread groups (512/G
   // threads) are at least a warp; fewer threads than a plane's y-lines take
   // two rounds per pass
-  if (planes > 0 && FUSED_THREADS / planes >= 32 && (planes & (planes - 1)) == 0) return planes;
-  return G0;  // at most 16 groups: 16 single-warp groups, or <= 8 with named barriers 1..8
+  if (planes > 0 && FUSED_THREADS / planes >= 32 && (planes & (planes - 1)) == 0 &&
+      fused_barriers_ok(planes))
+    return planes;
+  return fused_barriers_ok(G0) ? G0 : 0;
 }
 
 size_t hpsi_fused_smem(const SphereDev<float>& s, int planes) {
   if (s.N1 != s.N2 || s.N2 != s.N3 || !fused_tl(s.N1)) return 0;
   const int nslot = 2 * s.R3 + 1;
   const int G = hpsi_fused_planes(s, planes);
+  if (G <= 0) return 0;
   const size_t bytes = ((size_t)s.N1 * s.n_col + (size_t)G * nslot * (s.N2 + 8)) * sizeof(cpx<float>);
   return bytes <= 225 * 1024 ? bytes : 0;
 }
