@@ -13,6 +13,8 @@ response, projection), Rayleigh-Ritz, orthonormalisation.  The setup
            the library runs on, W warm-up steps then K timed steps
            (step_ms: median and p10-p90 of the per-step times).
   fp64     the same step with the plain FP64 path.
+  bf16     the same step in the PDEP_MIXED_BF16 mode, with its eigenvalue
+           error against the FP64 path.
   e2e      the mixed step through the public API with pinned host buffers
            (start block in, eigenvalues and eigenvectors out).
   roofline the dominant kernel class of the timed region, from the library's
@@ -403,6 +405,31 @@ def run_ours(args):
                 "mixed_eig_rel_err": [float(f"{x:.3e}") for x in err]}
         c64.close()
 
+    # the BF16 mode on the same step (BF16 coefficients inside the inner CG)
+    bf16 = None
+    if args.bf16_steps > 0:
+        c16 = pg.Context(system, precision=pg.PDEP_MIXED_BF16, stream=stream.cuda_stream, **opts)
+        c16.pdep_solve(phi0=phi0_dev, eigvals=ev, eigvecs=evec)
+        torch.cuda.synchronize(dev)
+        barrier()
+        e0.record(stream)
+        s16 = 0
+        for _ in range(args.bf16_steps):
+            _, _, st = c16.pdep_solve(phi0=phi0_dev, eigvals=ev, eigvecs=evec)
+            s16 += st["sternheimer_solves"]
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        t16 = reduce_scalar(e0.elapsed_time(e1) / 1e3, "max", dev if world > 1 else None)
+        s16 = reduce_scalar(s16, "sum", dev if world > 1 else None)
+        v16 = ev.cpu().numpy()
+        bf16 = {"value": round(s16 / t16, 2), "unit": "solves/s",
+                "ms_per_step": round(1e3 * t16 / args.bf16_steps, 1),
+                "steps": args.bf16_steps, "warmup": 1,
+                "refine_rounds_max": st["refine_rounds_max"],
+                "eig_rel_err_max_vs_fp64": (float(np.max(np.abs(v16 - v64) / np.abs(v64)))
+                                            if fp64 else None)}
+        c16.close()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds)
@@ -437,6 +464,7 @@ def run_ours(args):
                        "n_deflate": int(ctx_deflate)},
             "eigenpairs_per_s": round(eigpairs, 4),
             "fp64": fp64,
+            "bf16": bf16,
             "e2e": e2e,
             "gpu_launches": int(launches),
             "graph_launches_per_step": stats["graph_launches"],
@@ -693,6 +721,8 @@ def main(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--fp64-warmup", type=int, default=1)
+    ap.add_argument("--bf16-steps", type=int, default=2,
+                    help="steps of the PDEP_MIXED_BF16 mode on the same workload (0: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--eager", action="store_true",
                     help="diagnostics: CG loops from a host loop instead of CUDA graphs, so that "

@@ -88,6 +88,7 @@ struct SysData {
   double* d_psi = nullptr;   // [n_occ][ld]
   float* d_psif = nullptr;
   float* d_psit5 = nullptr;  // d_psif as TF32 hi / lo tiles of the tcgen05 coefficients
+  unsigned short* d_psib16 = nullptr;  // d_psif as BF16 tiles (PDEP_MIXED_BF16)
   double* d_u = nullptr;     // [n_occ][n_r]  u_v(r) = Omega^{1/2} psi_v(r)
   double* d_negeps = nullptr;   // -eps_v
   float* d_negeps32 = nullptr;
@@ -163,6 +164,7 @@ struct pdep_ctx {
   int cg_variant[2] = {-1, -1};
   // autotuned FP32 projection kernel (0 CUDA-core, 1 tensor-core; -1 untuned)
   int proj_variant = -1;
+  bool cg_inner = false;  // inside an FP32 inner CG loop (BF16 coefficients in PDEP_MIXED_BF16)
   int proj_tune_next = 0;
   double proj_tune_ms[3] = {0, 0, 0};
   int proj_tune_calls = 0;
@@ -591,6 +593,19 @@ int apply_h(pdep_ctx* c, SysData& s, const R* X, R* Y, int n, const int* d_list,
       // accumulators and the update on mma.sync (variant 2).  While untuned,
       // calls with many columns take the variants in turn and keep their
       // time per column; afterwards the fastest one is used.
+      if (c->cg_inner && s.d_psib16) {
+        // PDEP_MIXED_BF16, inside the inner CG: the coefficients as one BF16
+        // product per k-step (tcgen05 kind::f16), the update in 3xTF32; the
+        // refinement rounds' products never come here
+        const long long lds = (s.n_ext + 3) & ~3;
+        float* S;
+        RET(ws(c, "pv_32", (size_t)lds * std::max(m, 1), &S));
+        CK(tc5_proj_coeffs(s.n_ext, m, s.n_pw, s.d_psib16, X, s.ld, d_list, s.d_sigma32, S, lds,
+                           st, d_count, c->d_status, true));
+        CK(tc_proj_update(s.n_pw, m, s.n_ext, s.d_psif, s.ld, S, lds, Y, s.ld, d_list, st,
+                          d_count));
+        return PDEP_OK;
+      }
       int pv = c->opt.proj_variant >= 0 ? c->opt.proj_variant : c->proj_variant;
       const bool tuning = c->opt.autotune && pv < 0 && m >= 256;
       if (pv < 0) pv = tuning ? c->proj_tune_next : 2;
@@ -1047,6 +1062,10 @@ int setup_states(pdep_ctx* c, SysData& s, cudaStream_t st) {
   CK((convert<float, double>(s.d_psif, s.ld, s.d_psi, s.ld, s.ld, next, st)));
   RET(persistent(c, &s.d_psit5, tc5_split_floats(next, s.n_pw)));
   CK(tc5_split_states(next, s.n_pw, s.d_psif, s.ld, s.d_psit5, st));
+  if (c->opt.precision == PDEP_MIXED_BF16) {
+    RET(persistent(c, &s.d_psib16, tc5_split_bytes_bf16(next, s.n_pw) / 2));
+    CK(tc5_split_states_bf16(next, s.n_pw, s.d_psif, s.ld, s.d_psib16, st));
+  }
   std::vector<double> ne(nocc);
   for (int v = 0; v < nocc; ++v) ne[v] = -s.eps[v];
   CK(cudaMemcpyAsync(s.d_negeps, ne.data(), sizeof(double) * nocc, cudaMemcpyHostToDevice, st));
@@ -1088,7 +1107,8 @@ int setup_states(pdep_ctx* c, SysData& s, cudaStream_t st) {
 // captured in a graph.
 bool tuned(const pdep_ctx* c, const SysData& s, int pi) {
   if (!c->opt.autotune) return true;
-  const bool pv_ok = pi == 1 || c->opt.proj_variant >= 0 || c->proj_variant >= 0;
+  const bool pv_ok = pi == 1 || c->opt.proj_variant >= 0 || c->proj_variant >= 0 ||
+                     c->opt.precision == PDEP_MIXED_BF16;
   const bool fused_ok = pi == 1 || !c->opt.fused_hpsi || hpsi_fused_smem(s.sf) == 0 ||
                         tune_done(c, "fused_planes:" + std::to_string(s.N[0]));
   return c->cg_variant[pi] >= 0 && pv_ok && fused_ok;
@@ -1212,6 +1232,13 @@ template <typename R>
 int cg_loop(pdep_ctx* c, SysData& s, const R* b, R* x, int n, double tol, int max_iter,
             CgScal* sc, const double* mask, cudaStream_t st, const double* tolv) {
   const int si = (int)(&s - c->sys.data());
+  // H x inside this loop is the inner CG's (restored on every return)
+  struct InnerFlag {
+    bool& f;
+    bool old;
+    InnerFlag(bool& ff, bool v) : f(ff), old(ff) { f = v; }
+    ~InnerFlag() { f = old; }
+  } inner_flag(c->cg_inner, sizeof(R) == 4);
   R *r, *p, *ap;
   int* list;
   RET(cg_workspace<R>(c, s, n, &r, &p, &ap, &list));
@@ -1337,6 +1364,16 @@ int cg_loop(pdep_ctx* c, SysData& s, const R* b, R* x, int n, double tol, int ma
 // unconverged count: the A delta and the residual update run on that many
 // listed RHS (launches sized for n).  Rounds whose list is empty cost only
 // their launches.
+// Relative reduction each FP32 inner solve aims for.  With BF16
+// coefficients the CG operator is perturbed at about 2^-9 of the projection
+// term, so a round gains little more than ~3e-3 however long the inner CG
+// runs (measured on 48^3: 5 rounds whatever the inner tolerance, fastest at
+// 3e-3): the inner CG stops there.
+inline double inner_tol_of(const pdep_ctx* c) {
+  return c->opt.precision == PDEP_MIXED_BF16 ? std::max(c->opt.inner_tol, 3e-3)
+                                             : c->opt.inner_tol;
+}
+
 template <typename Ri>
 int refine_rounds(pdep_ctx* c, SysData& s, const double* b, const double* xd, double* x, int n,
                   double* dn, int* its_total, double* rel, double* r64, double* ad,
@@ -1376,7 +1413,7 @@ int refine_rounds(pdep_ctx* c, SysData& s, const double* b, const double* xd, do
     if (fp64)
       RET(cg_loop<Ri>(c, s, ri, di, n, 0.0, c->opt.cg_max_iter, sc, rn, st, tolv));
     else
-      RET(cg_loop<Ri>(c, s, ri, di, n, c->opt.inner_tol, c->opt.inner_max_iter, sc, rn, st,
+      RET(cg_loop<Ri>(c, s, ri, di, n, inner_tol_of(c), c->opt.inner_max_iter, sc, rn, st,
                       nullptr));
     CK(cg_collect(sc, n, its_total, c->d_dstats, st));
     // delta = rn d (+ xd in the first round, when every RHS is listed)
@@ -1597,7 +1634,9 @@ int read_stats(pdep_ctx* c, pdep_stats* out, cudaStream_t st) {
   memcpy(&mr, &d.max_res_bits, sizeof(double));
   out->max_cg_residual = mr;
   out->cg_variant = c->cg_variant[c->opt.precision == PDEP_FP64 ? 1 : 0];
-  out->proj_variant = c->opt.proj_variant >= 0 ? c->opt.proj_variant : c->proj_variant;
+  out->proj_variant = c->opt.precision == PDEP_MIXED_BF16
+                          ? 3
+                          : (c->opt.proj_variant >= 0 ? c->opt.proj_variant : c->proj_variant);
   out->chi0_chunks = c->st_chunks;
   // launches outside graphs are counted on the host; a graph contributes its
   // prologue (2 kernels) per launch and its body per step, the steps counted
@@ -1824,8 +1863,6 @@ int pdep_setup(const pdep_system_desc* sys, int n_sys, const pdep_options* opt, 
   if (c->opt.precision != PDEP_FP64 && c->opt.precision != PDEP_MIXED_TF32 &&
       c->opt.precision != PDEP_MIXED_BF16)
     return bail(fail(PDEP_ERR_INVALID_ARG, "unknown precision mode"));
-  if (c->opt.precision == PDEP_MIXED_BF16)
-    return bail(fail(PDEP_ERR_UNSUPPORTED, "PDEP_MIXED_BF16: no BF16 projection kernel in this build"));
   if (c->opt.clock_budget_cycles < 0) return bail(fail(PDEP_ERR_INVALID_ARG, "negative clock budget"));
   if (c->opt.df_refine < 0 || c->opt.df_refine > 2)
     return bail(fail(PDEP_ERR_INVALID_ARG, "unknown df_refine mode"));

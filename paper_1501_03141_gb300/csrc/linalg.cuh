@@ -151,9 +151,15 @@ cudaError_t tc_proj_update(int M, int N, int K, const float* P, long long ldp, c
 size_t tc5_split_floats(int n_ext, int K);
 cudaError_t tc5_split_states(int n_ext, int K, const float* P, long long ldp, float* Pt,
                              cudaStream_t st);
-cudaError_t tc5_proj_coeffs(int n_ext, int N, int K, const float* Pt, const float* X,
+// bf16: the states as BF16 tiles (tc5_split_states_bf16, tc5_split_bytes_bf16
+// bytes) and one BF16 product per k-step (PDEP_MIXED_BF16)
+size_t tc5_split_bytes_bf16(int n_ext, int K);
+cudaError_t tc5_split_states_bf16(int n_ext, int K, const float* P, long long ldp, void* Pt,
+                                  cudaStream_t st);
+cudaError_t tc5_proj_coeffs(int n_ext, int N, int K, const void* Pt, const float* X,
                             long long ldx, const int* bmap, const float* sigma, float* S,
-                            long long lds, cudaStream_t st, const int* ndev, unsigned* status);
+                            long long lds, cudaStream_t st, const int* ndev, unsigned* status,
+                            bool bf16 = false);
 
 // Per-RHS preconditioned CG kernels (one CTA per RHS vector).
 // State of one RHS: x, r, p (length n_pw, stride ld), scalars in CgScal.

@@ -19,6 +19,11 @@
 // errors of 6.5e-7 of sum |terms| (rms), 30 times those of a sequential FP32
 // FMA sum, while the flush after every stage gives 5e-9.
 //
+// A BF16 variant (PDEP_MIXED_BF16: the inner CG's coefficients to about
+// 2^-8 relative) converts X and the states to BF16 and issues one
+// tcgen05.mma.kind::f16 per 16-wide k-step; 16-bit core matrices hold 8 rows
+// x 8 elements, so a 32-wide stage has 4 of them along K (stride 512 bytes).
+//
 // Every mbarrier wait is bounded (about a second of SM cycles); a wait that
 // runs out marks the CTA aborted, the other warps give up their waits, the
 // MMA-issuing thread waits (bounded) for its MMAs and copies in flight, the
@@ -56,6 +61,20 @@ __device__ __forceinline__ int cm_off(int r, int k) {
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) |
          ((uint64_t)(1024u >> 4) << 32) | ((uint64_t)1 << 46);
+}
+__device__ __forceinline__ uint64_t smem_desc_sbo(uint32_t addr, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) |
+         ((uint64_t)(sbo >> 4) << 32) | ((uint64_t)1 << 46);
+}
+// bf16 offset of element (row r, k) of a 32-wide stage in the 16-bit
+// core-matrix layout (core (r / 8, k / 8) at (r / 8 * 4 + k / 8) * 128 bytes)
+__device__ __forceinline__ int cm_off16(int r, int k) {
+  return ((r >> 3) * 4 + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7);
+}
+__device__ __forceinline__ uint32_t bf16x2_bits(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -184,7 +203,8 @@ constexpr int C5_THREADS = 384, C5_PD = 3, C5_NTMAX = 128, C5_RMAX = 6;
 constexpr int C5_PROD = 96;                      // producer threads (warps 0-2)
 constexpr int C5_SLOT = 128 * 32 * 4;            // one X stage (raw, hi or lo)
 constexpr int C5_SMEM_MAX = 227 * 1024;          // opt-in shared memory per block
-__host__ __device__ inline int c5_pbytes(int nt) { return 256 * nt; }  // hi + lo, 32 k
+// one stage of the states: TF32 hi + lo (256 nt bytes) or BF16 (64 nt bytes)
+__host__ __device__ inline int c5_pbytes(int nt, int bf = 0) { return bf ? 64 * nt : 256 * nt; }
 // raw slots that fit beside the two converted buffers and the P ring
 // (alignment slack and the static shared memory kept aside)
 __host__ __device__ inline int c5_ring(int nt) {
@@ -220,8 +240,9 @@ struct C5Pos {
   }
 };
 
+template <int BF>
 __global__ void __launch_bounds__(C5_THREADS, 1)
-    k_tc5_coeffs(int n_ext, int N, int K, C5Geom g, const float* __restrict__ Pt,
+    k_tc5_coeffs(int n_ext, int N, int K, C5Geom g, const unsigned char* __restrict__ Pt,
                  const float* __restrict__ X, long long ldx, const int* __restrict__ bmap,
                  const float* __restrict__ sigma, float* __restrict__ S, long long lds,
                  const int* __restrict__ ndev, unsigned* status) {
@@ -314,6 +335,15 @@ __global__ void __launch_bounds__(C5_THREADS, 1)
       const float4* src = (const float4*)(base + (i % R) * C5_SLOT);
       uint4* hi = (uint4*)(base + R * C5_SLOT + (i & 1) * 2 * C5_SLOT);
       uint4* lo = hi + C5_SLOT / 16;
+      if constexpr (BF) {
+        // float4 f holds (r, k..k+3): f = (r / 8) 64 + (k / 4) 8 + r % 8
+        unsigned char* b16 = (unsigned char*)hi;
+        for (int f = tid; f < C5_SLOT / 16; f += C5_PROD) {
+          const float4 v = src[f];
+          const int r = (f >> 6) * 8 + (f & 7), k = ((f >> 3) & 7) * 4;
+          *(uint2*)(b16 + 2 * cm_off16(r, k)) = make_uint2(bf16x2_bits(v.x, v.y), bf16x2_bits(v.z, v.w));
+        }
+      } else
       for (int f = tid; f < C5_SLOT / 16; f += C5_PROD) {
         const float4 v = src[f];
         uint4 h, l;
@@ -336,14 +366,17 @@ __global__ void __launch_bounds__(C5_THREADS, 1)
   } else if (warp == 3) {
     // ---------------- MMA issue and the states' bulk copies (one lane) ----------------
     if (lane == 0) {
-      const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NT >> 3) << 17) |
+      // D FP32; A, B TF32 (2) or BF16 (1); N = NT, M = 128
+      const uint32_t fmt = BF ? 1u : 2u;
+      const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(NT >> 3) << 17) |
                              ((uint32_t)(128 >> 4) << 24);
+      const int pb = c5_pbytes(NT, BF);
       C5Pos pp = start;
       int p_i = 0;
       auto issue_p = [&]() {
         if (p_i < n) {
-          const float* src = Pt + (long long)(pp.nt * g.nks + pp.ks) * (64 * NT);
-          bulk_g2s(p0 + (p_i % C5_PD) * c5_pbytes(NT), src, c5_pbytes(NT), &p_full[p_i % C5_PD]);
+          const unsigned char* src = Pt + (long long)(pp.nt * g.nks + pp.ks) * pb;
+          bulk_g2s(p0 + (p_i % C5_PD) * pb, src, pb, &p_full[p_i % C5_PD]);
           pp.next(g, rtiles);
           ++p_i;
         }
@@ -360,8 +393,20 @@ __global__ void __launch_bounds__(C5_THREADS, 1)
           break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t ah0 = conv0 + (i & 1) * 2 * C5_SLOT, al0 = ah0 + C5_SLOT;
-        const uint32_t bh0 = p0 + (i % C5_PD) * c5_pbytes(NT), bl0 = bh0 + NT * 128;
+        const uint32_t bh0 = p0 + (i % C5_PD) * pb, bl0 = bh0 + NT * 128;
         const uint32_t td = tmem + (uint32_t)((i & 1) * 128);
+        if constexpr (BF) {
+          // two k-steps of 16 (2 core matrices along K each), one product
+#pragma unroll
+          for (int s = 0; s < 2; ++s) {
+            const uint64_t ad = smem_desc_sbo(ah0 + s * 256, 512), bd = smem_desc_sbo(bh0 + s * 256, 512);
+            asm volatile(
+                "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(td),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(s > 0 ? 1u : 0u)
+                : "memory");
+          }
+        } else
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
           const uint32_t off = s * 256;  // 8 k = 2 core matrices along K
@@ -484,6 +529,22 @@ __global__ void k_tc5_split(int n_ext, int K, C5Geom g, const float* __restrict_
   }
 }
 
+// states -> BF16 tiles [state tile][stage][NT x 32 16-bit core-matrix layout]
+__global__ void k_tc5_split_bf16(int n_ext, int K, C5Geom g, const float* __restrict__ P,
+                                 long long ldp, unsigned short* __restrict__ Pt) {
+  const long long per = 32LL * g.nt;
+  const long long total = (long long)g.ntl * g.nks * per;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long blk = e / per;
+    const int rem = (int)(e % per), r = rem >> 5, k = rem & 31;
+    const int nt = (int)(blk / g.nks), ks = (int)(blk % g.nks);
+    const int w = nt * g.nt + r, kk = ks * 32 + k;
+    const float x = (w < n_ext && kk < K) ? P[(long long)w * ldp + kk] : 0.f;
+    Pt[blk * per + cm_off16(r, k)] = (unsigned short)(bf16x2_bits(x, 0.f) & 0xFFFFu);
+  }
+}
+
 int t5_sms() {
   static const int n = [] {
     int dev = 0, sms = 0;
@@ -513,19 +574,37 @@ cudaError_t tc5_split_states(int n_ext, int K, const float* P, long long ldp, fl
   return cudaGetLastError();
 }
 
-cudaError_t tc5_proj_coeffs(int n_ext, int N, int K, const float* Pt, const float* X,
+size_t tc5_split_bytes_bf16(int n_ext, int K) {
+  if (n_ext <= 0 || K <= 0) return 0;
+  const C5Geom g = c5_geom(n_ext, K);
+  return (size_t)g.ntl * g.nks * c5_pbytes(g.nt, 1);
+}
+
+cudaError_t tc5_split_states_bf16(int n_ext, int K, const float* P, long long ldp, void* Pt,
+                                  cudaStream_t st) {
+  if (n_ext <= 0 || K <= 0) return cudaSuccess;
+  const C5Geom g = c5_geom(n_ext, K);
+  const long long total = (long long)g.ntl * g.nks * 32 * g.nt;
+  const int blocks = (int)std::min<long long>((total + 255) / 256, 8LL * t5_sms());
+  count_launch();
+  k_tc5_split_bf16<<<blocks, 256, 0, st>>>(n_ext, K, g, P, ldp, (unsigned short*)Pt);
+  return cudaGetLastError();
+}
+
+cudaError_t tc5_proj_coeffs(int n_ext, int N, int K, const void* Pt, const float* X,
                             long long ldx, const int* bmap, const float* sigma, float* S,
-                            long long lds, cudaStream_t st, const int* ndev, unsigned* status) {
+                            long long lds, cudaStream_t st, const int* ndev, unsigned* status,
+                            bool bf16) {
   if (n_ext <= 0 || N <= 0) return cudaSuccess;
   if (K <= 0) return cudaMemsetAsync(S, 0, sizeof(float) * (size_t)lds * N, st);
   const C5Geom g = c5_geom(n_ext, K);
   const int smem = c5_smem(g.nt);
-  static int attr = 0;
-  if (smem > attr) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_tc5_coeffs, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  static int attr[2] = {0, 0};
+  if (smem > attr[bf16]) {
+    cudaError_t e = cudaFuncSetAttribute(bf16 ? k_tc5_coeffs<1> : k_tc5_coeffs<0>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    attr = smem;
+    attr[bf16] = smem;
   }
   cudaError_t e = cudaMemsetAsync(S, 0, sizeof(float) * (size_t)lds * N, st);
   if (e != cudaSuccess) return e;
@@ -536,8 +615,13 @@ cudaError_t tc5_proj_coeffs(int n_ext, int N, int K, const float* Pt, const floa
   ProfScope ps(PC_GEMM_TF32, st, 2.0 * n_ext * N * (double)K,
                ((double)n_ext * K + (double)K * N + (double)n_ext * N) * sizeof(float), ndev, N);
   count_launch();
-  k_tc5_coeffs<<<grid, C5_THREADS, smem, st>>>(n_ext, N, K, g, Pt, X, ldx, bmap, sigma, S, lds,
-                                               ndev, status);
+  const unsigned char* pt = (const unsigned char*)Pt;
+  if (bf16)
+    k_tc5_coeffs<1><<<grid, C5_THREADS, smem, st>>>(n_ext, N, K, g, pt, X, ldx, bmap, sigma, S,
+                                                    lds, ndev, status);
+  else
+    k_tc5_coeffs<0><<<grid, C5_THREADS, smem, st>>>(n_ext, N, K, g, pt, X, ldx, bmap, sigma, S,
+                                                    lds, ndev, status);
   return cudaGetLastError();
 }
 

@@ -26,7 +26,7 @@ def tiny_ref():
     return pdep_reference(chi0bar_dense(b, ks), s.n_pdep)
 
 
-@pytest.mark.parametrize("precision,tol", [(0, 1e-8), (1, 1e-6)])
+@pytest.mark.parametrize("precision,tol", [(0, 1e-8), (1, 1e-6), (2, 1e-6)])
 def test_tiny_eigenpairs(precision, tol, tiny_ref):
     need_gpu()
     lib_ready()
@@ -70,9 +70,16 @@ def test_cube48_mixed_vs_fp64_and_rayleigh():
         ev64, vec64, st64 = ctx.pdep_solve()
     with pg.Context(s, precision=pg.PDEP_MIXED, **opts) as ctx:
         ev32, vec32, st32 = ctx.pdep_solve()
+    with pg.Context(s, precision=pg.PDEP_MIXED_BF16, **opts) as ctx:
+        ev16, _, st16 = ctx.pdep_solve()
     assert st64["dav_iterations"] == 6 and st32["dav_iterations"] == 6
+    assert st16["dav_iterations"] == 6 and st16["proj_variant"] == 3
+    assert st16["max_cg_residual"] <= 1e-10
     err = np.abs(ev32 - ev64) / np.abs(ev64)
     assert err.max() < 1e-6, err
+    err16 = np.abs(ev16 - ev64) / np.abs(ev64)
+    print(f"cube48, 128 eigenvalues vs FP64: TF32 mode {err.max():.2e}, BF16 mode {err16.max():.2e}")
+    assert err16.max() < 1e-6, err16
     assert np.all(np.diff(ev64) >= 0) and ev64[-1] < 0
     # oracle chi0bar on sampled eigenvectors: Rayleigh quotients equal the Ritz values
     V = vec64.reshape(s.n_pdep, b.n_pdep_dim)
