@@ -204,14 +204,58 @@ __device__ __forceinline__ cpx<df> pm<df>(cpx<df> p, cpx<df> v, bool up) {
   return mk(p.x + w.x, p.y + w.y);
 }
 
+// Twiddle sources of the cross-lane line FFTs.  TableTw reads e^{2 pi i j/N}
+// from the global table per use; RegTw holds, for one lane position t, the
+// M twiddles w^{t k2} and the twiddles of the cross-lane stages with span
+// L > 4 in registers, for kernels whose threads keep one lane position
+// across many lines.
+template <typename R>
+struct TableTw {
+  const cpx<R>* __restrict__ tw;
+  template <int S>
+  __device__ __forceinline__ cpx<R> k2w(int t, int k2) const {
+    return table_w<R, S>(tw, t * k2);  // t k2 < TPL M = N
+  }
+  template <int S, int N>
+  __device__ __forceinline__ cpx<R> stage(int j, int L) const {
+    return table_w<R, S>(tw, j * (N / L));
+  }
+};
+template <typename R, int N, int TPL>
+struct RegTw {
+  static constexpr int M = N / TPL;
+  static constexpr int NS = 3;  // stages with L = 8, 16, 32 (TPL <= 32)
+  cpx<R> w[M];
+  cpx<R> sw[NS];
+  __device__ __forceinline__ void init(const cpx<R>* __restrict__ tw, int t) {
+#pragma unroll
+    for (int k2 = 0; k2 < M; ++k2) w[k2] = table_w<R, +1>(tw, t * k2);
+#pragma unroll
+    for (int si = 0; si < NS; ++si) {
+      const int half = 4 << si;  // L = 2 half
+      sw[si] = half < TPL ? table_w<R, +1>(tw, (t & (half - 1)) * (N / (2 * half))) : w[0];
+    }
+  }
+  template <int S>
+  __device__ __forceinline__ cpx<R> k2w(int, int k2) const {
+    return S > 0 ? w[k2] : conj(w[k2]);
+  }
+  // L: the stage's span (8, 16, ...), a constant once the stage loop unrolls
+  template <int S, int N_>
+  __device__ __forceinline__ cpx<R> stage(int, int L) const {
+    const int si = L >= 32 ? 2 : L >= 16 ? 1 : 0;  // L = 8, 16, 32
+    return S > 0 ? sw[si] : conj(sw[si]);
+  }
+};
+
 // Distribution A -> B.  t = lane index inside the group (0..TPL-1).
-template <typename R, int N, int TPL, int S>
-__device__ __forceinline__ void fft_a2b(cpx<R> (&v)[N / TPL], int t, const cpx<R>* __restrict__ tw) {
+template <typename R, int N, int TPL, int S, typename TW>
+__device__ __forceinline__ void fft_a2b(cpx<R> (&v)[N / TPL], int t, const TW& src) {
   constexpr int M = N / TPL;
   DFT<R, M, S>::run(v);
   if constexpr (TPL > 1) {
 #pragma unroll
-    for (int k2 = 1; k2 < M; ++k2) v[k2] = v[k2] * table_w<R, S>(tw, t * k2);  // t k2 < TPL M = N
+    for (int k2 = 1; k2 < M; ++k2) v[k2] = v[k2] * src.template k2w<S>(t, k2);
 #pragma unroll
     for (int half = TPL / 2; half >= 1; half >>= 1) {
       const int L = 2 * half;
@@ -228,7 +272,7 @@ __device__ __forceinline__ void fft_a2b(cpx<R> (&v)[N / TPL], int t, const cpx<R
           v[i] = rot ? mul_si<R, S>(d) : d;
         }
       } else {
-        const cpx<R> W = table_w<R, S>(tw, j * (N / L));
+        const cpx<R> W = src.template stage<S, N>(j, L);
 #pragma unroll
         for (int i = 0; i < M; ++i) {
           cpx<R> p = shfl_xor(v[i], half);
@@ -239,10 +283,14 @@ __device__ __forceinline__ void fft_a2b(cpx<R> (&v)[N / TPL], int t, const cpx<R
     }
   }
 }
+template <typename R, int N, int TPL, int S>
+__device__ __forceinline__ void fft_a2b(cpx<R> (&v)[N / TPL], int t, const cpx<R>* __restrict__ tw) {
+  fft_a2b<R, N, TPL, S>(v, t, TableTw<R>{tw});
+}
 
 // Distribution B -> A (the transposed network of fft_a2b).
-template <typename R, int N, int TPL, int S>
-__device__ __forceinline__ void fft_b2a(cpx<R> (&v)[N / TPL], int t, const cpx<R>* __restrict__ tw) {
+template <typename R, int N, int TPL, int S, typename TW>
+__device__ __forceinline__ void fft_b2a(cpx<R> (&v)[N / TPL], int t, const TW& src) {
   constexpr int M = N / TPL;
   if constexpr (TPL > 1) {
 #pragma unroll
@@ -259,7 +307,7 @@ __device__ __forceinline__ void fft_b2a(cpx<R> (&v)[N / TPL], int t, const cpx<R
           v[i] = pm(p, own, up);
         }
       } else {
-        const cpx<R> W = table_w<R, S>(tw, j * (N / L));
+        const cpx<R> W = src.template stage<S, N>(j, L);
 #pragma unroll
         for (int i = 0; i < M; ++i) {
           const cpx<R> own = up ? v[i] * W : v[i];
@@ -269,9 +317,13 @@ __device__ __forceinline__ void fft_b2a(cpx<R> (&v)[N / TPL], int t, const cpx<R
       }
     }
 #pragma unroll
-    for (int k2 = 1; k2 < M; ++k2) v[k2] = v[k2] * table_w<R, S>(tw, t * k2);  // t k2 < TPL M = N
+    for (int k2 = 1; k2 < M; ++k2) v[k2] = v[k2] * src.template k2w<S>(t, k2);
   }
   DFT<R, M, S>::run(v);
+}
+template <typename R, int N, int TPL, int S>
+__device__ __forceinline__ void fft_b2a(cpx<R> (&v)[N / TPL], int t, const cpx<R>* __restrict__ tw) {
+  fft_b2a<R, N, TPL, S>(v, t, TableTw<R>{tw});
 }
 
 // position held by (lane t, register i) in each distribution

@@ -84,11 +84,12 @@ __device__ __forceinline__ void cols_fwd_line(const SphereDev<R>& s,
                                               long long ldx, const ItemMap& map, int nl,
                                               int coef, cpx<R>* __restrict__ b1, long long g,
                                               long long total);
-template <typename R, int N1>
+template <typename R, int N1, typename TW>
 __device__ __forceinline__ void xline_inverse(const SphereDev<R>& s,
                                               const typename Io<R>::T* __restrict__ x,
                                               long long ldx, const ItemMap& map, int nl, int coef,
-                                              int item, int uc, bool live, cpx<R>* base);
+                                              int item, int uc, bool live, cpx<R>* base,
+                                              const TW& tws);
 
 template <typename R, int N1>
 __global__ void __launch_bounds__(128) k_cols_fwd(SphereDev<R> s,
@@ -115,17 +116,18 @@ __device__ __forceinline__ void cols_fwd_line(const SphereDev<R>& s,
   const int item = live ? (int)(g / s.n_ucol) : 0;
   const int uc = live ? (int)(g - (long long)item * s.n_ucol) : 0;
   xline_inverse<R, N1>(s, x, ldx, map, nl, coef, item, uc, live,
-                       b1 + (long long)item * N1 * s.n_col);
+                       b1 + (long long)item * N1 * s.n_col, TableTw<R>{s.tw1});
 }
 
 // x-line uc of item (both members of its mirror pair) from the sphere into
 // the item's column scratch 'base' ([N1][n_col], global or shared memory);
 // every lane of the warp must call it (the FFT shuffles), live or not.
-template <typename R, int N1>
+template <typename R, int N1, typename TW>
 __device__ __forceinline__ void xline_inverse(const SphereDev<R>& s,
                                               const typename Io<R>::T* __restrict__ x,
                                               long long ldx, const ItemMap& map, int nl, int coef,
-                                              int item, int uc, bool live, cpx<R>* base) {
+                                              int item, int uc, bool live, cpx<R>* base,
+                                              const TW& tws) {
   constexpr int TPL = Tpl<R, N1>::v;
   constexpr int M = N1 / TPL;
   const int t = threadIdx.x & (TPL - 1);
@@ -173,8 +175,8 @@ __device__ __forceinline__ void xline_inverse(const SphereDev<R>& s,
       }
     }
   }
-  fft_a2b<R, N1, TPL, +1>(v0, t, s.tw1);
-  fft_a2b<R, N1, TPL, +1>(v1, t, s.tw1);
+  fft_a2b<R, N1, TPL, +1>(v0, t, tws);
+  fft_a2b<R, N1, TPL, +1>(v1, t, tws);
   if (!active) return;
 #pragma unroll
   for (int i = 0; i < M; ++i) {
@@ -206,10 +208,10 @@ __device__ __forceinline__ void cols_bwd_line(const SphereDev<R>& s,
                                               const cpx<R>* __restrict__ b1, const ItemMap& map,
                                               int nl, const Epilogue<R>& ep, long long g,
                                               long long total);
-template <typename R, int N1>
+template <typename R, int N1, typename TW>
 __device__ __forceinline__ void xline_forward(const SphereDev<R>& s, const cpx<R>* base,
                                               const ItemMap& map, int nl, const Epilogue<R>& ep,
-                                              int item, int uc, bool live);
+                                              int item, int uc, bool live, const TW& tws);
 
 template <typename R, int N1>
 __global__ void __launch_bounds__(128) k_cols_bwd(SphereDev<R> s, const cpx<R>* __restrict__ b1,
@@ -230,16 +232,17 @@ __device__ __forceinline__ void cols_bwd_line(const SphereDev<R>& s,
   const bool live = g < total;
   const int item = live ? (int)(g / s.n_ucol) : 0;
   const int uc = live ? (int)(g - (long long)item * s.n_ucol) : 0;
-  xline_forward<R, N1>(s, b1 + (long long)item * N1 * s.n_col, map, nl, ep, item, uc, live);
+  xline_forward<R, N1>(s, b1 + (long long)item * N1 * s.n_col, map, nl, ep, item, uc, live,
+                       TableTw<R>{s.tw1});
 }
 
 // x-line uc of item from its column scratch 'base' back to the sphere, the
 // two real fields unpacked, through the epilogue; every lane of the warp
 // must call it.
-template <typename R, int N1>
+template <typename R, int N1, typename TW>
 __device__ __forceinline__ void xline_forward(const SphereDev<R>& s, const cpx<R>* base,
                                               const ItemMap& map, int nl, const Epilogue<R>& ep,
-                                              int item, int uc, bool live) {
+                                              int item, int uc, bool live, const TW& tws) {
   constexpr int TPL = Tpl<R, N1>::v;
   constexpr int M = N1 / TPL;
   const int lane = threadIdx.x & 31;
@@ -255,8 +258,8 @@ __device__ __forceinline__ void xline_forward(const SphereDev<R>& s, const cpx<R
     v0[i] = active ? base[(long long)i1 * s.n_col + c.col] : zero<R>();
     v1[i] = (active && !self) ? base[(long long)i1 * s.n_col + c.mcol] : zero<R>();
   }
-  fft_b2a<R, N1, TPL, -1>(v0, t, s.tw1);
-  fft_b2a<R, N1, TPL, -1>(v1, t, s.tw1);
+  fft_b2a<R, N1, TPL, -1>(v0, t, tws);
+  fft_b2a<R, N1, TPL, -1>(v1, t, tws);
 
   const int src = (lane & ~(TPL - 1)) | ((TPL - t) & (TPL - 1));
   const int ia = map.vec(item, 0, nl), ib = map.vec(item, 1, nl);
@@ -345,9 +348,9 @@ __device__ __forceinline__ int t2_at(int row, int col, int ts) {
 
 // tid / nthreads: the thread's index in, and the size of, the (warp-aligned)
 // group of threads that transforms this plane
-template <typename R, int N2>
+template <typename R, int N2, typename TW>
 __device__ __forceinline__ void y_inverse(const SphereDev<R>& s, const cpx<R>* S1, cpx<R>* T2,
-                                          int tid, int nthreads) {
+                                          int tid, int nthreads, const TW& tws) {
   constexpr int TL = Tpl<R, N2>::v;
   constexpr int TS = T2Stride<R, N2>::v;
   constexpr int M = N2 / TL;
@@ -369,7 +372,7 @@ __device__ __forceinline__ void y_inverse(const SphereDev<R>& s, const cpx<R>* S
       const int n2 = freq_of(pos_a<N2, TL>(t, i), N2);
       v[i] = (act && iabs(n2) <= info.x) ? S1[info.y + n2 + info.x] : zero<R>();
     }
-    fft_a2b<R, N2, TL, +1>(v, t, s.tw2);
+    fft_a2b<R, N2, TL, +1>(v, t, tws);
     if (act) {
 #pragma unroll
       for (int i = 0; i < M; ++i) T2[t2_at<R>(sl, pos_b<N2, TL>(t, i), TS)] = v[i];
@@ -377,9 +380,9 @@ __device__ __forceinline__ void y_inverse(const SphereDev<R>& s, const cpx<R>* S
   }
 }
 
-template <typename R, int N2>
+template <typename R, int N2, typename TW>
 __device__ __forceinline__ void y_forward(const SphereDev<R>& s, const cpx<R>* T2, cpx<R>* S1,
-                                          int tid, int nthreads) {
+                                          int tid, int nthreads, const TW& tws) {
   constexpr int TL = Tpl<R, N2>::v;
   constexpr int TS = T2Stride<R, N2>::v;
   constexpr int M = N2 / TL;
@@ -396,7 +399,7 @@ __device__ __forceinline__ void y_forward(const SphereDev<R>& s, const cpx<R>* T
     cpx<R> v[M];
 #pragma unroll
     for (int i = 0; i < M; ++i) v[i] = act ? T2[t2_at<R>(sl, pos_b<N2, TL>(t, i), TS)] : zero<R>();
-    fft_b2a<R, N2, TL, -1>(v, t, s.tw2);
+    fft_b2a<R, N2, TL, -1>(v, t, tws);
     if (act) {
 #pragma unroll
       for (int i = 0; i < M; ++i) {
@@ -423,7 +426,7 @@ __device__ __forceinline__ void slab_unit(const SphereDev<R>& s, const SlabArgs<
   if (a.mode != SLAB_FROM_GRID) {
     for (int j = threadIdx.x; j < s.n_col; j += blockDim.x) S1[j] = row[j];
     __syncthreads();
-    y_inverse<R, N2>(s, S1, T2, threadIdx.x, blockDim.x);
+    y_inverse<R, N2>(s, S1, T2, threadIdx.x, blockDim.x, TableTw<R>{s.tw2});
     __syncthreads();
   }
 
@@ -517,7 +520,7 @@ __device__ __forceinline__ void slab_unit(const SphereDev<R>& s, const SlabArgs<
   }
   if (a.mode == SLAB_TO_GRID) return;
   __syncthreads();
-  y_forward<R, N2>(s, T2, S1, threadIdx.x, blockDim.x);
+  y_forward<R, N2>(s, T2, S1, threadIdx.x, blockDim.x, TableTw<R>{s.tw2});
   __syncthreads();
   for (int j = threadIdx.x; j < s.n_col; j += blockDim.x) row[j] = S1[j];
 }
@@ -568,9 +571,10 @@ constexpr int FUSED_THREADS = 512;
 
 // z-lines of one x-plane (T2: its (n3 slot, i2) plane), the potential
 // multiplied on the grid between the inverse and forward FFTs
-template <int N>
+template <int N, typename TW>
 __device__ __forceinline__ void z_hpsi(const SphereDev<float>& s, cpx<float>* T2,
-                                       const float* __restrict__ vplane, int tid, int nthreads) {
+                                       const float* __restrict__ vplane, int tid, int nthreads,
+                                       const TW& tws) {
   constexpr int TL3 = Tpl<float, N>::v;
   constexpr int M3 = N / TL3;
   constexpr int TS = T2Stride<float, N>::v;
@@ -586,11 +590,11 @@ __device__ __forceinline__ void z_hpsi(const SphereDev<float>& s, cpx<float>* T2
       const int n3 = freq_of(pos_a<N, TL3>(t3, i), N);
       v[i] = (act && iabs(n3) <= R3) ? T2[t2_at<float>(n3 + R3, i2, TS)] : zero<float>();
     }
-    fft_a2b<float, N, TL3, +1>(v, t3, s.tw3);
+    fft_a2b<float, N, TL3, +1>(v, t3, tws);
     const float* vr = vplane + (act ? i2 : 0) * N;
 #pragma unroll
     for (int i = 0; i < M3; ++i) v[i] = scale(v[i], act ? vr[pos_b<N, TL3>(t3, i)] : 0.f);
-    fft_b2a<float, N, TL3, -1>(v, t3, s.tw3);
+    fft_b2a<float, N, TL3, -1>(v, t3, tws);
     if (act) {
 #pragma unroll
       for (int i = 0; i < M3; ++i) {
@@ -628,13 +632,17 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
   const int vt = threadIdx.x - g * VT;
   cpx<float>* T2 = B1 + (size_t)N * s.n_col + (size_t)g * nslot * TS;
   const int lines = blockDim.x / TL;
+  // a cubic grid: the x, y and z lines have one length and one twiddle
+  // table, and every pass keeps this thread at lane position t of its lines
+  RegTw<float, N, TL> rtw;
+  rtw.init(s.tw1, threadIdx.x & (TL - 1));
 #pragma unroll 1
   for (int item = blockIdx.x; item < items; item += gridDim.x) {
     __syncthreads();  // the previous item's reads of B1 are done
 #pragma unroll 1
     for (int base = 0; base < s.n_ucol; base += lines) {
       const int uc = base + threadIdx.x / TL;
-      xline_inverse<float, N>(s, x, ldx, map, nl, COEF_ONE, item, uc, uc < s.n_ucol, B1);
+      xline_inverse<float, N>(s, x, ldx, map, nl, COEF_ONE, item, uc, uc < s.n_ucol, B1, rtw);
     }
     __syncthreads();
     // the plane groups touch disjoint data (their own plane row of B1 and
@@ -645,11 +653,11 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
       const int i1 = p0 + g;
       if (i1 < N) {  // uniform over the plane group's warps
         cpx<float>* S1 = B1 + (size_t)i1 * s.n_col;
-        y_inverse<float, N>(s, S1, T2, vt, VT);
+        y_inverse<float, N>(s, S1, T2, vt, VT, rtw);
         group_sync(g, VT);
-        z_hpsi<N>(s, T2, v + (size_t)i1 * N * N, vt, VT);
+        z_hpsi<N>(s, T2, v + (size_t)i1 * N * N, vt, VT, rtw);
         group_sync(g, VT);
-        y_forward<float, N>(s, T2, S1, vt, VT);
+        y_forward<float, N>(s, T2, S1, vt, VT, rtw);
         group_sync(g, VT);
       }
     }
@@ -657,7 +665,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
 #pragma unroll 1
     for (int base = 0; base < s.n_ucol; base += lines) {
       const int uc = base + threadIdx.x / TL;
-      xline_forward<float, N>(s, B1, map, nl, ep, item, uc, uc < s.n_ucol);
+      xline_forward<float, N>(s, B1, map, nl, ep, item, uc, uc < s.n_ucol, rtw);
     }
   }
   if (threadIdx.x == 0) {
