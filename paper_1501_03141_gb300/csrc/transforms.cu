@@ -190,15 +190,47 @@ __device__ __forceinline__ void xline_inverse(const SphereDev<R>& s,
 // column pass back: x-lines -> sphere (forward transform, S = -1), Hermitian
 // unpacking of the two real fields and the epilogue
 // ---------------------------------------------------------------------------
+// One output vector's epilogue state.  FP32 (the transform of the inner
+// CG): its output and input rows and its shift, set up once per line.
+// FP64 and double-float: recomputed per element, which keeps their column
+// kernels' register counts (precomputing raised the double-float 64-point
+// one from 192 to 253).
+template <typename R, bool Pre = std::is_same<R, float>::value>
+struct OutRow;
 template <typename R>
-__device__ __forceinline__ void write_out(const Epilogue<R>& ep, int vec, int j, R val, R coefv,
-                                          R diag) {
-  typename Io<R>::T* y = ep.y + (long long)vec * ep.ldy;
-  R r = ep.scale * coefv * val;
-  if (ep.x_in) {
-    const R sh = ep.shift ? ld_io<R>(ep.shift + vec % ep.shift_period) : R(0);
-    r += (diag + sh) * ld_io<R>(ep.x_in + (long long)vec * ep.ldx + j);
+struct OutRow<R, true> {
+  typename Io<R>::T* y_;
+  const typename Io<R>::T* x_;  // null: no diagonal term
+  R sh_;
+  __device__ __forceinline__ OutRow(const Epilogue<R>& ep, int vec) {
+    y_ = ep.y + (long long)(vec >= 0 ? vec : 0) * ep.ldy;
+    x_ = ep.x_in ? ep.x_in + (long long)(vec >= 0 ? vec : 0) * ep.ldx : nullptr;
+    sh_ = (ep.x_in && ep.shift && vec >= 0) ? ld_io<R>(ep.shift + vec % ep.shift_period) : R(0);
   }
+  __device__ __forceinline__ typename Io<R>::T* y(const Epilogue<R>&) const { return y_; }
+  __device__ __forceinline__ const typename Io<R>::T* x(const Epilogue<R>&) const { return x_; }
+  __device__ __forceinline__ R sh(const Epilogue<R>&) const { return sh_; }
+};
+template <typename R>
+struct OutRow<R, false> {
+  int vec;
+  __device__ __forceinline__ OutRow(const Epilogue<R>&, int v) : vec(v) {}
+  __device__ __forceinline__ typename Io<R>::T* y(const Epilogue<R>& ep) const {
+    return ep.y + (long long)vec * ep.ldy;
+  }
+  __device__ __forceinline__ const typename Io<R>::T* x(const Epilogue<R>& ep) const {
+    return ep.x_in ? ep.x_in + (long long)vec * ep.ldx : nullptr;
+  }
+  __device__ __forceinline__ R sh(const Epilogue<R>& ep) const {
+    return ep.shift ? ld_io<R>(ep.shift + vec % ep.shift_period) : R(0);
+  }
+};
+template <typename R>
+__device__ __forceinline__ void write_out(const Epilogue<R>& ep, const OutRow<R>& o, int j, R val,
+                                          R coefv, R diag) {
+  typename Io<R>::T* y = o.y(ep);
+  R r = ep.scale * coefv * val;
+  if (const typename Io<R>::T* x = o.x(ep)) r += (diag + o.sh(ep)) * ld_io<R>(x + j);
   if (ep.beta != 0) r += R(ep.beta) * ld_io<R>(y + j);
   y[j] = io_of<R>(r);
 }
@@ -263,6 +295,7 @@ __device__ __forceinline__ void xline_forward(const SphereDev<R>& s, const cpx<R
 
   const int src = (lane & ~(TPL - 1)) | ((TPL - t) & (TPL - 1));
   const int ia = map.vec(item, 0, nl), ib = map.vec(item, 1, nl);
+  const OutRow<R> oa(ep, ia), ob(ep, ib);
   const R rs2 = R(0.70710678118654752440084436210485);
 #pragma unroll
   for (int i = 0; i < M; ++i) {
@@ -285,18 +318,18 @@ __device__ __forceinline__ void xline_forward(const SphereDev<R>& s, const cpx<R
       const R cf = coef_of<R>(ep.coef, s.g2, k);
       const R dg = ep.kin * s.kin[k];
       if (ia >= 0) {
-        write_out(ep, ia, 2 * k, rs2 * sa.x, cf, dg);
-        write_out(ep, ia, 2 * k + 1, rs2 * sa.y, cf, dg);
+        write_out(ep, oa, 2 * k, rs2 * sa.x, cf, dg);
+        write_out(ep, oa, 2 * k + 1, rs2 * sa.y, cf, dg);
       }
       if (ib >= 0) {
-        write_out(ep, ib, 2 * k, rs2 * sb.y, cf, dg);
-        write_out(ep, ib, 2 * k + 1, -rs2 * sb.x, cf, dg);
+        write_out(ep, ob, 2 * k, rs2 * sb.y, cf, dg);
+        write_out(ep, ob, 2 * k + 1, -rs2 * sb.x, cf, dg);
       }
     } else if (self && n1 == 0) {
       const R cf = (ep.coef == COEF_ONE) ? R(1) : R(0);
       const int j0 = 2 * s.n_half;
-      if (ia >= 0) write_out(ep, ia, j0, d.x, cf, R(0));
-      if (ib >= 0) write_out(ep, ib, j0, d.y, cf, R(0));
+      if (ia >= 0) write_out(ep, oa, j0, d.x, cf, R(0));
+      if (ib >= 0) write_out(ep, ob, j0, d.y, cf, R(0));
     }
   }
 }
