@@ -348,13 +348,14 @@ struct SlabThreads {
 // FP32 slabs keep three blocks of up to 256 threads per SM resident
 // (register budget ~85-110); FP64 slabs are bound by the FP64 pipe at one
 // block per SM.
-// Double-float slabs run on the FP32 pipe: two resident blocks per SM (at
-// most 170 registers for 192 threads) give its dependent add chains more
-// warps to hide latency behind.
+// Double-float slabs run on the FP32 pipe and are latency-bound (ncu on 48^3
+// at two blocks: 12 warps per SM, issue active 33%, short-scoreboard and
+// wait stalls first): three resident blocks per SM, although the 48^3 slab
+// then spills 64 bytes, made the 48^3 PDEP step 3.2% faster.
 template <typename R, int N2, int N3>
 struct SlabMinBlocks {
   static constexpr int t = SlabThreads<R, N2, N3>::v;
-  static constexpr int v = std::is_same<R, df>::value ? (t <= 192 ? 2 : 1)
+  static constexpr int v = std::is_same<R, df>::value ? (t <= 192 ? 3 : 1)
                            : sizeof(R) != 4                ? 1
                            : t <= 128                      ? 384 / t
                            : t <= 256                      ? 3
