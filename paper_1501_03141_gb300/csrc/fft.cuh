@@ -335,5 +335,18 @@ __device__ __forceinline__ int pos_b(int t, int i) {
 }
 // signed frequency of grid position p (|n| < N/2 for every sphere member)
 __device__ __forceinline__ int freq_of(int p, int N) { return p < N / 2 ? p : p - N; }
+// True when register i of distribution A holds, in every lane, a frequency
+// with |n| >= N/4.  The setup's aliasing guard keeps every sphere member at
+// |n| < N/4 on each axis, so such a register is zero on the way in and
+// unused on the way out; the condition folds to a constant once the
+// register loops unroll, and the compiler drops that register's work.
+__host__ __device__ constexpr bool a_outside(int N, int TPL, int i) {
+  for (int t = 0; t < TPL; ++t) {
+    const int p = t + TPL * i;
+    const int f = p < N / 2 ? p : p - N;
+    if ((f < 0 ? -f : f) < N / 4) return false;
+  }
+  return true;
+}
 
 }  // namespace pdep

@@ -145,6 +145,7 @@ __device__ __forceinline__ void xline_inverse(const SphereDev<R>& s,
   for (int i = 0; i < M; ++i) {
     v0[i] = zero<R>();
     v1[i] = zero<R>();
+    if (a_outside(N1, TPL, i)) continue;
     const int n1 = freq_of(pos_a<N1, TPL>(t, i), N1);
     if (!active) continue;
     if (!self) {
@@ -299,6 +300,7 @@ __device__ __forceinline__ void xline_forward(const SphereDev<R>& s, const cpx<R
   const R rs2 = R(0.70710678118654752440084436210485);
 #pragma unroll
   for (int i = 0; i < M; ++i) {
+    if (a_outside(N1, TPL, i)) continue;  // the same i in every lane
     // value of the mirror line at position (N1 - p) mod N1
     cpx<R> send = self ? v0[M - 1 - i] : v1[M - 1 - i];
     cpx<R> dm = shfl_idx(send, src);
@@ -404,7 +406,8 @@ __device__ __forceinline__ void y_inverse(const SphereDev<R>& s, const cpx<R>* S
 #pragma unroll
     for (int i = 0; i < M; ++i) {
       const int n2 = freq_of(pos_a<N2, TL>(t, i), N2);
-      v[i] = (act && iabs(n2) <= info.x) ? S1[info.y + n2 + info.x] : zero<R>();
+      v[i] = (!a_outside(N2, TL, i) && act && iabs(n2) <= info.x) ? S1[info.y + n2 + info.x]
+                                                                   : zero<R>();
     }
     fft_a2b<R, N2, TL, +1>(v, t, tws);
     if (act) {
@@ -437,6 +440,7 @@ __device__ __forceinline__ void y_forward(const SphereDev<R>& s, const cpx<R>* T
     if (act) {
 #pragma unroll
       for (int i = 0; i < M; ++i) {
+        if (a_outside(N2, TL, i)) continue;
         const int n2 = freq_of(pos_a<N2, TL>(t, i), N2);
         if (iabs(n2) <= info.x) S1[info.y + n2 + info.x] = v[i];
       }
@@ -622,16 +626,24 @@ __device__ __forceinline__ void z_hpsi(const SphereDev<float>& s, cpx<float>* T2
 #pragma unroll
     for (int i = 0; i < M3; ++i) {
       const int n3 = freq_of(pos_a<N, TL3>(t3, i), N);
-      v[i] = (act && iabs(n3) <= R3) ? T2[t2_at<float>(n3 + R3, i2, TS)] : zero<float>();
+      v[i] = (!a_outside(N, TL3, i) && act && iabs(n3) <= R3) ? T2[t2_at<float>(n3 + R3, i2, TS)]
+                                                              : zero<float>();
     }
     fft_a2b<float, N, TL3, +1>(v, t3, tws);
-    const float* vr = vplane + (act ? i2 : 0) * N;
+    // this lane's M3 (even) potential values are consecutive: 8-byte loads
+    const float* vr = vplane + (act ? i2 : 0) * N + pos_b<N, TL3>(t3, 0);
+    static_assert(M3 % 2 == 0, "paired potential loads");
 #pragma unroll
-    for (int i = 0; i < M3; ++i) v[i] = scale(v[i], act ? vr[pos_b<N, TL3>(t3, i)] : 0.f);
+    for (int i = 0; i < M3; i += 2) {
+      const float2 f = act ? __ldg(reinterpret_cast<const float2*>(vr + i)) : make_float2(0.f, 0.f);
+      v[i] = scale(v[i], f.x);
+      v[i + 1] = scale(v[i + 1], f.y);
+    }
     fft_b2a<float, N, TL3, -1>(v, t3, tws);
     if (act) {
 #pragma unroll
       for (int i = 0; i < M3; ++i) {
+        if (a_outside(N, TL3, i)) continue;
         const int n3 = freq_of(pos_a<N, TL3>(t3, i), N);
         if (iabs(n3) <= R3) T2[t2_at<float>(n3 + R3, i2, TS)] = v[i];
       }
