@@ -91,8 +91,16 @@ __device__ __forceinline__ void xline_inverse(const SphereDev<R>& s,
                                               int item, int uc, bool live, cpx<R>* base,
                                               const TW& tws);
 
+// resident 128-thread blocks per SM the column kernels ask for: the
+// double-float ones up to 48-point lines are latency-bound like their slab
+// (the 64-point ones would spill hundreds of bytes at four blocks)
 template <typename R, int N1>
-__global__ void __launch_bounds__(128) k_cols_fwd(SphereDev<R> s,
+struct ColsMinBlocks {
+  static constexpr int v = (std::is_same<R, df>::value && N1 <= 48) ? 4 : 1;
+};
+
+template <typename R, int N1>
+__global__ void __launch_bounds__(128, ColsMinBlocks<R, N1>::v) k_cols_fwd(SphereDev<R> s,
                                                   const typename Io<R>::T* __restrict__ x,
                                                   long long ldx, ItemMap map, int n_items,
                                                   int coef, cpx<R>* __restrict__ b1) {
@@ -247,7 +255,7 @@ __device__ __forceinline__ void xline_forward(const SphereDev<R>& s, const cpx<R
                                               int item, int uc, bool live, const TW& tws);
 
 template <typename R, int N1>
-__global__ void __launch_bounds__(128) k_cols_bwd(SphereDev<R> s, const cpx<R>* __restrict__ b1,
+__global__ void __launch_bounds__(128, ColsMinBlocks<R, N1>::v) k_cols_bwd(SphereDev<R> s, const cpx<R>* __restrict__ b1,
                                                   ItemMap map, int n_items, Epilogue<R> ep) {
   const int nl = listed_count(map);
   const long long total = (long long)items_of(map, n_items, nl) * s.n_ucol;
@@ -361,6 +369,7 @@ struct SlabMinBlocks {
                            : sizeof(R) != 4                ? 1
                            : t <= 128                      ? 384 / t
                            : t <= 256                      ? 3
+                           : t <= 384                      ? 2
                                                            : 1;
 };
 // Row stride of the (n3, i2) shared-memory plane (FP32 rows padded by 8
