@@ -360,12 +360,13 @@ struct SlabThreads {
 // block per SM.
 // Double-float slabs run on the FP32 pipe and are latency-bound (ncu on 48^3
 // at two blocks: 12 warps per SM, issue active 33%, short-scoreboard and
-// wait stalls first): three resident blocks per SM, although the 48^3 slab
-// then spills 64 bytes, made the 48^3 PDEP step 3.2% faster.
+// wait stalls first): more resident blocks win although they spill — on
+// 48^3, three blocks (64 bytes spilled) made the PDEP step 3.2% faster and
+// four (184 bytes) 1.9% more; other shapes keep three.
 template <typename R, int N2, int N3>
 struct SlabMinBlocks {
   static constexpr int t = SlabThreads<R, N2, N3>::v;
-  static constexpr int v = std::is_same<R, df>::value ? (t <= 192 ? 3 : 1)
+  static constexpr int v = std::is_same<R, df>::value ? (t <= 192 ? (N2 == 48 ? 4 : 3) : 1)
                            : sizeof(R) != 4                ? 1
                            : t <= 128                      ? 384 / t
                            : t <= 256                      ? 3
