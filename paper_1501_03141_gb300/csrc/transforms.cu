@@ -45,10 +45,9 @@ template <typename R> struct Tpl<R, 32> { static constexpr int v = 4; };
 template <typename R> struct Tpl<R, 40> { static constexpr int v = 4; };
 template <typename R> struct Tpl<R, 48> { static constexpr int v = 4; };
 template <typename R> struct Tpl<R, 64> { static constexpr int v = 4; };
-// FP32 48-point lines on 8 lanes (6 points each): measured 1.2% faster per
-// PDEP solve than 4 lanes and 15% faster than 2 (fewer registers, more
-// resident work, at the price of one more shuffle stage)
-template <> struct Tpl<float, 48> { static constexpr int v = 8; };
+// (48-point FP32 lines: 4 lanes measured fastest per PDEP solve once the
+// line FFTs skip the registers outside every sphere — half of each lane's
+// 12 here — 2.4% ahead of 8 lanes and 26% ahead of 2)
 template <typename R> struct Tpl<R, 192> { static constexpr int v = 8; };
 
 bool grid_supported(int N1, int N2, int N3) {
