@@ -76,5 +76,8 @@ def test_python_options_by_name(lib):
     o = pg.default_options(cg_tol=1e-9, dav_max_iter=7, precision=pg.PDEP_MIXED)
     assert o.cg_tol == 1e-9 and o.dav_max_iter == 7 and o.precision == pg.PDEP_MIXED
     assert o.n_deflate == 16 and o.proj_variant == -1 and o.inner_tol == 1e-5
+    # refinement products: double-float in the first round, FP32 after it
+    assert o.df_refine == 2
+    assert pg.PDEP_MIXED == pg.PDEP_MIXED_TF32 == 1 and pg.PDEP_MIXED_BF16 == 2
     with pytest.raises(KeyError):
         pg.default_options(cg_toll=1e-9)
