@@ -2175,7 +2175,6 @@ int pdep_lanczos(pdep_ctx* c, int sys, const double* R, int n, int n_steps, cons
   cudaStream_t st = (cudaStream_t)stream;
   SysData& s = c->sys[sys];
   const int K = n_steps;
-  const int nocc = s.n_occ;
   double* dL = nullptr;
   if (n_L > 0) {
     RET(ws(c, "lz_L", (size_t)n_L * s.ld, &dL));
